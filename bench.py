@@ -1,0 +1,302 @@
+"""Benchmark of the fused fluctuating lattice-Boltzmann step on GB300.
+
+One benchmark step is one time step of eq. LB (pull-stream, density, relax,
+Philox noise in the non-conserved moments, store) over the whole lattice.
+Default workload: D2Q9, FP32, periodic 2048 x 2048, tau = 0.8,
+rho_mean = 100, local Gaussian noise, uniform start.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload d2q9|d3q19|d1q3] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+lattice (seed and Philox lattice id offset by the rank): independent
+replicas, weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & % of HBM peak vs plain per-sim launch; served p50/p99 latency"
+UNIT = "GLUPS"
+
+WORKLOADS = {
+    "d2q9": dict(lattice=1, dims=(2048, 2048), tau=0.8, rho=100.0, precision=0,
+                 name="D2Q9 FP32 periodic 2048x2048, tau=0.8, rho_mean=100, local Gaussian noise, uniform start"),
+    "d3q19": dict(lattice=2, dims=(256, 256, 256), tau=1.0, rho=50.0, precision=0,
+                  name="D3Q19 FP32 periodic 256^3, tau=1.0, rho_mean=50, local Gaussian noise, uniform start"),
+    "d1q3": dict(lattice=0, dims=(256,), tau=1.0, rho=10.0, precision=1,
+                 name="D1Q3 FP64 periodic L=256, tau=1.0, rho_mean=10, local Gaussian noise, sine start"),
+}
+Q_OF = {0: 3, 1: 9, 2: 19}
+KERNEL_SOURCES = ["paper_1606_07801_gb300/csrc/step.cu", "paper_1606_07801_gb300/csrc/device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """dram bytes per launch of k_step from the committed ncu summary, or None
+    if none exists or the kernel changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != kernel_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [n for k, n in enumerate(names) if any(r[5 + k].strip() == "Active" for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(wl: dict, budget_s: float = 12.0):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of
+    the workload (fewer steps or a sub-lattice), in the metric's unit."""
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    lat, dims = wl["lattice"], wl["dims"]
+    Q = Q_OF[lat]
+    # probe on a slab to size the sample, then run a bounded number of full-lattice steps
+    N = int(np.prod(dims))
+    f = oracle.init_equilibrium(lat, np.full(N, wl["rho"]))
+    t0 = time.perf_counter()
+    f = oracle.run(lat, dims, f, 1, wl["tau"], oracle.NOISE_LOCAL, oracle.GAUSSIAN, rho_eq=wl["rho"], seed=1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(1000, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(lat, dims, f, steps, wl["tau"], oracle.NOISE_LOCAL, oracle.GAUSSIAN, rho_eq=wl["rho"], seed=1, t0=1)
+    dt = time.perf_counter() - t0
+    glups = N * steps / dt / 1e9
+    return {"value": glups, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full-lattice steps of the workload ({N} sites, Q={Q}) in FP64, {dt:.1f} s"}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    lat, dims = wl["lattice"], wl["dims"]
+    N = int(np.prod(dims))
+    f = oracle.init_equilibrium(lat, np.full(N, wl["rho"]))
+    # each reference step: one full LB step of the workload (bounded: the oracle is slow)
+    t = 0
+    for _ in range(args.warmup):
+        f = oracle.run(lat, dims, f, 1, wl["tau"], oracle.NOISE_LOCAL, oracle.GAUSSIAN, rho_eq=wl["rho"], seed=1, t0=t)
+        t += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.run(lat, dims, f, 1, wl["tau"], oracle.NOISE_LOCAL, oracle.GAUSSIAN, rho_eq=wl["rho"], seed=1, t0=t)
+        t += 1
+    dt = time.perf_counter() - t0
+    value = N * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "reference": "FP64 CPU oracle (plain C, OpenMP over sites)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} timed full-lattice steps after {args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--workload", default="d2q9", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+
+    import paper_1606_07801_gb300 as lb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    lb.load()
+
+    lat, dims, tau, rho, prec = wl["lattice"], wl["dims"], wl["tau"], wl["rho"], wl["precision"]
+    Q, N = Q_OF[lat], int(np.prod(dims))
+    elem = 8 if prec == 1 else 4
+    stream = torch.cuda.Stream()
+    init = lb.INIT_SINE if args.workload == "d1q3" else lb.INIT_UNIFORM
+    sim = lb.Simulation(lat, dims, tau, rho, 1 + rank, precision=prec, lattice_id=rank, stream=stream,
+                        torch_buffers=True, device=local, init=init, sine_amp=1.0, sine_k=(1, 0, 0))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    sim.step(args.warmup)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = lb.abi.lbfd_kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    launches = lb.abi.lbfd_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    clocks = clk.summary()
+    ms_per_step = ms / args.steps
+    value = world * N * args.steps / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (k_step is the only kernel in the timed region)
+    bytes_per_launch = 2 * Q * elem * N
+    achieved = bytes_per_launch / (ms_per_step * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic(args.workload)
+
+    # end to end through the C ABI with host buffers: per step, the state goes
+    # host -> device (pinned), one step runs, the density comes back
+    h_f = torch.empty(Q * N, dtype=torch.float64 if prec == 1 else torch.float32).pin_memory()
+    h_rho = torch.empty(N, dtype=torch.float64).pin_memory()
+    lb.abi.lbfd_get_f_raw(sim.h, h_f.data_ptr())
+    barrier()
+    e_steps = max(1, args.e2e_steps)
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        lb.abi.lbfd_set_f_raw(sim.h, h_f.data_ptr())
+        sim.step(1)
+        lb.abi.load().lbfd_moments(sim.h, h_rho.data_ptr(), None)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * N * e_steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * N * elem,
+           "d2h_bytes_per_step": N * 8}
+    sim.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == 1 else "f32", "data": "synthetic",
+            "config": {"workload": wl["name"], "sites": N, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2: %.0f MB per population buffer vs 129 MB L2" % (Q * N * elem / 1e6),
+                       "per_sim": "one lattice per GPU, one k_step launch per time step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "kernel": "k_step",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * lbfd.h -- C ABI of the GB300 fluctuating lattice-Boltzmann diffusion library.
+ *
+ * The method is the fluctuating lattice-Boltzmann scheme for the diffusion
+ * equation of Wagner & Strand (arXiv:1606.07801):
+ *   f_i(x + v_i, t + 1) = f_i(x, t) + Omega_i                       (eq. LB)
+ *   Omega_i = sum_j Lambda_ij (f^0_j - f_j) + xi_i           (eq. collision)
+ * with f^0_i = rho w_i (eq. f0def), single relaxation time Lambda = 1/tau
+ * (eq. coll), and noise xi^a in the non-conserved moments of a weighted
+ * orthonormal basis with variance rho (2 tau - 1)/tau^2 (eq. xiglobal with
+ * the global density rho^eq, eq. xilocal with the local density, which is
+ * clamped at zero as in Sec. IV).  Streaming is periodic.
+ *
+ * Every entry point returns LBFD_OK (0) or a negative status; none aborts the
+ * process.  lbfd_last_error() returns a message for the calling thread's
+ * last failure.  A handle may be used by one host thread at a time.
+ * Pointers named *_host are host memory (pageable or pinned); pointers named
+ * *_dev are device memory of the handle's device.  The library never frees
+ * memory it did not allocate.
+ */
+#ifndef LBFD_H
+#define LBFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBFD_ABI_VERSION 1
+
+/* ---- status codes ---------------------------------------------------- */
+#define LBFD_OK 0
+#define LBFD_EINVAL (-1)   /* bad argument (unknown lattice, dim < 1, tau <= 1/2, rho_mean < 0, n < 0, ...) */
+#define LBFD_ENOMEM (-2)   /* a device or host allocation failed */
+#define LBFD_ECUDA (-3)    /* a CUDA call failed; lbfd_last_error() names it */
+#define LBFD_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define LBFD_EBUSY (-5)    /* the resource is in use */
+#define LBFD_ENOTSUP (-6)  /* valid but not supported by this build */
+
+/* ---- lattices (velocity order is part of the ABI: f is stored [i][site]) -- */
+#define LBFD_D1Q3 0  /* v = 0, +1, -1;  w = 2/3, 1/6, 1/6 */
+#define LBFD_D2Q9 1  /* v = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1); w = 4/9, 1/9 x4, 1/36 x4 */
+#define LBFD_D3Q19 2 /* v = 0; (+-1,0,0),(0,+-1,0),(0,0,+-1) as +x,-x,+y,-y,+z,-z;
+                        (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0); (1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1);
+                        (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1);  w = 1/3, 1/18 x6, 1/36 x12 */
+
+/* ---- arithmetic and storage ------------------------------------------ */
+#define LBFD_F32 0 /* FP32 arithmetic and storage (default) */
+#define LBFD_F64 1 /* FP64 arithmetic and storage */
+
+/* ---- noise ------------------------------------------------------------- */
+#define LBFD_NOISE_LOCAL 0  /* variance from the local density, clamped at 0 (eq. xilocal) */
+#define LBFD_NOISE_GLOBAL 1 /* variance from rho^eq = rho_mean, the conserved mass per site (eq. xiglobal) */
+#define LBFD_NOISE_OFF 2    /* deterministic lattice-Boltzmann diffusion */
+#define LBFD_GAUSSIAN 0     /* unit normals (Box-Muller on Philox4x32-10 words) */
+#define LBFD_UNIFORM 1      /* unit-variance flat variates on (-sqrt3, sqrt3) (Sec. IV) */
+
+/* ---- initial state ------------------------------------------------------ */
+#define LBFD_INIT_UNIFORM 0 /* f_i = w_i rho_mean */
+#define LBFD_INIT_SINE 1    /* f_i = w_i (rho_mean + sine_amp sin(2 pi (kx x/Lx + ky y/Ly + kz z/Lz))) */
+#define LBFD_INIT_NONE 2    /* contents undefined until lbfd_set_f */
+
+#define LBFD_MAX_Q 19
+#define LBFD_MAX_MODES 16
+
+/* Options of lbfd_create_ex.  Fill with lbfd_options_init, then override. */
+typedef struct lbfd_options {
+    int32_t lattice;    /* LBFD_D1Q3 / LBFD_D2Q9 / LBFD_D3Q19 */
+    int32_t precision;  /* LBFD_F32 / LBFD_F64 */
+    int32_t noise_mode; /* LBFD_NOISE_* */
+    int32_t noise_dist; /* LBFD_GAUSSIAN / LBFD_UNIFORM */
+    int32_t init;       /* LBFD_INIT_* */
+    int32_t device;     /* CUDA device ordinal; -1 = the calling thread's current device */
+    int64_t dims[3];    /* Lx, Ly, Lz (x fastest); trailing dims of lower-D lattices must be 1 */
+    double tau;         /* relaxation time, > 1/2 */
+    double rho_mean;    /* mean density per site, >= 0 */
+    double sine_amp;    /* amplitude for LBFD_INIT_SINE */
+    int32_t sine_k[3];  /* integer wave vector for LBFD_INIT_SINE */
+    uint32_t lattice_id; /* Philox counter word 1: distinguishes lattices sharing a seed */
+    uint64_t seed;      /* Philox key */
+    void *stream;       /* cudaStream_t the handle works on; NULL = legacy default stream */
+    void *f_dev[2];     /* optional caller-owned device buffers, each Q*N values of the
+                           precision's type; both or neither.  Never freed by the library. */
+    int32_t n_modes;    /* structure-factor wave vectors sampled by lbfd_sample */
+    int32_t modes[LBFD_MAX_MODES][3];
+    int32_t reserved[8];
+} lbfd_options;
+
+/* Observables accumulated by lbfd_sample (FP64, deterministic reductions). */
+typedef struct lbfd_obs {
+    int64_t t;         /* steps taken since creation (or the last lbfd_set_t) */
+    int64_t n_samples; /* lbfd_sample calls since creation or lbfd_reset_obs */
+    int32_t Q, n_modes;
+    double sum_rho;    /* sum over samples of sum_x rho(x) */
+    double sum_rho2;   /* sum over samples of sum_x rho(x)^2 */
+    double sum_f[LBFD_MAX_Q];              /* sum over samples of sum_x f_i(x) */
+    double sum_ff[LBFD_MAX_Q * LBFD_MAX_Q]; /* sum over samples of sum_x f_i(x) f_j(x), [i*Q + j] */
+    double sum_sk[LBFD_MAX_MODES];         /* sum over samples of |sum_x (rho(x) - rho_mean) e^{-2 pi i k.x/L}|^2 */
+} lbfd_obs;
+
+typedef struct lbfd_sim *lbfd_t;
+
+/* Fills *opt with defaults: D2Q9, FP32, local Gaussian noise, uniform start,
+ * dims 1, tau 1, rho_mean 1, seed 1, current device, legacy default stream. */
+int lbfd_options_init(lbfd_options *opt);
+
+/* Creates a simulation (the boundary named in the method: lattice, dims, tau,
+ * rho_mean, seed) with FP32 arithmetic, local Gaussian noise and a uniform
+ * start f_i = w_i rho_mean.  dims has D entries (D = 1, 2, 3 for D1Q3, D2Q9,
+ * D3Q19).  Allocates two Q*N device buffers on the current device. */
+int lbfd_create(lbfd_t *out, int32_t lattice, const int64_t *dims, double tau, double rho_mean,
+                uint64_t seed);
+
+/* Creates a simulation from a full option set (see lbfd_options). */
+int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt);
+
+/* Frees what the handle allocated; caller-owned buffers are left alone.
+ * Synchronises the handle's stream first.  NULL is accepted. */
+int lbfd_destroy(lbfd_t h);
+
+/* Advances the state by n >= 0 steps of eq. LB (collide, add noise,
+ * stream).  Asynchronous on the handle's stream; t advances by n. */
+int lbfd_step(lbfd_t h, int64_t n);
+
+/* Waits for all work queued on the handle's stream. */
+int lbfd_sync(lbfd_t h);
+
+/* Step counter t; lbfd_set_t sets it (resume from a checkpoint: the noise
+ * is keyed by t, so a resumed run is bit-identical to an unbroken one). */
+int lbfd_get_t(lbfd_t h, int64_t *t);
+int lbfd_set_t(lbfd_t h, int64_t t);
+
+/* Copies the populations out to / in from host memory as FP64, layout
+ * [i][site], site = x + Lx (y + Ly z).  Synchronous. */
+int lbfd_get_f(lbfd_t h, double *f_host);
+int lbfd_set_f(lbfd_t h, const double *f_host);
+
+/* Same in the storage type (float for LBFD_F32, double for LBFD_F64), with
+ * no conversion: one cudaMemcpyAsync of Q*N values, then a stream sync.
+ * Pinned host memory makes these run at full link speed. */
+int lbfd_get_f_raw(lbfd_t h, void *f_host);
+int lbfd_set_f_raw(lbfd_t h, const void *f_host);
+
+/* Density rho(x) = sum_i f_i (N values) and, if j_host is not NULL, flux
+ * j_a(x) = sum_i f_i v_ia (D*N values, [a][site]), FP64, to host memory.
+ * Synchronous. */
+int lbfd_moments(lbfd_t h, double *rho_host, double *j_host);
+
+/* Same into caller-owned device buffers; asynchronous on the handle's stream. */
+int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev);
+
+/* Total mass sum_x sum_i f_i by a deterministic FP64 reduction.  Synchronous. */
+int lbfd_mass(lbfd_t h, double *mass);
+
+/* Adds the current state's statistics to the FP64 accumulators (sums of rho,
+ * rho^2, f_i, f_i f_j over sites and |rho(k)|^2 for the configured modes).
+ * Asynchronous. */
+int lbfd_sample(lbfd_t h);
+int lbfd_reset_obs(lbfd_t h);
+
+/* Reads the accumulators and the current mass.  Synchronous. */
+int lbfd_observables(lbfd_t h, lbfd_obs *obs);
+
+/* Static facts of a handle: Q, D, N (sites), bytes per stored value. */
+int lbfd_query(lbfd_t h, int32_t *Q, int32_t *D, int64_t *N, int32_t *value_bytes);
+
+/* Device buffer that holds the current state (valid until the next step),
+ * and the stream the handle works on. */
+int lbfd_state_device(lbfd_t h, void **f_dev, void **stream);
+
+/* Lattice tables the CUDA kernels use: velocities v[Q][3], weights w[Q] and
+ * the moment matrix m[a][i] (Gram-Schmidt basis of Sec. II, n_i^a = m_i^a w_i).
+ * Any output pointer may be NULL.  No device work. */
+int lbfd_lattice_tables(int32_t lattice, int32_t *Q, int32_t *v, double *w, double *m);
+
+/* Noise variates the step kernel draws: z^1..z^nmom (unit variance) of sites
+ * site0 .. site0+nsites-1 at step t, computed on the current device in the
+ * given precision and returned as FP64 [site][moment] in host memory.
+ * Philox4x32-10 call j has counter (site, lattice_id, t mod 2^32,
+ * (t >> 32) * 8 + j) and key (seed mod 2^32, seed >> 32); moments
+ * 4j+1..4j+4 take its four words.  Synchronous; allocates a temporary
+ * device buffer. */
+int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lattice_id, uint64_t t,
+                    int64_t site0, int64_t nsites, int32_t nmom, double *z_host);
+
+/* Message for the calling thread's last failure ("" if none). */
+const char *lbfd_last_error(void);
+
+/* Number of step-kernel launches the calling process has issued. */
+int64_t lbfd_kernel_launches(void);
+
+/* sizeof(lbfd_options) and sizeof(lbfd_obs) as compiled into the library,
+ * for bindings that mirror the structs.  Either pointer may be NULL. */
+int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBFD_H */

@@ -1,0 +1,132 @@
+"""GB300-native fluctuating lattice-Boltzmann diffusion (Wagner & Strand, arXiv:1606.07801).
+
+The compute path is the CUDA library ``liblbfd.so`` (sources in ``csrc/``,
+C ABI in ``include/lbfd.h``).  This package holds its ctypes binding
+(``lbfd``), the build step (``build``), seeded synthetic workloads
+(``synth``) and a small convenience wrapper, :class:`Simulation`.  PyTorch,
+when used, only provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build_mod
+from .lbfd import (D1Q3, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F64, GAUSSIAN,
+                   INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL, NOISE_LOCAL, NOISE_OFF, OK,
+                   Q_OF, UNIFORM, LbfdError, Options, load)
+from . import lbfd as abi
+
+__all__ = ["Simulation", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
+           "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
+           "INIT_NONE", "Q_OF", "D_OF"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liblbfd.so`` for sm_103a (in-tree) and return its path."""
+    return _build_mod.build(force=force)
+
+
+class Simulation:
+    """One lattice on one GPU, owned through an ``lbfd_t`` handle.
+
+    With ``torch_buffers=True`` the two population buffers are torch tensors
+    (caller-owned device memory handed to ``lbfd_create_ex``); ``stream`` may
+    be a ``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer.
+    """
+
+    def __init__(self, lattice: int, dims, tau: float, rho_mean: float, seed: int = 1, *, precision: int = F32,
+                 noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN, init: int = INIT_UNIFORM,
+                 sine_amp: float = 0.0, sine_k=(1, 0, 0), lattice_id: int = 0, modes=(), stream=None,
+                 torch_buffers: bool = False, device: int = -1):
+        o = abi.lbfd_options_init()
+        o.lattice, o.precision, o.noise_mode, o.noise_dist, o.init = lattice, precision, noise_mode, noise_dist, init
+        d = [int(x) for x in dims] + [1] * (3 - len(dims))
+        for a in range(3):
+            o.dims[a] = d[a]
+        o.tau, o.rho_mean, o.seed, o.lattice_id, o.device = float(tau), float(rho_mean), int(seed), int(lattice_id), device
+        o.sine_amp = float(sine_amp)
+        for a in range(3):
+            o.sine_k[a] = int(sine_k[a]) if a < len(sine_k) else 0
+        modes = list(modes)
+        if len(modes) > MAX_MODES:
+            raise ValueError(f"at most {MAX_MODES} structure-factor modes")
+        o.n_modes = len(modes)
+        for m, k in enumerate(modes):
+            for a in range(3):
+                o.modes[m][a] = int(k[a]) if a < len(k) else 0
+        self._keep = []
+        if stream is not None:
+            o.stream = int(getattr(stream, "cuda_stream", stream))
+            self._keep.append(stream)
+        if torch_buffers:
+            import torch
+
+            q, n = Q_OF[lattice], int(np.prod(d))
+            dt = torch.float64 if precision == F64 else torch.float32
+            dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
+            bufs = [torch.empty(q * n, dtype=dt, device=dev) for _ in range(2)]
+            o.f_dev[0], o.f_dev[1] = bufs[0].data_ptr(), bufs[1].data_ptr()
+            self._keep.extend(bufs)
+        self.lattice, self.dims, self.precision = lattice, tuple(d), precision
+        self.Q, self.D, self.N = Q_OF[lattice], D_OF[lattice], int(np.prod(d))
+        self.h = abi.lbfd_create_ex(o)
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            h, self.h = self.h, None
+            abi.lbfd_destroy(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- dynamics ----------------------------------------------------------------
+    def step(self, n: int = 1) -> None:
+        abi.lbfd_step(self.h, n)
+
+    def sync(self) -> None:
+        abi.lbfd_sync(self.h)
+
+    @property
+    def t(self) -> int:
+        return abi.lbfd_get_t(self.h)
+
+    @t.setter
+    def t(self, value: int) -> None:
+        abi.lbfd_set_t(self.h, value)
+
+    # -- state -------------------------------------------------------------------
+    def get_f(self) -> np.ndarray:
+        return abi.lbfd_get_f(self.h)
+
+    def set_f(self, f) -> None:
+        abi.lbfd_set_f(self.h, np.asarray(f, dtype=np.float64))
+
+    def moments(self, with_flux: bool = False):
+        return abi.lbfd_moments(self.h, with_flux)
+
+    def mass(self) -> float:
+        return abi.lbfd_mass(self.h)
+
+    def sample(self) -> None:
+        abi.lbfd_sample(self.h)
+
+    def reset_obs(self) -> None:
+        abi.lbfd_reset_obs(self.h)
+
+    def observables(self) -> dict:
+        return abi.lbfd_observables(self.h)
+
+    def state_device(self):
+        return abi.lbfd_state_device(self.h)

@@ -1,0 +1,432 @@
+// C ABI of the library (declared in include/lbfd.h): argument checks, device
+// memory, the step loop and the reductions.  No torch types cross it.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lbfd.h"
+
+using namespace lbfd;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(const char *what, cudaError_t e) {
+  return fail(e == cudaErrorMemoryAllocation ? LBFD_ENOMEM : LBFD_ECUDA,
+              std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define LBFD_CU(call)                                 \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(#call, e_); \
+  } while (0)
+
+// Makes a device current for the scope of an entry point, then restores.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int lattice_dims(int lattice) { return lattice == LBFD_D1Q3 ? 1 : (lattice == LBFD_D2Q9 ? 2 : 3); }
+int lattice_q(int lattice) { return lattice == LBFD_D1Q3 ? 3 : (lattice == LBFD_D2Q9 ? 9 : 19); }
+
+}  // namespace
+
+struct lbfd_sim {
+  lbfd_options opt{};
+  int Q = 0, D = 0, elem = 0;
+  int64_t N = 0;
+  void *f[2] = {nullptr, nullptr};
+  bool owns_f = false;
+  int cur = 0;
+  int64_t t = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double *partials = nullptr;  // reduction scratch, kReduceBlocks x obs_quantities
+  double *acc = nullptr;       // observable accumulators
+  int acc_n = 0;
+  double *d_mass = nullptr;
+  double *mom = nullptr;  // rho and j for lbfd_moments, allocated on first use
+  int64_t n_samples = 0;
+  int32_t modes_host[LBFD_MAX_MODES][3] = {};
+};
+
+extern "C" {
+
+int lbfd_options_init(lbfd_options *o) {
+  if (!o) return fail(LBFD_EINVAL, "lbfd_options_init: null options");
+  std::memset(o, 0, sizeof(*o));
+  o->lattice = LBFD_D2Q9;
+  o->precision = LBFD_F32;
+  o->noise_mode = LBFD_NOISE_LOCAL;
+  o->noise_dist = LBFD_GAUSSIAN;
+  o->init = LBFD_INIT_UNIFORM;
+  o->device = -1;
+  o->dims[0] = o->dims[1] = o->dims[2] = 1;
+  o->tau = 1.0;
+  o->rho_mean = 1.0;
+  o->seed = 1;
+  return LBFD_OK;
+}
+
+static int validate(const lbfd_options *o) {
+  if (o->lattice < LBFD_D1Q3 || o->lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
+  if (o->precision != LBFD_F32 && o->precision != LBFD_F64) return fail(LBFD_EINVAL, "unknown precision");
+  if (o->noise_mode < LBFD_NOISE_LOCAL || o->noise_mode > LBFD_NOISE_OFF) return fail(LBFD_EINVAL, "unknown noise mode");
+  if (o->noise_dist != LBFD_GAUSSIAN && o->noise_dist != LBFD_UNIFORM) return fail(LBFD_EINVAL, "unknown noise distribution");
+  if (o->init < LBFD_INIT_UNIFORM || o->init > LBFD_INIT_NONE) return fail(LBFD_EINVAL, "unknown init");
+  const int D = lattice_dims(o->lattice);
+  for (int a = 0; a < 3; ++a) {
+    if (o->dims[a] < 1) return fail(LBFD_EINVAL, "every dimension must be >= 1");
+    if (a >= D && o->dims[a] != 1) return fail(LBFD_EINVAL, "dimensions beyond the lattice's D must be 1");
+  }
+  if (o->dims[0] > 0x7fffffffLL) return fail(LBFD_EINVAL, "Lx too large");
+  if (o->dims[1] > 65535 || o->dims[2] > 65535) return fail(LBFD_EINVAL, "Ly and Lz must be <= 65535");
+  const double n = double(o->dims[0]) * double(o->dims[1]) * double(o->dims[2]);
+  if (n >= 2147483648.0) return fail(LBFD_EINVAL, "lattice has 2^31 sites or more");
+  if (!(o->tau > 0.5) || !std::isfinite(o->tau)) return fail(LBFD_EINVAL, "tau must be a finite number > 1/2");
+  if (!(o->rho_mean >= 0.0) || !std::isfinite(o->rho_mean)) return fail(LBFD_EINVAL, "rho_mean must be finite and >= 0");
+  if (!std::isfinite(o->sine_amp)) return fail(LBFD_EINVAL, "sine_amp must be finite");
+  if (o->n_modes < 0 || o->n_modes > LBFD_MAX_MODES) return fail(LBFD_EINVAL, "n_modes out of range");
+  if ((o->f_dev[0] == nullptr) != (o->f_dev[1] == nullptr)) return fail(LBFD_EINVAL, "give both f_dev buffers or neither");
+  if (o->f_dev[0] && o->f_dev[0] == o->f_dev[1]) return fail(LBFD_EINVAL, "the two f_dev buffers must differ");
+  return LBFD_OK;
+}
+
+static void free_sim(lbfd_sim *h) {
+  if (!h) return;
+  if (h->owns_f) {
+    cudaFree(h->f[0]);
+    cudaFree(h->f[1]);
+  }
+  cudaFree(h->partials);
+  cudaFree(h->acc);
+  cudaFree(h->d_mass);
+  cudaFree(h->mom);
+  delete h;
+}
+
+int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
+  if (!out || !opt) return fail(LBFD_EINVAL, "lbfd_create_ex: null argument");
+  *out = nullptr;
+  int rc = validate(opt);
+  if (rc) return rc;
+  int dev = opt->device;
+  if (dev < 0) LBFD_CU(cudaGetDevice(&dev));
+  DeviceGuard g(dev);
+  if (!g.ok) return fail(LBFD_ECUDA, "cannot make device current");
+  lbfd_sim *h = new (std::nothrow) lbfd_sim();
+  if (!h) return fail(LBFD_ENOMEM, "host allocation failed");
+  h->opt = *opt;
+  h->device = dev;
+  h->Q = lattice_q(opt->lattice);
+  h->D = lattice_dims(opt->lattice);
+  h->N = opt->dims[0] * opt->dims[1] * opt->dims[2];
+  h->elem = opt->precision == LBFD_F64 ? 8 : 4;
+  h->stream = static_cast<cudaStream_t>(opt->stream);
+  for (int m = 0; m < opt->n_modes; ++m)
+    for (int k = 0; k < 3; ++k) h->modes_host[m][k] = opt->modes[m][k];
+  const size_t fbytes = size_t(h->Q) * size_t(h->N) * size_t(h->elem);
+  cudaError_t e = cudaSuccess;
+  if (opt->f_dev[0]) {
+    h->f[0] = opt->f_dev[0];
+    h->f[1] = opt->f_dev[1];
+    h->owns_f = false;
+  } else {
+    h->owns_f = true;
+    e = cudaMalloc(&h->f[0], fbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->f[1], fbytes);
+  }
+  h->acc_n = 2 + h->Q + h->Q * h->Q + LBFD_MAX_MODES;
+  if (e == cudaSuccess)
+    e = cudaMalloc(&h->partials, sizeof(double) * size_t(kReduceBlocks) * obs_quantities(h->Q, LBFD_MAX_MODES));
+  if (e == cudaSuccess) e = cudaMalloc(&h->acc, sizeof(double) * h->acc_n);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_mass, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream);
+  if (e == cudaSuccess && opt->init != LBFD_INIT_NONE) {
+    const double amp = opt->init == LBFD_INIT_SINE ? opt->sine_amp : 0.0;
+    e = launch_init(opt->lattice, opt->precision, h->f[0], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
+                    int32_t(opt->dims[2]), opt->rho_mean, amp, opt->sine_k, h->stream);
+  }
+  if (e != cudaSuccess) {
+    rc = cuda_fail("lbfd_create_ex", e);
+    free_sim(h);
+    return rc;
+  }
+  *out = h;
+  return LBFD_OK;
+}
+
+int lbfd_create(lbfd_t *out, int32_t lattice, const int64_t *dims, double tau, double rho_mean, uint64_t seed) {
+  if (!out || !dims) return fail(LBFD_EINVAL, "lbfd_create: null argument");
+  if (lattice < LBFD_D1Q3 || lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
+  lbfd_options o;
+  lbfd_options_init(&o);
+  o.lattice = lattice;
+  const int D = lattice_dims(lattice);
+  for (int a = 0; a < D; ++a) o.dims[a] = dims[a];
+  o.tau = tau;
+  o.rho_mean = rho_mean;
+  o.seed = seed;
+  return lbfd_create_ex(out, &o);
+}
+
+int lbfd_destroy(lbfd_t h) {
+  if (!h) return LBFD_OK;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  free_sim(h);
+  if (e != cudaSuccess) return cuda_fail("lbfd_destroy: stream sync", e);
+  return LBFD_OK;
+}
+
+int lbfd_step(lbfd_t h, int64_t n) {
+  if (!h) return fail(LBFD_EINVAL, "lbfd_step: null handle");
+  if (n < 0) return fail(LBFD_EINVAL, "lbfd_step: n must be >= 0");
+  if (n == 0) return LBFD_OK;
+  DeviceGuard g(h->device);
+  const lbfd_options &o = h->opt;
+  StepArgs a{};
+  a.Lx = int32_t(o.dims[0]);
+  a.Ly = int32_t(o.dims[1]);
+  a.Lz = int32_t(o.dims[2]);
+  a.N = h->N;
+  a.omega = 1.0 - 1.0 / o.tau;
+  a.inv_tau = 1.0 / o.tau;
+  a.noise_var = (2.0 * o.tau - 1.0) / (o.tau * o.tau);
+  a.rho_eq = o.rho_mean;
+  a.noise_mode = o.noise_mode;
+  a.noise_dist = o.noise_dist;
+  a.key0 = uint32_t(o.seed);
+  a.key1 = uint32_t(o.seed >> 32);
+  a.lattice_id = o.lattice_id;
+  for (int64_t k = 0; k < n; ++k) {
+    const uint64_t t = uint64_t(h->t);
+    a.t_lo = uint32_t(t);
+    a.t_hi8 = uint32_t(t >> 32) << 3;
+    cudaError_t e = launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream);
+    if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
+    h->cur ^= 1;
+    h->t += 1;
+  }
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  return LBFD_OK;
+}
+
+int lbfd_sync(lbfd_t h) {
+  if (!h) return fail(LBFD_EINVAL, "lbfd_sync: null handle");
+  DeviceGuard g(h->device);
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  return LBFD_OK;
+}
+
+int lbfd_get_t(lbfd_t h, int64_t *t) {
+  if (!h || !t) return fail(LBFD_EINVAL, "lbfd_get_t: null argument");
+  *t = h->t;
+  return LBFD_OK;
+}
+
+int lbfd_set_t(lbfd_t h, int64_t t) {
+  if (!h || t < 0) return fail(LBFD_EINVAL, "lbfd_set_t: null handle or negative t");
+  h->t = t;
+  return LBFD_OK;
+}
+
+int lbfd_get_f_raw(lbfd_t h, void *f_host) {
+  if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_get_f_raw: null argument");
+  DeviceGuard g(h->device);
+  LBFD_CU(cudaMemcpyAsync(f_host, h->f[h->cur], size_t(h->Q) * h->N * h->elem, cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  return LBFD_OK;
+}
+
+int lbfd_set_f_raw(lbfd_t h, const void *f_host) {
+  if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_set_f_raw: null argument");
+  DeviceGuard g(h->device);
+  LBFD_CU(cudaMemcpyAsync(h->f[h->cur], f_host, size_t(h->Q) * h->N * h->elem, cudaMemcpyHostToDevice, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  return LBFD_OK;
+}
+
+int lbfd_get_f(lbfd_t h, double *f_host) {
+  if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_get_f: null argument");
+  if (h->elem == 8) return lbfd_get_f_raw(h, f_host);
+  std::vector<float> tmp;
+  try {
+    tmp.resize(size_t(h->Q) * h->N);
+  } catch (...) {
+    return fail(LBFD_ENOMEM, "lbfd_get_f: host staging allocation failed");
+  }
+  int rc = lbfd_get_f_raw(h, tmp.data());
+  if (rc) return rc;
+  for (size_t k = 0; k < tmp.size(); ++k) f_host[k] = double(tmp[k]);
+  return LBFD_OK;
+}
+
+int lbfd_set_f(lbfd_t h, const double *f_host) {
+  if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_set_f: null argument");
+  if (h->elem == 8) return lbfd_set_f_raw(h, f_host);
+  std::vector<float> tmp;
+  try {
+    tmp.resize(size_t(h->Q) * h->N);
+  } catch (...) {
+    return fail(LBFD_ENOMEM, "lbfd_set_f: host staging allocation failed");
+  }
+  for (size_t k = 0; k < tmp.size(); ++k) tmp[k] = float(f_host[k]);
+  return lbfd_set_f_raw(h, tmp.data());
+}
+
+int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev) {
+  if (!h || !rho_dev) return fail(LBFD_EINVAL, "lbfd_moments_device: null argument");
+  DeviceGuard g(h->device);
+  const lbfd_options &o = h->opt;
+  LBFD_CU(launch_moments(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                         int32_t(o.dims[2]), rho_dev, j_dev, h->stream));
+  return LBFD_OK;
+}
+
+int lbfd_moments(lbfd_t h, double *rho_host, double *j_host) {
+  if (!h || !rho_host) return fail(LBFD_EINVAL, "lbfd_moments: null argument");
+  DeviceGuard g(h->device);
+  if (!h->mom) LBFD_CU(cudaMalloc(&h->mom, sizeof(double) * size_t(h->N) * (1 + h->D)));
+  int rc = lbfd_moments_device(h, h->mom, j_host ? h->mom + h->N : nullptr);
+  if (rc) return rc;
+  LBFD_CU(cudaMemcpyAsync(rho_host, h->mom, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+  if (j_host)
+    LBFD_CU(cudaMemcpyAsync(j_host, h->mom + h->N, sizeof(double) * h->N * h->D, cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  return LBFD_OK;
+}
+
+int lbfd_mass(lbfd_t h, double *mass) {
+  if (!h || !mass) return fail(LBFD_EINVAL, "lbfd_mass: null argument");
+  DeviceGuard g(h->device);
+  const lbfd_options &o = h->opt;
+  LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, h->partials, h->d_mass, h->stream));
+  LBFD_CU(cudaMemcpyAsync(mass, h->d_mass, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  return LBFD_OK;
+}
+
+int lbfd_sample(lbfd_t h) {
+  if (!h) return fail(LBFD_EINVAL, "lbfd_sample: null handle");
+  DeviceGuard g(h->device);
+  const lbfd_options &o = h->opt;
+  LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                             int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials, h->acc,
+                             h->stream));
+  h->n_samples += 1;
+  return LBFD_OK;
+}
+
+int lbfd_reset_obs(lbfd_t h) {
+  if (!h) return fail(LBFD_EINVAL, "lbfd_reset_obs: null handle");
+  DeviceGuard g(h->device);
+  LBFD_CU(cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream));
+  h->n_samples = 0;
+  return LBFD_OK;
+}
+
+int lbfd_observables(lbfd_t h, lbfd_obs *obs) {
+  if (!h || !obs) return fail(LBFD_EINVAL, "lbfd_observables: null argument");
+  DeviceGuard g(h->device);
+  std::vector<double> acc(h->acc_n);
+  LBFD_CU(cudaMemcpyAsync(acc.data(), h->acc, sizeof(double) * h->acc_n, cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  std::memset(obs, 0, sizeof(*obs));
+  obs->t = h->t;
+  obs->n_samples = h->n_samples;
+  obs->Q = h->Q;
+  obs->n_modes = h->opt.n_modes;
+  const int Q = h->Q;
+  obs->sum_rho = acc[0];
+  obs->sum_rho2 = acc[1];
+  for (int i = 0; i < Q; ++i) obs->sum_f[i] = acc[2 + i];
+  for (int i = 0; i < Q * Q; ++i) obs->sum_ff[i] = acc[2 + Q + i];
+  for (int m = 0; m < h->opt.n_modes; ++m) obs->sum_sk[m] = acc[2 + Q + Q * Q + m];
+  return LBFD_OK;
+}
+
+int lbfd_query(lbfd_t h, int32_t *Q, int32_t *D, int64_t *N, int32_t *value_bytes) {
+  if (!h) return fail(LBFD_EINVAL, "lbfd_query: null handle");
+  if (Q) *Q = h->Q;
+  if (D) *D = h->D;
+  if (N) *N = h->N;
+  if (value_bytes) *value_bytes = h->elem;
+  return LBFD_OK;
+}
+
+int lbfd_state_device(lbfd_t h, void **f_dev, void **stream) {
+  if (!h) return fail(LBFD_EINVAL, "lbfd_state_device: null handle");
+  if (f_dev) *f_dev = h->f[h->cur];
+  if (stream) *stream = static_cast<void *>(h->stream);
+  return LBFD_OK;
+}
+
+int lbfd_lattice_tables(int32_t lattice, int32_t *Q, int32_t *v, double *w, double *m) {
+  if (lattice < LBFD_D1Q3 || lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
+  int q = 0, d = 0;
+  int vv[LBFD_MAX_Q * 3];
+  double ww[LBFD_MAX_Q];
+  lattice_table(lattice, &q, &d, vv, ww);
+  if (Q) *Q = q;
+  if (v)
+    for (int k = 0; k < 3 * q; ++k) v[k] = vv[k];
+  if (w)
+    for (int k = 0; k < q; ++k) w[k] = ww[k];
+  if (m) basis_table(lattice, m);
+  return LBFD_OK;
+}
+
+int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lattice_id, uint64_t t, int64_t site0,
+                    int64_t nsites, int32_t nmom, double *z_host) {
+  if (!z_host || nsites < 0 || site0 < 0) return fail(LBFD_EINVAL, "lbfd_noise_draw: bad argument");
+  if (precision != LBFD_F32 && precision != LBFD_F64) return fail(LBFD_EINVAL, "unknown precision");
+  if (dist != LBFD_GAUSSIAN && dist != LBFD_UNIFORM) return fail(LBFD_EINVAL, "unknown noise distribution");
+  if (nmom != 2 && nmom != 4 && nmom != 8 && nmom != 18) return fail(LBFD_EINVAL, "nmom must be 2, 4, 8 or 18");
+  if (site0 + nsites > 0xffffffffLL) return fail(LBFD_EINVAL, "site index beyond 32 bits");
+  if (nsites == 0) return LBFD_OK;
+  double *d = nullptr;
+  const size_t bytes = sizeof(double) * size_t(nsites) * nmom;
+  LBFD_CU(cudaMalloc(&d, bytes));
+  cudaError_t e = launch_noise_draw(precision, dist, uint32_t(seed), uint32_t(seed >> 32), lattice_id, uint32_t(t),
+                                    uint32_t(t >> 32) << 3, site0, nsites, nmom, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(z_host, d, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail("lbfd_noise_draw", e);
+  return LBFD_OK;
+}
+
+const char *lbfd_last_error(void) { return g_err.c_str(); }
+
+int64_t lbfd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes) {
+  if (options_bytes) *options_bytes = int64_t(sizeof(lbfd_options));
+  if (obs_bytes) *obs_bytes = int64_t(sizeof(lbfd_obs));
+  return LBFD_OK;
+}
+
+}  // extern "C"

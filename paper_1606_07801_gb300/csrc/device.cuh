@@ -1,0 +1,303 @@
+// Device-side building blocks of the fluctuating lattice-Boltzmann step:
+// lattice traits, the moment basis as compile-time constants, Philox4x32-10,
+// the noise variates and the noise back-transform.
+//
+// Method: Wagner & Strand, arXiv:1606.07801.
+//   - f^0_i = rho w_i, sum_i w_i v_i v_i = theta (Sec. II, eqs. f0_0-f0_2, f0def)
+//   - moments M^a = sum_i m_i^a f_i with n_i^a = m_i^a w_i and
+//     sum_i m_i^a w_i m_i^b = delta^{ab} (Sec. II, Gram-Schmidt passage)
+//   - noise xi^a, a >= 1, variance rho (2 tau - 1)/tau^2 (eqs. xiglobal, xilocal)
+#pragma once
+
+#include <stdint.h>
+
+#include <utility>
+
+namespace lbfd {
+
+enum LatticeId : int { kD1Q3 = 0, kD2Q9 = 1, kD3Q19 = 2 };
+enum NoiseMode : int { kNoiseLocal = 0, kNoiseGlobal = 1, kNoiseOff = 2 };
+enum NoiseDist : int { kGaussian = 0, kUniform = 1 };
+
+// ---------------------------------------------------------------------------
+// Compile-time iteration
+// ---------------------------------------------------------------------------
+template <int... Is, class F>
+__host__ __device__ __forceinline__ constexpr void static_for_impl(std::integer_sequence<int, Is...>, F &&f) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__host__ __device__ __forceinline__ constexpr void static_for(F &&f) {
+  static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// ---------------------------------------------------------------------------
+// Lattices.  Velocity order is the storage order of the populations.
+// ---------------------------------------------------------------------------
+template <int LAT>
+struct Lattice;
+
+template <>
+struct Lattice<kD1Q3> {
+  static constexpr int D = 1, Q = 3;
+  __host__ __device__ static constexpr int v(int i, int a) {
+    constexpr int t[3] = {0, 1, -1};
+    return a == 0 ? t[i] : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+  // seed monomial exponents (p, q, r) of v_x^p v_y^q v_z^r, Gram-Schmidt order
+  __host__ __device__ static constexpr int mono(int a, int k) { return k == 0 ? a : 0; }
+};
+
+template <>
+struct Lattice<kD2Q9> {
+  static constexpr int D = 2, Q = 9;
+  __host__ __device__ static constexpr int v(int i, int a) {
+    constexpr int t[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    return a < 2 ? t[i][a] : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+  // v_x^p v_y^q, p-major: a = 3p + q
+  __host__ __device__ static constexpr int mono(int a, int k) { return k == 0 ? a / 3 : (k == 1 ? a % 3 : 0); }
+};
+
+template <>
+struct Lattice<kD3Q19> {
+  static constexpr int D = 3, Q = 19;
+  __host__ __device__ static constexpr int v(int i, int a) {
+    constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},  {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                              {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][a];
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+  // v_x^p v_y^q v_z^r with p, q, r <= 2 and at most two of them non-zero,
+  // by total degree, then (p, q, r) descending
+  __host__ __device__ static constexpr int mono(int a, int k) {
+    constexpr int t[19][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1},
+                              {0, 2, 0}, {0, 1, 1}, {0, 0, 2}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 0, 2},
+                              {0, 2, 1}, {0, 1, 2}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}};
+    return t[a][k];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Moment basis by weighted Gram-Schmidt, evaluated by the compiler.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double ce_sqrt(double x) {
+  // Newton's iteration from above; stops when the iterate no longer falls.
+  if (!(x > 0.0)) return 0.0;
+  double r = x > 1.0 ? x : 1.0;
+  for (int k = 0; k < 2000; ++k) {
+    double n = 0.5 * (r + x / r);
+    if (!(n < r)) break;
+    r = n;
+  }
+  return r;
+}
+
+__host__ __device__ constexpr double ce_pow(int x, int p) {
+  double r = 1.0;
+  for (int k = 0; k < p; ++k) r *= static_cast<double>(x);
+  return r;
+}
+
+template <int Q>
+struct BasisTable {
+  double m[Q][Q];  // m[a][i] = m_i^a
+};
+
+template <int LAT>
+__host__ __device__ constexpr BasisTable<Lattice<LAT>::Q> make_basis() {
+  using L = Lattice<LAT>;
+  constexpr int Q = L::Q;
+  BasisTable<Q> B{};
+  for (int a = 0; a < Q; ++a) {
+    double u[Q] = {};
+    for (int i = 0; i < Q; ++i)
+      u[i] = ce_pow(L::v(i, 0), L::mono(a, 0)) * ce_pow(L::v(i, 1), L::mono(a, 1)) *
+             ce_pow(L::v(i, 2), L::mono(a, 2));
+    for (int b = 0; b < a; ++b) {
+      double p = 0.0;
+      for (int i = 0; i < Q; ++i) p += u[i] * L::w(i) * B.m[b][i];
+      for (int i = 0; i < Q; ++i) u[i] -= p * B.m[b][i];
+    }
+    double n2 = 0.0;
+    for (int i = 0; i < Q; ++i) n2 += u[i] * L::w(i) * u[i];
+    const double inv = 1.0 / ce_sqrt(n2);
+    for (int i = 0; i < Q; ++i) {
+      double x = u[i] * inv;
+      // entries that vanish by symmetry come out as exact zeros already;
+      // rounding dust below 1e-13 is zeroed so the kernel can skip it
+      B.m[a][i] = (x < 1e-13 && x > -1e-13) ? 0.0 : x;
+    }
+  }
+  return B;
+}
+
+template <int LAT>
+inline constexpr BasisTable<Lattice<LAT>::Q> kBasisTable = make_basis<LAT>();
+template <int LAT, int A, int I>
+inline constexpr double kBasis = kBasisTable<LAT>.m[A][I];
+
+// D1Q3 basis functions mu^p(v) (p = 0, 1, 2): 1, sqrt3 v, (3 v^2 - 1)/sqrt2.
+// D2Q9's basis is their product mu^p(v_x) mu^q(v_y), moment a = 3p + q.
+inline constexpr double kSqrt2 = 1.41421356237309504880;
+inline constexpr double kSqrt3 = 1.73205080756887729353;
+inline constexpr double kInvSqrt2 = 0.70710678118654752440;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+struct Philox {
+  static constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  static constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = c.x * Philox::M0, hi0 = __umulhi(c.x, Philox::M0);
+    const uint32_t lo1 = c.z * Philox::M1, hi1 = __umulhi(c.z, Philox::M1);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += Philox::W0;
+    k1 += Philox::W1;
+  }
+  return c;
+}
+
+// Top 24 bits of a word as a cell-centred uniform on (0, 1); exact in FP32.
+template <typename R>
+__device__ __forceinline__ R unit24(uint32_t r) {
+  return (static_cast<R>(r >> 8) + R(0.5)) * R(5.9604644775390625e-08);
+}
+
+template <typename R>
+struct Math;
+template <>
+struct Math<double> {
+  __device__ static __forceinline__ double log(double x) { return ::log(x); }
+  __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  __device__ static __forceinline__ void sincospi(double x, double *s, double *c) { ::sincospi(x, s, c); }
+};
+template <>
+struct Math<float> {
+  __device__ static __forceinline__ float log(float x) { return ::logf(x); }
+  __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
+  __device__ static __forceinline__ void sincospi(float x, float *s, float *c) { ::sincospif(x, s, c); }
+};
+
+// Unit-variance variates z[0..NMOM-1] (moments a = 1..NMOM) of one site.
+// Call j has counter (site, lattice_id, t_lo, t_hi * 8 + j); moment 4j + k + 1
+// takes word k.  Gaussian: Box-Muller on the word pairs (0,1) and (2,3).
+template <typename R, int NMOM>
+__device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, uint32_t lattice_id, uint32_t t_lo,
+                                              uint32_t t_hi8, uint32_t key0, uint32_t key1, int dist) {
+  constexpr int NCALL = (NMOM + 3) / 4;
+#pragma unroll
+  for (int j = 0; j < NCALL; ++j) {
+    const uint4 r = philox4x32_10(make_uint4(site, lattice_id, t_lo, t_hi8 | uint32_t(j)), key0, key1);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    if (dist == kGaussian) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        if (4 * j + 2 * p < NMOM) {
+          const R u0 = unit24<R>(w[2 * p]), u1 = unit24<R>(w[2 * p + 1]);
+          const R rad = Math<R>::sqrt(R(-2) * Math<R>::log(u0));
+          R s, c;
+          Math<R>::sincospi(R(2) * u1, &s, &c);
+          z[4 * j + 2 * p] = rad * c;
+          if (4 * j + 2 * p + 1 < NMOM) z[4 * j + 2 * p + 1] = rad * s;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (4 * j + k < NMOM) z[4 * j + k] = R(kSqrt3) * (R(2) * unit24<R>(w[k]) - R(1));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Noise back-transform T_i = sum_{a >= 1} m_i^a z^a (the f-space noise is
+// xi_i = w_i sigma T_i).
+// ---------------------------------------------------------------------------
+template <int LAT, typename R>
+struct NoiseTransform {
+  // generic: the compile-time basis with its zeros skipped
+  __device__ static __forceinline__ void apply(const R (&z)[Lattice<LAT>::Q - 1], R (&T)[Lattice<LAT>::Q]) {
+    constexpr int Q = Lattice<LAT>::Q;
+    static_for<Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      R acc = R(0);
+      bool first = true;
+      static_for<Q - 1>([&](auto A) {
+        constexpr int a = decltype(A)::value + 1;
+        constexpr double c = kBasis<LAT, a, i>;
+        if constexpr (c != 0.0) {
+          if (first) {
+            acc = R(c) * z[a - 1];
+            first = false;
+          } else {
+            acc = fma(R(c), z[a - 1], acc);
+          }
+        }
+      });
+      T[i] = acc;
+    });
+  }
+};
+
+// D2Q9: the basis factorises as mu^p(v_x) mu^q(v_y), so the transform is a
+// 3x3 pass over q followed by a 3x3 pass over p (24 multiply-adds).
+template <typename R>
+struct NoiseTransform<kD2Q9, R> {
+  __device__ static __forceinline__ void apply(const R (&z)[8], R (&T)[9]) {
+    // zeta[p][q] = z^{3p+q}, zeta[0][0] = 0
+    const R zeta[3][3] = {{R(0), z[0], z[1]}, {z[2], z[3], z[4]}, {z[5], z[6], z[7]}};
+    R G[3][3];  // G[p][c]: c = 0 (v_y = 0), 1 (v_y = +1), 2 (v_y = -1)
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      G[p][0] = fma(R(-kInvSqrt2), zeta[p][2], zeta[p][0]);
+      const R even = fma(R(kSqrt2), zeta[p][2], zeta[p][0]);
+      G[p][1] = fma(R(kSqrt3), zeta[p][1], even);
+      G[p][2] = fma(R(-kSqrt3), zeta[p][1], even);
+    }
+    R H[3][3];  // H[cx][cy]
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      H[0][c] = fma(R(-kInvSqrt2), G[2][c], G[0][c]);
+      const R even = fma(R(kSqrt2), G[2][c], G[0][c]);
+      H[1][c] = fma(R(kSqrt3), G[1][c], even);
+      H[2][c] = fma(R(-kSqrt3), G[1][c], even);
+    }
+    // velocity -> (cx, cy): 0 -> 0, +1 -> 1, -1 -> 2
+    T[0] = H[0][0];
+    T[1] = H[1][0];
+    T[2] = H[0][1];
+    T[3] = H[2][0];
+    T[4] = H[0][2];
+    T[5] = H[1][1];
+    T[6] = H[2][1];
+    T[7] = H[2][2];
+    T[8] = H[1][2];
+  }
+};
+
+// D1Q3: T(0) = -z^2/sqrt2, T(+-1) = +-sqrt3 z^1 + sqrt2 z^2.
+template <typename R>
+struct NoiseTransform<kD1Q3, R> {
+  __device__ static __forceinline__ void apply(const R (&z)[2], R (&T)[3]) {
+    T[0] = R(-kInvSqrt2) * z[1];
+    const R even = R(kSqrt2) * z[1];
+    T[1] = fma(R(kSqrt3), z[0], even);
+    T[2] = fma(R(-kSqrt3), z[0], even);
+  }
+};
+
+// Full moment matrix of the D2Q9 product basis, for export and checks.
+__host__ __device__ constexpr double d1q3_mu(int p, int v) {
+  return p == 0 ? 1.0 : (p == 1 ? kSqrt3 * v : (v == 0 ? -kInvSqrt2 : kSqrt2));
+}
+
+}  // namespace lbfd

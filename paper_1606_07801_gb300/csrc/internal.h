@@ -1,0 +1,64 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define LBFD_MAX_MODES_DEV 16
+
+namespace lbfd {
+
+// Per-launch arguments of the step kernel (passed by value).
+struct StepArgs {
+  int32_t Lx, Ly, Lz;
+  int64_t N;           // sites
+  double omega;        // 1 - 1/tau (what is left of the non-equilibrium part)
+  double inv_tau;      // 1/tau
+  double noise_var;    // (2 tau - 1)/tau^2: noise variance per unit density
+  double rho_eq;       // density of the global-noise variant
+  int32_t noise_mode;  // kNoiseLocal / kNoiseGlobal / kNoiseOff
+  int32_t noise_dist;  // kGaussian / kUniform
+  uint32_t key0, key1; // Philox key (seed)
+  uint32_t lattice_id; // Philox counter word 1
+  uint32_t t_lo, t_hi8; // Philox counter words 2 and 3 (t_hi * 8; the call index is OR-ed in)
+};
+
+// One step of eq. LB from src to dst (pull streaming, two buffers).
+cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
+                        cudaStream_t stream);
+
+// f_i = w_i rho(x), rho = rho_mean (+ amp sin(2 pi k.x / L)).
+cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
+                        double amp, const int32_t *k, cudaStream_t stream);
+
+// rho(x) = sum_i f_i, j_a(x) = sum_i f_i v_ia (FP64 outputs; j may be null).
+cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz, double *rho,
+                           double *j, cudaStream_t stream);
+
+// Noise variates of sites [site0, site0 + nsites) at step t into z[site][moment] (FP64).
+cudaError_t launch_noise_draw(int precision, int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id,
+                              uint32_t t_lo, uint32_t t_hi8, int64_t site0, int64_t nsites, int nmom, double *z,
+                              cudaStream_t stream);
+
+// Deterministic FP64 reductions.
+//   Stage 1 writes per-block partials of `nq` quantities to partials[block][nq];
+//   stage 2 sums them in block order and adds the totals into acc[nq] (or
+//   stores them when accumulate == 0).
+constexpr int kReduceBlocks = 304;   // 2 x 152 SMs
+constexpr int kReduceThreads = 256;
+
+// Number of FP64 quantities the observable pass produces for a lattice and mode count.
+int obs_quantities(int Q, int n_modes);
+
+cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double *partials, double *out,
+                        cudaStream_t stream);
+
+cudaError_t launch_observables(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
+                               double rho_mean, int n_modes, const int32_t *modes /*device, n_modes*3*/,
+                               double *partials, double *acc, cudaStream_t stream);
+
+// Host copy of the moment matrix the kernels use, m[a*Q + i].
+int basis_table(int lattice, double *m);
+int lattice_table(int lattice, int *Q, int *D, int *v, double *w);
+
+}  // namespace lbfd

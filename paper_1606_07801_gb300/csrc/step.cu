@@ -1,0 +1,295 @@
+// The fused fluctuating lattice-Boltzmann step and its helpers.
+//
+// One thread updates one site x per step (Wagner & Strand, arXiv:1606.07801):
+//   pull    f_i <- f*_i(x - v_i, t)            (eq. LB, periodic, two buffers)
+//   density rho = sum_i f_i
+//   noise   sigma^2 = rho_n (2 tau - 1)/tau^2,  rho_n = max(rho, 0) (local,
+//           eq. xilocal; the clamp of Sec. IV) or rho^eq (global, eq. xiglobal)
+//           z^a, a = 1..Q-1, from Philox4x32-10 keyed by (seed, site, t)
+//   collide f*_i = (1 - 1/tau) f_i + w_i (rho/tau + sigma sum_{a>=1} m_i^a z^a)
+//           which is eq. collision with Lambda = 1/tau (eq. coll) written in
+//           f-space: M^{a*} = (1 - 1/tau) M^a + sigma z^a for a >= 1,
+//           M^{0*} = rho, back-transformed with n_i^a = m_i^a w_i
+//   store   f*_i(x) into the other buffer
+// Everything lives in registers; the populations are read and written once.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace lbfd {
+
+template <int LAT, typename R>
+__global__ void __launch_bounds__(256) k_step(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
+  using L = Lattice<LAT>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.Lx || y >= a.Ly) return;
+  // periodic neighbours
+  const int xm = (x == 0 ? a.Lx : x) - 1, xp = (x + 1 == a.Lx) ? 0 : x + 1;
+  const int ym = (y == 0 ? a.Ly : y) - 1, yp = (y + 1 == a.Ly) ? 0 : y + 1;
+  const int zm = (z == 0 ? a.Lz : z) - 1, zp = (z + 1 == a.Lz) ? 0 : z + 1;
+  const uint32_t Lx = static_cast<uint32_t>(a.Lx), Lxy = Lx * static_cast<uint32_t>(a.Ly);
+  const uint32_t s = static_cast<uint32_t>(x) + Lx * static_cast<uint32_t>(y) + Lxy * static_cast<uint32_t>(z);
+
+  // pull: population i arrives from x - v_i
+  R f[Q];
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int vx = L::v(i, 0), vy = L::v(i, 1), vz = L::v(i, 2);
+    const int xs = vx == 0 ? x : (vx > 0 ? xm : xp);
+    const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
+    const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
+    const uint32_t so = static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
+    f[i] = __ldg(src + static_cast<size_t>(i) * static_cast<size_t>(a.N) + so);
+  });
+
+  R rho = f[0];
+  static_for<Q - 1>([&](auto I) { rho += f[decltype(I)::value + 1]; });
+
+  R sigma = R(0);
+  R T[Q];
+  static_for<Q>([&](auto I) { T[decltype(I)::value] = R(0); });
+  if (a.noise_mode != kNoiseOff) {
+    const R rho_n = a.noise_mode == kNoiseLocal ? (rho > R(0) ? rho : R(0)) : static_cast<R>(a.rho_eq);
+    sigma = Math<R>::sqrt(rho_n * static_cast<R>(a.noise_var));
+    R zz[Q - 1];
+    draw_variates<R, Q - 1>(zz, s, a.lattice_id, a.t_lo, a.t_hi8, a.key0, a.key1, a.noise_dist);
+    NoiseTransform<LAT, R>::apply(zz, T);
+  }
+
+  const R omega = static_cast<R>(a.omega);
+  const R relaxed = rho * static_cast<R>(a.inv_tau);
+  static_for<Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const R eq_and_noise = fma(sigma, T[i], relaxed);
+    dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = fma(omega, f[i], static_cast<R>(L::w(i)) * eq_and_noise);
+  });
+}
+
+static void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block) {
+  int bx = 256;
+  while (bx > 32 && bx / 2 >= Lx) bx /= 2;
+  int by = 256 / bx;
+  while (by > 1 && by / 2 >= Ly) by /= 2;
+  block = dim3(bx, by, 1);
+  grid = dim3((Lx + bx - 1) / bx, (Ly + by - 1) / by, Lz);
+}
+
+template <int LAT, typename R>
+static cudaError_t step_t(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
+  dim3 grid, block;
+  step_shape(a.Lx, a.Ly, a.Lz, grid, block);
+  k_step<LAT, R><<<grid, block, 0, stream>>>(static_cast<const R *>(src), static_cast<R *>(dst), a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
+                        cudaStream_t stream) {
+  const bool f64 = precision == 1;
+  switch (lattice) {
+    case kD1Q3: return f64 ? step_t<kD1Q3, double>(src, dst, a, stream) : step_t<kD1Q3, float>(src, dst, a, stream);
+    case kD2Q9: return f64 ? step_t<kD2Q9, double>(src, dst, a, stream) : step_t<kD2Q9, float>(src, dst, a, stream);
+    case kD3Q19:
+      return f64 ? step_t<kD3Q19, double>(src, dst, a, stream) : step_t<kD3Q19, float>(src, dst, a, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Initial state f_i = w_i rho(x) (local equilibrium, eq. f0def)
+// ---------------------------------------------------------------------------
+template <int LAT, typename R>
+__global__ void k_init(R *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, int32_t kx,
+                       int32_t ky, int32_t kz) {
+  using L = Lattice<LAT>;
+  const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < N;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t x = s % Lx, y = (s / Lx) % Ly, z = s / (static_cast<int64_t>(Lx) * Ly);
+    double rho = rho_mean;
+    if (amp != 0.0) {
+      // phase / (2 pi) reduced exactly with integers before the sine
+      const int64_t px = ((static_cast<int64_t>(kx) * x) % Lx + Lx) % Lx;
+      const int64_t py = ((static_cast<int64_t>(ky) * y) % Ly + Ly) % Ly;
+      const int64_t pz = ((static_cast<int64_t>(kz) * z) % Lz + Lz) % Lz;
+      const double frac = double(px) / Lx + double(py) / Ly + double(pz) / Lz;
+      rho += amp * sinpi(2.0 * frac);
+    }
+    static_for<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      f[i * N + s] = static_cast<R>(L::w(i) * rho);
+    });
+  }
+}
+
+template <int LAT, typename R>
+static cudaError_t init_t(void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, const int32_t *k,
+                          cudaStream_t stream) {
+  const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
+  const int64_t blocks = (N + 255) / 256;
+  const int grid = static_cast<int>(blocks < 152 * 64 ? blocks : 152 * 64);
+  k_init<LAT, R><<<grid, 256, 0, stream>>>(static_cast<R *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
+                        double amp, const int32_t *k, cudaStream_t stream) {
+  const bool f64 = precision == 1;
+  switch (lattice) {
+    case kD1Q3:
+      return f64 ? init_t<kD1Q3, double>(f, Lx, Ly, Lz, rho_mean, amp, k, stream)
+                 : init_t<kD1Q3, float>(f, Lx, Ly, Lz, rho_mean, amp, k, stream);
+    case kD2Q9:
+      return f64 ? init_t<kD2Q9, double>(f, Lx, Ly, Lz, rho_mean, amp, k, stream)
+                 : init_t<kD2Q9, float>(f, Lx, Ly, Lz, rho_mean, amp, k, stream);
+    case kD3Q19:
+      return f64 ? init_t<kD3Q19, double>(f, Lx, Ly, Lz, rho_mean, amp, k, stream)
+                 : init_t<kD3Q19, float>(f, Lx, Ly, Lz, rho_mean, amp, k, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Density and flux (FP64 outputs)
+// ---------------------------------------------------------------------------
+template <int LAT, typename R>
+__global__ void k_moments(const R *__restrict__ f, int64_t N, double *__restrict__ rho, double *__restrict__ j) {
+  using L = Lattice<LAT>;
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < N;
+       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    static_for<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const double fi = static_cast<double>(f[i * N + s]);
+      r += fi;
+      if constexpr (L::v(i, 0) != 0) jx += L::v(i, 0) * fi;
+      if constexpr (L::v(i, 1) != 0) jy += L::v(i, 1) * fi;
+      if constexpr (L::v(i, 2) != 0) jz += L::v(i, 2) * fi;
+    });
+    rho[s] = r;
+    if (j) {
+      j[s] = jx;
+      if (L::D > 1) j[N + s] = jy;
+      if (L::D > 2) j[2 * N + s] = jz;
+    }
+  }
+}
+
+template <int LAT, typename R>
+static cudaError_t moments_t(const void *f, int64_t N, double *rho, double *j, cudaStream_t stream) {
+  const int64_t blocks = (N + 255) / 256;
+  const int grid = static_cast<int>(blocks < 152 * 32 ? blocks : 152 * 32);
+  k_moments<LAT, R><<<grid, 256, 0, stream>>>(static_cast<const R *>(f), N, rho, j);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz, double *rho,
+                           double *j, cudaStream_t stream) {
+  const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
+  const bool f64 = precision == 1;
+  switch (lattice) {
+    case kD1Q3: return f64 ? moments_t<kD1Q3, double>(f, N, rho, j, stream) : moments_t<kD1Q3, float>(f, N, rho, j, stream);
+    case kD2Q9: return f64 ? moments_t<kD2Q9, double>(f, N, rho, j, stream) : moments_t<kD2Q9, float>(f, N, rho, j, stream);
+    case kD3Q19:
+      return f64 ? moments_t<kD3Q19, double>(f, N, rho, j, stream) : moments_t<kD3Q19, float>(f, N, rho, j, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Noise probe: the variates the step kernel draws, for checks of the RNG
+// ---------------------------------------------------------------------------
+template <typename R, int NMOM>
+__global__ void k_noise_draw(int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id, uint32_t t_lo, uint32_t t_hi8,
+                             int64_t site0, int64_t nsites, double *__restrict__ out) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nsites;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    R z[NMOM];
+    draw_variates<R, NMOM>(z, static_cast<uint32_t>(site0 + k), lattice_id, t_lo, t_hi8, key0, key1, dist);
+#pragma unroll
+    for (int a = 0; a < NMOM; ++a) out[k * NMOM + a] = static_cast<double>(z[a]);
+  }
+}
+
+template <typename R, int NMOM>
+static cudaError_t noise_t(int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id, uint32_t t_lo, uint32_t t_hi8,
+                           int64_t site0, int64_t nsites, double *z, cudaStream_t stream) {
+  const int64_t blocks = (nsites + 255) / 256;
+  const int grid = static_cast<int>(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
+  k_noise_draw<R, NMOM><<<grid, 256, 0, stream>>>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t noise_p(int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id, uint32_t t_lo, uint32_t t_hi8,
+                           int64_t site0, int64_t nsites, int nmom, double *z, cudaStream_t stream) {
+  switch (nmom) {
+    case 2: return noise_t<R, 2>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
+    case 4: return noise_t<R, 4>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
+    case 8: return noise_t<R, 8>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
+    case 18: return noise_t<R, 18>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_noise_draw(int precision, int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id,
+                              uint32_t t_lo, uint32_t t_hi8, int64_t site0, int64_t nsites, int nmom, double *z,
+                              cudaStream_t stream) {
+  return precision == 1 ? noise_p<double>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, nmom, z, stream)
+                        : noise_p<float>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, nmom, z, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Host copies of the tables the kernels are compiled with
+// ---------------------------------------------------------------------------
+template <int LAT>
+static void tables_t(int *Q, int *D, int *v, double *w, double *m) {
+  using L = Lattice<LAT>;
+  if (Q) *Q = L::Q;
+  if (D) *D = L::D;
+  for (int i = 0; i < L::Q; ++i) {
+    if (v)
+      for (int a = 0; a < 3; ++a) v[3 * i + a] = L::v(i, a);
+    if (w) w[i] = L::w(i);
+  }
+  if (m) {
+    constexpr BasisTable<L::Q> B = make_basis<LAT>();
+    for (int a = 0; a < L::Q; ++a)
+      for (int i = 0; i < L::Q; ++i) m[a * L::Q + i] = B.m[a][i];
+  }
+}
+
+int lattice_table(int lattice, int *Q, int *D, int *v, double *w) {
+  switch (lattice) {
+    case kD1Q3: tables_t<kD1Q3>(Q, D, v, w, nullptr); return 0;
+    case kD2Q9: tables_t<kD2Q9>(Q, D, v, w, nullptr); return 0;
+    case kD3Q19: tables_t<kD3Q19>(Q, D, v, w, nullptr); return 0;
+  }
+  return -1;
+}
+
+int basis_table(int lattice, double *m) {
+  switch (lattice) {
+    case kD1Q3: {
+      // the factorised kernel path uses mu^p(v) directly
+      const int vs[3] = {0, 1, -1};
+      for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 3; ++i) m[a * 3 + i] = d1q3_mu(a, vs[i]);
+      return 0;
+    }
+    case kD2Q9: {
+      using L = Lattice<kD2Q9>;
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+          for (int i = 0; i < 9; ++i) m[(3 * p + q) * 9 + i] = d1q3_mu(p, L::v(i, 0)) * d1q3_mu(q, L::v(i, 1));
+      return 0;
+    }
+    case kD3Q19: tables_t<kD3Q19>(nullptr, nullptr, nullptr, nullptr, m); return 0;
+  }
+  return -1;
+}
+
+}  // namespace lbfd

@@ -1,0 +1,271 @@
+"""ctypes binding of the C ABI in ``include/lbfd.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``liblbfd.so``.  Loading fails loudly when the library has not been
+built; there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+c_int32, c_int64, c_uint32, c_uint64, c_double, c_void_p = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                                            ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p)
+P = ctypes.POINTER
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+D1Q3, D2Q9, D3Q19 = 0, 1, 2
+F32, F64 = 0, 1
+NOISE_LOCAL, NOISE_GLOBAL, NOISE_OFF = 0, 1, 2
+GAUSSIAN, UNIFORM = 0, 1
+INIT_UNIFORM, INIT_SINE, INIT_NONE = 0, 1, 2
+MAX_Q, MAX_MODES = 19, 16
+
+Q_OF = {D1Q3: 3, D2Q9: 9, D3Q19: 19}
+D_OF = {D1Q3: 1, D2Q9: 2, D3Q19: 3}
+
+
+class Options(ctypes.Structure):
+    """Mirror of ``lbfd_options``."""
+    _fields_ = [
+        ("lattice", c_int32), ("precision", c_int32), ("noise_mode", c_int32), ("noise_dist", c_int32),
+        ("init", c_int32), ("device", c_int32), ("dims", c_int64 * 3), ("tau", c_double),
+        ("rho_mean", c_double), ("sine_amp", c_double), ("sine_k", c_int32 * 3), ("lattice_id", c_uint32),
+        ("seed", c_uint64), ("stream", c_void_p), ("f_dev", c_void_p * 2), ("n_modes", c_int32),
+        ("modes", (c_int32 * 3) * MAX_MODES), ("reserved", c_int32 * 8),
+    ]
+
+
+class Obs(ctypes.Structure):
+    """Mirror of ``lbfd_obs``."""
+    _fields_ = [
+        ("t", c_int64), ("n_samples", c_int64), ("Q", c_int32), ("n_modes", c_int32), ("sum_rho", c_double),
+        ("sum_rho2", c_double), ("sum_f", c_double * MAX_Q), ("sum_ff", c_double * (MAX_Q * MAX_Q)),
+        ("sum_sk", c_double * MAX_MODES),
+    ]
+
+
+class LbfdError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+# name -> (restype, argtypes); every function declared in include/lbfd.h
+SIGNATURES = {
+    "lbfd_options_init": (c_int32, [P(Options)]),
+    "lbfd_create": (c_int32, [P(c_void_p), c_int32, P(c_int64), c_double, c_double, c_uint64]),
+    "lbfd_create_ex": (c_int32, [P(c_void_p), P(Options)]),
+    "lbfd_destroy": (c_int32, [c_void_p]),
+    "lbfd_step": (c_int32, [c_void_p, c_int64]),
+    "lbfd_sync": (c_int32, [c_void_p]),
+    "lbfd_get_t": (c_int32, [c_void_p, P(c_int64)]),
+    "lbfd_set_t": (c_int32, [c_void_p, c_int64]),
+    "lbfd_get_f": (c_int32, [c_void_p, c_void_p]),
+    "lbfd_set_f": (c_int32, [c_void_p, c_void_p]),
+    "lbfd_get_f_raw": (c_int32, [c_void_p, c_void_p]),
+    "lbfd_set_f_raw": (c_int32, [c_void_p, c_void_p]),
+    "lbfd_moments": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "lbfd_moments_device": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "lbfd_mass": (c_int32, [c_void_p, P(c_double)]),
+    "lbfd_sample": (c_int32, [c_void_p]),
+    "lbfd_reset_obs": (c_int32, [c_void_p]),
+    "lbfd_observables": (c_int32, [c_void_p, P(Obs)]),
+    "lbfd_query": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int64), P(c_int32)]),
+    "lbfd_state_device": (c_int32, [c_void_p, P(c_void_p), P(c_void_p)]),
+    "lbfd_lattice_tables": (c_int32, [c_int32, P(c_int32), c_void_p, c_void_p, c_void_p]),
+    "lbfd_noise_draw": (c_int32, [c_int32, c_int32, c_uint64, c_uint32, c_uint64, c_int64, c_int64, c_int32,
+                                  c_void_p]),
+    "lbfd_last_error": (ctypes.c_char_p, []),
+    "lbfd_kernel_launches": (c_int64, []),
+    "lbfd_struct_sizes": (c_int32, [P(c_int64), P(c_int64)]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load ``liblbfd.so`` (building it first if asked and needed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing and not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"the CUDA library {_build.LIB} is missing: run build() first")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def last_error() -> str:
+    return load().lbfd_last_error().decode()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != OK:
+        raise LbfdError(rc, where, last_error())
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ---- thin wrappers with the C names ------------------------------------------
+
+def lbfd_options_init() -> Options:
+    o = Options()
+    _check(load().lbfd_options_init(ctypes.byref(o)), "lbfd_options_init")
+    return o
+
+
+def lbfd_create(lattice: int, dims, tau: float, rho_mean: float, seed: int) -> int:
+    h = c_void_p()
+    d = (c_int64 * 3)(*[int(x) for x in dims] + [1] * (3 - len(dims)))
+    _check(load().lbfd_create(ctypes.byref(h), lattice, d, tau, rho_mean, seed), "lbfd_create")
+    return h.value
+
+
+def lbfd_create_ex(opt: Options) -> int:
+    h = c_void_p()
+    _check(load().lbfd_create_ex(ctypes.byref(h), ctypes.byref(opt)), "lbfd_create_ex")
+    return h.value
+
+
+def lbfd_destroy(h: int) -> None:
+    _check(load().lbfd_destroy(h), "lbfd_destroy")
+
+
+def lbfd_step(h: int, n: int) -> None:
+    _check(load().lbfd_step(h, n), "lbfd_step")
+
+
+def lbfd_sync(h: int) -> None:
+    _check(load().lbfd_sync(h), "lbfd_sync")
+
+
+def lbfd_get_t(h: int) -> int:
+    t = c_int64()
+    _check(load().lbfd_get_t(h, ctypes.byref(t)), "lbfd_get_t")
+    return t.value
+
+
+def lbfd_set_t(h: int, t: int) -> None:
+    _check(load().lbfd_set_t(h, t), "lbfd_set_t")
+
+
+def lbfd_query(h: int):
+    Q, D, N, vb = c_int32(), c_int32(), c_int64(), c_int32()
+    _check(load().lbfd_query(h, ctypes.byref(Q), ctypes.byref(D), ctypes.byref(N), ctypes.byref(vb)), "lbfd_query")
+    return Q.value, D.value, N.value, vb.value
+
+
+def lbfd_get_f(h: int, out: np.ndarray | None = None) -> np.ndarray:
+    Q, D, N, _ = lbfd_query(h)
+    if out is None:
+        out = np.empty((Q, N), dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == Q * N
+    _check(load().lbfd_get_f(h, _ptr(out)), "lbfd_get_f")
+    return out
+
+
+def lbfd_set_f(h: int, f: np.ndarray) -> None:
+    Q, D, N, _ = lbfd_query(h)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    if f.size != Q * N:
+        raise ValueError(f"f must hold Q*N = {Q * N} values")
+    _check(load().lbfd_set_f(h, _ptr(f)), "lbfd_set_f")
+
+
+def lbfd_get_f_raw(h: int, host_ptr: int) -> None:
+    _check(load().lbfd_get_f_raw(h, host_ptr), "lbfd_get_f_raw")
+
+
+def lbfd_set_f_raw(h: int, host_ptr: int) -> None:
+    _check(load().lbfd_set_f_raw(h, host_ptr), "lbfd_set_f_raw")
+
+
+def lbfd_moments(h: int, with_flux: bool = False):
+    Q, D, N, _ = lbfd_query(h)
+    rho = np.empty(N, dtype=np.float64)
+    j = np.empty((D, N), dtype=np.float64) if with_flux else None
+    _check(load().lbfd_moments(h, _ptr(rho), _ptr(j) if j is not None else None), "lbfd_moments")
+    return (rho, j) if with_flux else rho
+
+
+def lbfd_moments_device(h: int, rho_dev_ptr: int, j_dev_ptr: int | None = None) -> None:
+    _check(load().lbfd_moments_device(h, rho_dev_ptr, j_dev_ptr), "lbfd_moments_device")
+
+
+def lbfd_mass(h: int) -> float:
+    m = c_double()
+    _check(load().lbfd_mass(h, ctypes.byref(m)), "lbfd_mass")
+    return m.value
+
+
+def lbfd_sample(h: int) -> None:
+    _check(load().lbfd_sample(h), "lbfd_sample")
+
+
+def lbfd_reset_obs(h: int) -> None:
+    _check(load().lbfd_reset_obs(h), "lbfd_reset_obs")
+
+
+def lbfd_observables(h: int) -> dict:
+    o = Obs()
+    _check(load().lbfd_observables(h, ctypes.byref(o)), "lbfd_observables")
+    Q, K = o.Q, o.n_modes
+    return {
+        "t": o.t, "n_samples": o.n_samples, "Q": Q, "n_modes": K, "sum_rho": o.sum_rho, "sum_rho2": o.sum_rho2,
+        "sum_f": np.array(o.sum_f[:Q]), "sum_ff": np.array(o.sum_ff[:Q * Q]).reshape(Q, Q),
+        "sum_sk": np.array(o.sum_sk[:K]),
+    }
+
+
+def lbfd_state_device(h: int):
+    f, s = c_void_p(), c_void_p()
+    _check(load().lbfd_state_device(h, ctypes.byref(f), ctypes.byref(s)), "lbfd_state_device")
+    return f.value, s.value
+
+
+def lbfd_lattice_tables(lattice: int):
+    """(v[Q,3], w[Q], m[Q,Q]) as compiled into the kernels."""
+    Q = c_int32()
+    v = np.zeros(3 * MAX_Q, dtype=np.int32)
+    w = np.zeros(MAX_Q)
+    m = np.zeros(MAX_Q * MAX_Q)
+    _check(load().lbfd_lattice_tables(lattice, ctypes.byref(Q), _ptr(v), _ptr(w), _ptr(m)), "lbfd_lattice_tables")
+    q = Q.value
+    return v[:3 * q].reshape(q, 3).astype(np.int64), w[:q].copy(), m[:q * q].reshape(q, q).copy()
+
+
+def lbfd_noise_draw(precision: int, dist: int, seed: int, lattice_id: int, t: int, site0: int, nsites: int,
+                    nmom: int) -> np.ndarray:
+    z = np.empty((nsites, nmom), dtype=np.float64)
+    _check(load().lbfd_noise_draw(precision, dist, seed, lattice_id, t, site0, nsites, nmom, _ptr(z)),
+           "lbfd_noise_draw")
+    return z
+
+
+def lbfd_kernel_launches() -> int:
+    return int(load().lbfd_kernel_launches())
+
+
+def lbfd_struct_sizes():
+    a, b = c_int64(), c_int64()
+    _check(load().lbfd_struct_sizes(ctypes.byref(a), ctypes.byref(b)), "lbfd_struct_sizes")
+    return a.value, b.value

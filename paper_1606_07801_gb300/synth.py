@@ -1,0 +1,59 @@
+"""Seeded synthetic inputs for tests and the benchmark.
+
+Nothing here computes any part of the method: these are random arrays,
+density fields and workload descriptions with the shapes and value ranges of
+the paper's experiments (periodic lattices at a given mean density, single
+Fourier modes, ensembles of lattices of mixed size).  Both the CUDA path and
+the oracle consume them.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.SeedSequence(int(seed)))
+
+
+def random_populations(Q: int, N: int, rho_mean: float, spread: float, seed: int,
+                       dtype=np.float64) -> np.ndarray:
+    """[Q, N] values rho_mean/Q * (1 + spread * U(-1, 1)): a positive,
+    non-equilibrium state with mean density about rho_mean."""
+    g = rng(seed)
+    if dtype == np.float64:
+        return (rho_mean / Q) * (1.0 + spread * g.uniform(-1.0, 1.0, size=(Q, N)))
+    out = g.random(size=(Q, N), dtype=np.float32)
+    out *= np.float32(2.0 * spread)
+    out += np.float32(1.0 - spread)
+    out *= np.float32(rho_mean / Q)
+    return out
+
+
+def density_sine(dims, k, amp: float, rho_mean: float) -> np.ndarray:
+    """rho(x) = rho_mean + amp * sin(2 pi (kx x/Lx + ky y/Ly + kz z/Lz)), site order x fastest."""
+    d = [int(v) for v in dims] + [1] * (3 - len(dims))
+    kk = [int(v) for v in k] + [0] * (3 - len(k))
+    z, y, x = np.meshgrid(np.arange(d[2]), np.arange(d[1]), np.arange(d[0]), indexing="ij")
+    frac = (kk[0] * x % d[0]) / d[0] + (kk[1] * y % d[1]) / d[1] + (kk[2] * z % d[2]) / d[2]
+    return (rho_mean + amp * np.sin(2 * np.pi * frac)).ravel()
+
+
+def density_noise(N: int, rho_mean: float, sd: float, seed: int) -> np.ndarray:
+    """Gaussian density field around rho_mean."""
+    return rho_mean + sd * rng(seed).normal(size=N)
+
+
+def ensemble(n: int, side_lo: int = 32, side_hi: int = 512, rho_lo: float = 0.5, rho_hi: float = 200.0,
+             tau_lo: float = 0.6, tau_hi: float = 1.5, seed: int = 12345):
+    """n D2Q9 lattices: sides drawn independently log-uniform in [side_lo, side_hi]
+    (rounded), mean density and tau uniform in their ranges, distinct seeds."""
+    g = rng(seed)
+    lx = np.rint(np.exp(g.uniform(math.log(side_lo), math.log(side_hi), n))).astype(np.int64)
+    ly = np.rint(np.exp(g.uniform(math.log(side_lo), math.log(side_hi), n))).astype(np.int64)
+    rho = g.uniform(rho_lo, rho_hi, n)
+    tau = g.uniform(tau_lo, tau_hi, n)
+    seeds = (int(seed) * 1000003 + np.arange(n)).astype(np.uint64)
+    return [dict(dims=(int(lx[i]), int(ly[i])), rho_mean=float(rho[i]), tau=float(tau[i]), seed=int(seeds[i]))
+            for i in range(n)]

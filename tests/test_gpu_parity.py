@@ -1,0 +1,206 @@
+"""Parity of the CUDA path with the FP64 oracle, element by element, on the
+same seeded inputs and the same Philox noise stream.
+
+Tolerances (max |f_gpu - f_oracle| after the stated number of steps):
+  FP64 arithmetic: 1e-12 * rho_mean
+  FP32 arithmetic: 2e-5  * rho_mean
+Lattices span several thread blocks and end in ragged tails in x and y.
+"""
+import numpy as np
+import pytest
+
+import paper_1606_07801_gb300 as lb
+from paper_1606_07801_gb300 import abi, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lb.F64: 1e-12, lb.F32: 2e-5}
+
+
+def _gpu_run(lat, dims, f0, nsteps, tau, precision, mode=lb.NOISE_LOCAL, dist=lb.GAUSSIAN, rho_mean=1.0, seed=1,
+             lattice_id=0, t0=0, **kw):
+    with lb.Simulation(lat, dims, tau, rho_mean, seed, precision=precision, noise_mode=mode, noise_dist=dist,
+                       init=lb.INIT_NONE, lattice_id=lattice_id, **kw) as s:
+        s.set_f(f0)
+        s.t = t0
+        s.step(nsteps)
+        return s.get_f()
+
+
+def _oracle_run(orc, lat, dims, f0, nsteps, tau, mode=lb.NOISE_LOCAL, dist=lb.GAUSSIAN, rho_mean=1.0, seed=1,
+                lattice_id=0, t0=0):
+    return orc.run(lat, dims, f0, nsteps, tau, mode, dist, rho_eq=rho_mean, seed=seed, lattice_id=lattice_id, t0=t0)
+
+
+CASES = [
+    # lattice, dims, tau, rho_mean
+    (lb.D1Q3, (1000,), 1.0, 10.0),
+    (lb.D2Q9, (67, 45), 0.8, 100.0),
+    (lb.D3Q19, (19, 13, 11), 1.0, 50.0),
+]
+
+
+@pytest.mark.parametrize("precision", [lb.F64, lb.F32])
+@pytest.mark.parametrize("lat,dims,tau,rho", CASES)
+def test_parity_1000_steps_local_gaussian(orc, lat, dims, tau, rho, precision):
+    Q, N = lb.Q_OF[lat], int(np.prod(dims))
+    f0 = synth.random_populations(Q, N, rho, 0.3, seed=11 + lat)
+    g = _gpu_run(lat, dims, f0, 1000, tau, precision, rho_mean=rho, seed=1)
+    o = _oracle_run(orc, lat, dims, f0, 1000, tau, rho_mean=rho, seed=1)
+    err = np.max(np.abs(g - o))
+    assert err <= TOL[precision] * rho, err
+    # the run did move far from its start
+    assert np.max(np.abs(o - f0)) > 0.1 * rho / Q
+
+
+@pytest.mark.parametrize("precision", [lb.F64, lb.F32])
+@pytest.mark.parametrize("mode,dist", [(lb.NOISE_GLOBAL, lb.GAUSSIAN), (lb.NOISE_OFF, lb.GAUSSIAN),
+                                       (lb.NOISE_LOCAL, lb.UNIFORM), (lb.NOISE_GLOBAL, lb.UNIFORM)])
+@pytest.mark.parametrize("lat,dims,tau,rho", [(lb.D2Q9, (40, 33), 0.6, 20.0), (lb.D3Q19, (9, 10, 7), 1.4, 30.0),
+                                              (lb.D1Q3, (300,), 0.75, 5.0)])
+def test_parity_noise_variants(orc, lat, dims, tau, rho, mode, dist, precision):
+    Q, N = lb.Q_OF[lat], int(np.prod(dims))
+    f0 = synth.random_populations(Q, N, rho, 0.2, seed=5)
+    g = _gpu_run(lat, dims, f0, 300, tau, precision, mode, dist, rho_mean=rho, seed=77, lattice_id=3)
+    o = _oracle_run(orc, lat, dims, f0, 300, tau, mode, dist, rho_mean=rho, seed=77, lattice_id=3)
+    assert np.max(np.abs(g - o)) <= TOL[precision] * rho
+
+
+@pytest.mark.parametrize("lat,dims", [
+    (lb.D1Q3, (1,)), (lb.D1Q3, (2,)), (lb.D2Q9, (1, 1)), (lb.D2Q9, (2, 1)), (lb.D2Q9, (1, 2)), (lb.D2Q9, (2, 2)),
+    (lb.D2Q9, (3, 300)), (lb.D2Q9, (513, 2)), (lb.D3Q19, (1, 1, 1)), (lb.D3Q19, (2, 2, 2)), (lb.D3Q19, (1, 5, 2)),
+    (lb.D3Q19, (33, 1, 3)),
+])
+def test_degenerate_sizes(orc, lat, dims):
+    """Sides of 1 and 2 (the periodic wrap aliases a site's neighbours) and
+    thin lattices."""
+    Q, N = lb.Q_OF[lat], int(np.prod(dims))
+    f0 = synth.random_populations(Q, N, 8.0, 0.5, seed=N)
+    g = _gpu_run(lat, dims, f0, 50, 0.9, lb.F64, rho_mean=8.0, seed=3)
+    o = _oracle_run(orc, lat, dims, f0, 50, 0.9, rho_mean=8.0, seed=3)
+    assert np.max(np.abs(g - o)) <= 1e-12 * 8.0
+
+
+@pytest.mark.parametrize("precision", [lb.F64, lb.F32])
+def test_zero_density_stays_zero(precision):
+    with lb.Simulation(lb.D2Q9, (17, 9), 0.8, 0.0, 5, precision=precision) as s:
+        s.step(20)
+        assert np.all(s.get_f() == 0.0)
+
+
+def test_low_density_local_noise(orc):
+    """rho = 0.5 with the zero-density clamp: FP64 follows the oracle pathwise;
+    in FP32 the kink of sqrt(max(rho, 0)) lets a few sites drift, so FP32 is
+    judged by the fraction of sites beyond tolerance and by mass."""
+    lat, dims, rho = lb.D2Q9, (64, 48), 0.5
+    Q, N = 9, 64 * 48
+    f0 = synth.random_populations(Q, N, rho, 0.3, seed=99)
+    o = _oracle_run(orc, lat, dims, f0, 200, 0.8, rho_mean=rho, seed=21)
+    assert (o.sum(0) < 0).mean() > 0.01  # the clamp is exercised
+    g64 = _gpu_run(lat, dims, f0, 200, 0.8, lb.F64, rho_mean=rho, seed=21)
+    assert np.max(np.abs(g64 - o)) <= 1e-12 * rho
+    g32 = _gpu_run(lat, dims, f0, 200, 0.8, lb.F32, rho_mean=rho, seed=21)
+    bad = np.any(np.abs(g32 - o) > 2e-5 * rho, axis=0).mean()
+    assert bad < 0.01
+    assert abs(g32.sum() - o.sum()) < 1e-4 * N * rho
+
+
+@pytest.mark.parametrize("precision,tol", [(lb.F64, 1e-14), (lb.F32, 3e-6)])
+@pytest.mark.parametrize("dist", [lb.GAUSSIAN, lb.UNIFORM])
+@pytest.mark.parametrize("nmom", [2, 8, 18])
+def test_noise_variates_match_oracle(orc, precision, tol, dist, nmom):
+    seed, lid, t = 0x123456789ABCDEF, 7, (5 << 32) + 99
+    z = abi.lbfd_noise_draw(precision, dist, seed, lid, t, 1000, 300, nmom)
+    zo = np.array([orc.site_noise(seed, lid, s, t, nmom, dist) for s in range(1000, 1300)])
+    assert np.max(np.abs(z - zo)) <= tol * max(1.0, np.max(np.abs(zo)))
+
+
+@pytest.mark.parametrize("precision", [lb.F64, lb.F32])
+def test_split_run_bit_identical(precision):
+    f0 = synth.random_populations(19, 12 * 7 * 5, 40.0, 0.2, seed=8)
+    whole = _gpu_run(lb.D3Q19, (12, 7, 5), f0, 9, 0.7, precision, rho_mean=40.0, seed=5)
+    with lb.Simulation(lb.D3Q19, (12, 7, 5), 0.7, 40.0, 5, precision=precision, init=lb.INIT_NONE) as s:
+        s.set_f(f0)
+        s.step(4)
+        mid = s.get_f()
+    with lb.Simulation(lb.D3Q19, (12, 7, 5), 0.7, 40.0, 5, precision=precision, init=lb.INIT_NONE) as s:
+        s.set_f(mid)
+        s.t = 4
+        s.step(5)
+        assert np.array_equal(s.get_f(), whole)
+
+
+def test_seed_and_lattice_id_select_streams():
+    f0 = synth.random_populations(9, 30 * 20, 10.0, 0.1, seed=1)
+    a = _gpu_run(lb.D2Q9, (30, 20), f0, 5, 0.8, lb.F64, rho_mean=10.0, seed=1, lattice_id=0)
+    b = _gpu_run(lb.D2Q9, (30, 20), f0, 5, 0.8, lb.F64, rho_mean=10.0, seed=2, lattice_id=0)
+    c = _gpu_run(lb.D2Q9, (30, 20), f0, 5, 0.8, lb.F64, rho_mean=10.0, seed=1, lattice_id=1)
+    assert not np.allclose(a, b) and not np.allclose(a, c) and not np.allclose(b, c)
+
+
+@pytest.mark.parametrize("precision", [lb.F64, lb.F32])
+def test_init_matches_equilibrium(orc, precision):
+    dims, k = (96, 40), (2, 1)
+    rho = synth.density_sine(dims, k, 3.0, 20.0)
+    with lb.Simulation(lb.D2Q9, dims, 0.8, 20.0, 1, precision=precision, init=lb.INIT_SINE, sine_amp=3.0,
+                       sine_k=k) as s:
+        g = s.get_f()
+    o = orc.init_equilibrium(lb.D2Q9, rho)
+    assert np.max(np.abs(g - o)) <= (1e-14 if precision == lb.F64 else 1e-6) * 23.0
+    with lb.Simulation(lb.D3Q19, (5, 6, 7), 0.8, 20.0, 1, precision=precision) as s:
+        g = s.get_f()
+    o = orc.init_equilibrium(lb.D3Q19, np.full(210, 20.0))
+    assert np.max(np.abs(g - o)) <= 1e-6 * 20.0
+
+
+@pytest.mark.parametrize("lat,dims", [(lb.D1Q3, (77,)), (lb.D2Q9, (31, 17)), (lb.D3Q19, (7, 6, 5))])
+def test_moments_mass_and_observables(lat, dims):
+    Q, N = lb.Q_OF[lat], int(np.prod(dims))
+    modes = [(1, 0, 0), (2, 1, 0), (0, 1, 1), (3, 2, 1)][: 2 + (lat != lb.D1Q3)]
+    with lb.Simulation(lat, dims, 0.8, 30.0, 4, precision=lb.F64, modes=modes) as s:
+        s.step(13)
+        f = s.get_f()
+        rho, j = s.moments(with_flux=True)
+        v, w, m = abi.lbfd_lattice_tables(lat)
+        assert np.max(np.abs(rho - f.sum(0))) < 1e-12
+        assert np.max(np.abs(j - v[:, : lb.D_OF[lat]].T @ f)) < 1e-12
+        assert abs(s.mass() - f.sum()) < 1e-12 * f.sum()
+        s.sample()
+        s.step(3)
+        f2 = s.get_f()
+        s.sample()
+        ob = s.observables()
+    r1, r2 = f.sum(0), f2.sum(0)
+    assert ob["n_samples"] == 2 and ob["t"] == 16
+    assert abs(ob["sum_rho"] - (r1.sum() + r2.sum())) < 1e-12 * N * 60
+    assert abs(ob["sum_rho2"] - ((r1 ** 2).sum() + (r2 ** 2).sum())) < 1e-12 * ob["sum_rho2"]
+    assert np.max(np.abs(ob["sum_f"] - (f.sum(1) + f2.sum(1)))) < 1e-10
+    ff = f @ f.T + f2 @ f2.T
+    assert np.max(np.abs(ob["sum_ff"] - ff)) < 1e-12 * np.max(ff)
+    d3 = list(dims) + [1] * (3 - len(dims))
+    for mi, k in enumerate(modes):
+        sk = 0.0
+        for r in (r1, r2):
+            field = (r - 30.0).reshape(d3[2], d3[1], d3[0])
+            ft = np.fft.fftn(field)
+            sk += abs(ft[k[2] % d3[2], k[1] % d3[1], k[0] % d3[0]]) ** 2
+        assert abs(ob["sum_sk"][mi] - sk) < 1e-5 * max(sk, 1.0)
+
+
+def test_torch_buffers_and_stream_give_same_result():
+    import torch
+
+    f0 = synth.random_populations(9, 50 * 40, 10.0, 0.2, seed=2)
+    ref = _gpu_run(lb.D2Q9, (50, 40), f0, 25, 0.8, lb.F32, rho_mean=10.0, seed=6)
+    st = torch.cuda.Stream()
+    got = _gpu_run(lb.D2Q9, (50, 40), f0, 25, 0.8, lb.F32, rho_mean=10.0, seed=6, torch_buffers=True, stream=st)
+    assert np.array_equal(ref, got)
+
+
+def test_error_reporting_on_gpu():
+    with pytest.raises(abi.LbfdError):
+        abi.lbfd_noise_draw(lb.F32, lb.GAUSSIAN, 1, 0, 0, 0, 10, 5)
+    with lb.Simulation(lb.D2Q9, (8, 8), 0.8, 1.0, 1) as s:
+        with pytest.raises(abi.LbfdError) as e:
+            s.step(-3)
+        assert e.value.code == abi.EINVAL
