@@ -11,6 +11,13 @@
  * the global density rho^eq, eq. xilocal with the local density, which is
  * clamped at zero as in Sec. IV).  Streaming is periodic.
  *
+ * State convention.  The populations a caller sees (lbfd_get_f, lbfd_set_f,
+ * lbfd_moments, lbfd_observables) are the paper's f_i(x, t): the values
+ * that enter the collision at step t.  Internally the library keeps the
+ * post-collision values of the previous step, g_i(x) = f_i(x + v_i, t)
+ * (the pull scheme's natural state); the entry points above convert with an
+ * exact streaming shift through the spare buffer.
+ *
  * Every entry point returns LBFD_OK (0) or a negative status; none aborts the
  * process.  lbfd_last_error() returns a message for the calling thread's
  * last failure.  A handle may be used by one host thread at a time.
@@ -165,8 +172,8 @@ int lbfd_observables(lbfd_t h, lbfd_obs *obs);
 /* Static facts of a handle: Q, D, N (sites), bytes per stored value. */
 int lbfd_query(lbfd_t h, int32_t *Q, int32_t *D, int64_t *N, int32_t *value_bytes);
 
-/* Device buffer that holds the current state (valid until the next step),
- * and the stream the handle works on. */
+/* Device buffer holding the stored state g_i(x) = f_i(x + v_i, t) (layout
+ * [i][site]; valid until the next step), and the stream the handle works on. */
 int lbfd_state_device(lbfd_t h, void **f_dev, void **stream);
 
 /* Lattice tables the CUDA kernels use: velocities v[Q][3], weights w[Q] and

@@ -73,6 +73,22 @@ struct lbfd_sim {
   int32_t modes_host[LBFD_MAX_MODES][3] = {};
 };
 
+// The handle stores the post-collision populations g of the last step (the
+// pull kernel's natural state).  The paper's f(x, t) is g streamed once.
+// These helpers convert through the spare buffer, which the next step
+// overwrites anyway.
+static cudaError_t materialize_f(lbfd_sim *h) {
+  const lbfd_options &o = h->opt;
+  return launch_shift(o.lattice, h->elem, h->f[h->cur], h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                      int32_t(o.dims[2]), +1, h->stream);
+}
+
+static cudaError_t store_f_from_spare(lbfd_sim *h) {
+  const lbfd_options &o = h->opt;
+  return launch_shift(o.lattice, h->elem, h->f[h->cur ^ 1], h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                      int32_t(o.dims[2]), -1, h->stream);
+}
+
 extern "C" {
 
 int lbfd_options_init(lbfd_options *o) {
@@ -166,9 +182,11 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mass, sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream);
   if (e == cudaSuccess && opt->init != LBFD_INIT_NONE) {
+    // f(x, 0) into the spare buffer, then stored as g = f shifted back
     const double amp = opt->init == LBFD_INIT_SINE ? opt->sine_amp : 0.0;
-    e = launch_init(opt->lattice, opt->precision, h->f[0], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
+    e = launch_init(opt->lattice, opt->precision, h->f[1], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
                     int32_t(opt->dims[2]), opt->rho_mean, amp, opt->sine_k, h->stream);
+    if (e == cudaSuccess) e = store_f_from_spare(h);
   }
   if (e != cudaSuccess) {
     rc = cuda_fail("lbfd_create_ex", e);
@@ -257,7 +275,8 @@ int lbfd_set_t(lbfd_t h, int64_t t) {
 int lbfd_get_f_raw(lbfd_t h, void *f_host) {
   if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_get_f_raw: null argument");
   DeviceGuard g(h->device);
-  LBFD_CU(cudaMemcpyAsync(f_host, h->f[h->cur], size_t(h->Q) * h->N * h->elem, cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(materialize_f(h));
+  LBFD_CU(cudaMemcpyAsync(f_host, h->f[h->cur ^ 1], size_t(h->Q) * h->N * h->elem, cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   return LBFD_OK;
 }
@@ -265,7 +284,8 @@ int lbfd_get_f_raw(lbfd_t h, void *f_host) {
 int lbfd_set_f_raw(lbfd_t h, const void *f_host) {
   if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_set_f_raw: null argument");
   DeviceGuard g(h->device);
-  LBFD_CU(cudaMemcpyAsync(h->f[h->cur], f_host, size_t(h->Q) * h->N * h->elem, cudaMemcpyHostToDevice, h->stream));
+  LBFD_CU(cudaMemcpyAsync(h->f[h->cur ^ 1], f_host, size_t(h->Q) * h->N * h->elem, cudaMemcpyHostToDevice, h->stream));
+  LBFD_CU(store_f_from_spare(h));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   return LBFD_OK;
 }
@@ -302,7 +322,8 @@ int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev) {
   if (!h || !rho_dev) return fail(LBFD_EINVAL, "lbfd_moments_device: null argument");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
-  LBFD_CU(launch_moments(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+  LBFD_CU(materialize_f(h));
+  LBFD_CU(launch_moments(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
                          int32_t(o.dims[2]), rho_dev, j_dev, h->stream));
   return LBFD_OK;
 }
@@ -334,7 +355,8 @@ int lbfd_sample(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_sample: null handle");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
-  LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+  LBFD_CU(materialize_f(h));
+  LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
                              int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials, h->acc,
                              h->stream));
   h->n_samples += 1;

@@ -154,11 +154,19 @@ struct Philox {
   static constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 };
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return static_cast<uint32_t>((static_cast<uint64_t>(a) * b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = c.x * Philox::M0, hi0 = __umulhi(c.x, Philox::M0);
-    const uint32_t lo1 = c.z * Philox::M1, hi1 = __umulhi(c.z, Philox::M1);
+    const uint32_t lo0 = c.x * Philox::M0, hi0 = mulhi32(c.x, Philox::M0);
+    const uint32_t lo1 = c.z * Philox::M1, hi1 = mulhi32(c.z, Philox::M1);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += Philox::W0;
     k1 += Philox::W1;
@@ -168,30 +176,46 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Top 24 bits of a word as a cell-centred uniform on (0, 1); exact in FP32.
 template <typename R>
-__device__ __forceinline__ R unit24(uint32_t r) {
+__host__ __device__ __forceinline__ R unit24(uint32_t r) {
   return (static_cast<R>(r >> 8) + R(0.5)) * R(5.9604644775390625e-08);
 }
 
 template <typename R>
 struct Math;
+// Device: CUDA's math library.  Host (unit tests of this header only):
+// the C library, with sin/cos of pi x.
 template <>
 struct Math<double> {
-  __device__ static __forceinline__ double log(double x) { return ::log(x); }
-  __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
-  __device__ static __forceinline__ void sincospi(double x, double *s, double *c) { ::sincospi(x, s, c); }
+  __host__ __device__ static __forceinline__ double log(double x) { return ::log(x); }
+  __host__ __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  __host__ __device__ static __forceinline__ void sincospi(double x, double *s, double *c) {
+#ifdef __CUDA_ARCH__
+    ::sincospi(x, s, c);
+#else
+    *s = ::sin(3.14159265358979323846 * x);
+    *c = ::cos(3.14159265358979323846 * x);
+#endif
+  }
 };
 template <>
 struct Math<float> {
-  __device__ static __forceinline__ float log(float x) { return ::logf(x); }
-  __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
-  __device__ static __forceinline__ void sincospi(float x, float *s, float *c) { ::sincospif(x, s, c); }
+  __host__ __device__ static __forceinline__ float log(float x) { return ::logf(x); }
+  __host__ __device__ static __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
+  __host__ __device__ static __forceinline__ void sincospi(float x, float *s, float *c) {
+#ifdef __CUDA_ARCH__
+    ::sincospif(x, s, c);
+#else
+    *s = ::sinf(3.14159265f * x);
+    *c = ::cosf(3.14159265f * x);
+#endif
+  }
 };
 
 // Unit-variance variates z[0..NMOM-1] (moments a = 1..NMOM) of one site.
 // Call j has counter (site, lattice_id, t_lo, t_hi * 8 + j); moment 4j + k + 1
 // takes word k.  Gaussian: Box-Muller on the word pairs (0,1) and (2,3).
 template <typename R, int NMOM>
-__device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, uint32_t lattice_id, uint32_t t_lo,
+__host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, uint32_t lattice_id, uint32_t t_lo,
                                               uint32_t t_hi8, uint32_t key0, uint32_t key1, int dist) {
   constexpr int NCALL = (NMOM + 3) / 4;
 #pragma unroll
@@ -225,7 +249,7 @@ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, uint3
 template <int LAT, typename R>
 struct NoiseTransform {
   // generic: the compile-time basis with its zeros skipped
-  __device__ static __forceinline__ void apply(const R (&z)[Lattice<LAT>::Q - 1], R (&T)[Lattice<LAT>::Q]) {
+  __host__ __device__ static __forceinline__ void apply(const R (&z)[Lattice<LAT>::Q - 1], R (&T)[Lattice<LAT>::Q]) {
     constexpr int Q = Lattice<LAT>::Q;
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -252,7 +276,7 @@ struct NoiseTransform {
 // 3x3 pass over q followed by a 3x3 pass over p (24 multiply-adds).
 template <typename R>
 struct NoiseTransform<kD2Q9, R> {
-  __device__ static __forceinline__ void apply(const R (&z)[8], R (&T)[9]) {
+  __host__ __device__ static __forceinline__ void apply(const R (&z)[8], R (&T)[9]) {
     // zeta[p][q] = z^{3p+q}, zeta[0][0] = 0
     const R zeta[3][3] = {{R(0), z[0], z[1]}, {z[2], z[3], z[4]}, {z[5], z[6], z[7]}};
     R G[3][3];  // G[p][c]: c = 0 (v_y = 0), 1 (v_y = +1), 2 (v_y = -1)
@@ -287,7 +311,7 @@ struct NoiseTransform<kD2Q9, R> {
 // D1Q3: T(0) = -z^2/sqrt2, T(+-1) = +-sqrt3 z^1 + sqrt2 z^2.
 template <typename R>
 struct NoiseTransform<kD1Q3, R> {
-  __device__ static __forceinline__ void apply(const R (&z)[2], R (&T)[3]) {
+  __host__ __device__ static __forceinline__ void apply(const R (&z)[2], R (&T)[3]) {
     T[0] = R(-kInvSqrt2) * z[1];
     const R even = R(kSqrt2) * z[1];
     T[1] = fma(R(kSqrt3), z[0], even);

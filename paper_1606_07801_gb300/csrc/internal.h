@@ -27,6 +27,11 @@ struct StepArgs {
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
                         cudaStream_t stream);
 
+// Streaming shift between the stored post-collision state g and the
+// paper's f: dir = +1 gives f_i(x) = g_i(x - v_i), dir = -1 the inverse.
+cudaError_t launch_shift(int lattice, int value_bytes, const void *src, void *dst, int32_t Lx, int32_t Ly, int32_t Lz,
+                         int dir, cudaStream_t stream);
+
 // f_i = w_i rho(x), rho = rho_mean (+ amp sin(2 pi k.x / L)).
 cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
                         double amp, const int32_t *k, cudaStream_t stream);

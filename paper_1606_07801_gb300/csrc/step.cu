@@ -99,6 +99,63 @@ cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, 
 }
 
 // ---------------------------------------------------------------------------
+// Streaming shifts (pure data movement).  The pull kernel keeps the
+// post-collision populations g of the last step, which relate to the
+// paper's f(x, t) (eq. LB) by one streaming: f_i(x, t) = g_i(x - v_i).
+//   dir = +1: dst_i(x) = src_i(x - v_i)   (g -> f)
+//   dir = -1: dst_i(x) = src_i(x + v_i)   (f -> g)
+// ---------------------------------------------------------------------------
+template <int LAT, typename T>
+__global__ void k_shift(const T *__restrict__ src, T *__restrict__ dst, int32_t Lx, int32_t Ly, int32_t Lz, int dir) {
+  using L = Lattice<LAT>;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= Lx || y >= Ly) return;
+  const int xm = (x == 0 ? Lx : x) - 1, xp = (x + 1 == Lx) ? 0 : x + 1;
+  const int ym = (y == 0 ? Ly : y) - 1, yp = (y + 1 == Ly) ? 0 : y + 1;
+  const int zm = (z == 0 ? Lz : z) - 1, zp = (z + 1 == Lz) ? 0 : z + 1;
+  const uint32_t ux = static_cast<uint32_t>(Lx), uxy = ux * static_cast<uint32_t>(Ly);
+  const size_t N = static_cast<size_t>(uxy) * static_cast<uint32_t>(Lz);
+  const uint32_t s = static_cast<uint32_t>(x) + ux * static_cast<uint32_t>(y) + uxy * static_cast<uint32_t>(z);
+  static_for<L::Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    constexpr int vx = L::v(i, 0), vy = L::v(i, 1), vz = L::v(i, 2);
+    // source = x - dir * v_i
+    const int xs = vx == 0 ? x : ((vx * dir) > 0 ? xm : xp);
+    const int ys = vy == 0 ? y : ((vy * dir) > 0 ? ym : yp);
+    const int zs = vz == 0 ? z : ((vz * dir) > 0 ? zm : zp);
+    const uint32_t so = static_cast<uint32_t>(xs) + ux * static_cast<uint32_t>(ys) + uxy * static_cast<uint32_t>(zs);
+    dst[i * N + s] = src[i * N + so];
+  });
+}
+
+template <int LAT, typename T>
+static cudaError_t shift_t(const void *src, void *dst, int32_t Lx, int32_t Ly, int32_t Lz, int dir, cudaStream_t stream) {
+  dim3 grid, block;
+  step_shape(Lx, Ly, Lz, grid, block);
+  k_shift<LAT, T><<<grid, block, 0, stream>>>(static_cast<const T *>(src), static_cast<T *>(dst), Lx, Ly, Lz, dir);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(int lattice, int value_bytes, const void *src, void *dst, int32_t Lx, int32_t Ly, int32_t Lz,
+                         int dir, cudaStream_t stream) {
+  const bool b8 = value_bytes == 8;
+  switch (lattice) {
+    case kD1Q3:
+      return b8 ? shift_t<kD1Q3, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream)
+                : shift_t<kD1Q3, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
+    case kD2Q9:
+      return b8 ? shift_t<kD2Q9, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream)
+                : shift_t<kD2Q9, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
+    case kD3Q19:
+      return b8 ? shift_t<kD3Q19, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream)
+                : shift_t<kD3Q19, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
 // Initial state f_i = w_i rho(x) (local equilibrium, eq. f0def)
 // ---------------------------------------------------------------------------
 template <int LAT, typename R>

@@ -1,0 +1,49 @@
+// Host build of the device header's arithmetic, for CPU unit tests: the
+// noise variates and the noise back-transform the step kernel uses,
+// evaluated by the same source on the host.
+#include <stdint.h>
+
+#include "device.cuh"
+
+using namespace lbfd;
+
+template <int LAT, typename R>
+static void transform_t(const double *z, double *T) {
+  constexpr int Q = Lattice<LAT>::Q;
+  R zz[Q - 1], TT[Q];
+  for (int a = 0; a < Q - 1; ++a) zz[a] = static_cast<R>(z[a]);
+  NoiseTransform<LAT, R>::apply(zz, TT);
+  for (int i = 0; i < Q; ++i) T[i] = static_cast<double>(TT[i]);
+}
+
+template <typename R, int NMOM>
+static void variates_t(int dist, uint64_t seed, uint32_t lid, uint32_t site, uint64_t t, double *z) {
+  R zz[NMOM];
+  draw_variates<R, NMOM>(zz, site, lid, uint32_t(t), uint32_t(t >> 32) << 3, uint32_t(seed), uint32_t(seed >> 32), dist);
+  for (int a = 0; a < NMOM; ++a) z[a] = static_cast<double>(zz[a]);
+}
+
+extern "C" {
+
+int dhc_transform(int lattice, int f64, const double *z, double *T) {
+  switch (lattice) {
+    case kD1Q3: f64 ? transform_t<kD1Q3, double>(z, T) : transform_t<kD1Q3, float>(z, T); return 0;
+    case kD2Q9: f64 ? transform_t<kD2Q9, double>(z, T) : transform_t<kD2Q9, float>(z, T); return 0;
+    case kD3Q19: f64 ? transform_t<kD3Q19, double>(z, T) : transform_t<kD3Q19, float>(z, T); return 0;
+  }
+  return -1;
+}
+
+int dhc_variates(int f64, int nmom, int dist, uint64_t seed, uint32_t lid, uint32_t site, uint64_t t, double *z) {
+  if (nmom == 2) { f64 ? variates_t<double, 2>(dist, seed, lid, site, t, z) : variates_t<float, 2>(dist, seed, lid, site, t, z); return 0; }
+  if (nmom == 8) { f64 ? variates_t<double, 8>(dist, seed, lid, site, t, z) : variates_t<float, 8>(dist, seed, lid, site, t, z); return 0; }
+  if (nmom == 18) { f64 ? variates_t<double, 18>(dist, seed, lid, site, t, z) : variates_t<float, 18>(dist, seed, lid, site, t, z); return 0; }
+  return -1;
+}
+
+int dhc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  uint4 r = philox4x32_10(make_uint4(ctr[0], ctr[1], ctr[2], ctr[3]), key[0], key[1]);
+  out[0] = r.x; out[1] = r.y; out[2] = r.z; out[3] = r.w;
+  return 0;
+}
+}

@@ -1,0 +1,69 @@
+"""CPU unit tests of the device header's arithmetic (device.cuh compiled for
+the host by nvcc): Philox4x32-10, the noise variates and the noise
+back-transform the step kernel uses, against the oracle."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1606_07801_gb300 as lb
+from tests import golden_io
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dhc(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("dhc") / "libdhc.so")
+    src = os.path.join(ROOT, "tests", "csrc", "device_host_check.cu")
+    inc = os.path.join(ROOT, "paper_1606_07801_gb300", "csrc")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "-I", inc, "-I",
+                    os.path.join(ROOT, "include"), src, "-o", out], check=True)
+    lib = ctypes.CDLL(out)
+    lib.dhc_transform.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.dhc_variates.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
+                                 ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p]
+    lib.dhc_philox.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    return lib
+
+
+def test_device_philox_known_answers(dhc):
+    for ctr, key, out in golden_io.philox_kat():
+        c = np.array(ctr, dtype=np.uint32)
+        k = np.array(key, dtype=np.uint32)
+        o = np.zeros(4, dtype=np.uint32)
+        dhc.dhc_philox(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+        assert o.tolist() == out
+
+
+@pytest.mark.parametrize("lat", [lb.D1Q3, lb.D2Q9, lb.D3Q19])
+@pytest.mark.parametrize("f64,tol", [(1, 1e-15), (0, 1e-6)])
+def test_noise_transform_is_the_basis(orc, dhc, lat, f64, tol):
+    """T_i = sum_{a>=1} m_i^a z^a for unit z: the kernel's (factorised or
+    sparse) transform reproduces the oracle's Gram-Schmidt basis."""
+    Q = lb.Q_OF[lat]
+    m = orc.basis(lat)
+    for a in range(Q - 1):
+        z = np.zeros(Q - 1)
+        z[a] = 1.0
+        T = np.zeros(Q)
+        dhc.dhc_transform(lat, f64, z.ctypes.data, T.ctypes.data)
+        assert np.max(np.abs(T - m[a + 1])) < tol * 4
+
+
+@pytest.mark.parametrize("nmom", [2, 8, 18])
+@pytest.mark.parametrize("dist", [0, 1])
+def test_variates_match_oracle(orc, dhc, nmom, dist):
+    for site, t in [(0, 0), (77, 99), (2**31 + 5, 2**33 + 7)]:
+        z = np.zeros(nmom)
+        dhc.dhc_variates(1, nmom, dist, 0xDEADBEEF12345, 9, site, t, z.ctypes.data)
+        zo = orc.site_noise(0xDEADBEEF12345, 9, site, t, nmom, dist)
+        assert np.max(np.abs(z - zo)) < 1e-14
+        dhc.dhc_variates(0, nmom, dist, 0xDEADBEEF12345, 9, site, t, z.ctypes.data)
+        assert np.max(np.abs(z - zo)) < 5e-6 * max(1.0, np.max(np.abs(zo)))
