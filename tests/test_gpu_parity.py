@@ -3,7 +3,13 @@ same seeded inputs and the same Philox noise stream.
 
 Tolerances (max |f_gpu - f_oracle| after the stated number of steps):
   FP64 arithmetic: 1e-12 * rho_mean
-  FP32 arithmetic: 2e-5  * rho_mean
+  FP32 arithmetic: 2e-5  * rho_mean, where the local density stays away
+                   from zero.  Local noise has amplitude sqrt(max(rho, 0)),
+                   whose slope is unbounded at rho = 0: a site that comes
+                   within FP32 rounding of zero density draws visibly
+                   different noise in FP32 and FP64, and the difference
+                   then diffuses.  Runs that reach rho ~ 0 are compared
+                   pathwise in FP64 and statistically in FP32.
 Lattices span several thread blocks and end in ragged tails in x and y.
 """
 import numpy as np
@@ -33,15 +39,17 @@ def _oracle_run(orc, lat, dims, f0, nsteps, tau, mode=lb.NOISE_LOCAL, dist=lb.GA
 
 
 CASES = [
-    # lattice, dims, tau, rho_mean
-    (lb.D1Q3, (1000,), 1.0, 10.0),
-    (lb.D2Q9, (67, 45), 0.8, 100.0),
-    (lb.D3Q19, (19, 13, 11), 1.0, 50.0),
+    # lattice, dims, tau, rho_mean, precision
+    (lb.D1Q3, (1000,), 1.0, 10.0, lb.F64),   # the D1Q3 workload's density; reaches rho ~ 0 at times
+    (lb.D1Q3, (1000,), 1.0, 100.0, lb.F32),
+    (lb.D2Q9, (67, 45), 0.8, 100.0, lb.F64),
+    (lb.D2Q9, (67, 45), 0.8, 100.0, lb.F32),
+    (lb.D3Q19, (19, 13, 11), 1.0, 50.0, lb.F64),
+    (lb.D3Q19, (19, 13, 11), 1.0, 50.0, lb.F32),
 ]
 
 
-@pytest.mark.parametrize("precision", [lb.F64, lb.F32])
-@pytest.mark.parametrize("lat,dims,tau,rho", CASES)
+@pytest.mark.parametrize("lat,dims,tau,rho,precision", CASES)
 def test_parity_1000_steps_local_gaussian(orc, lat, dims, tau, rho, precision):
     Q, N = lb.Q_OF[lat], int(np.prod(dims))
     f0 = synth.random_populations(Q, N, rho, 0.3, seed=11 + lat)
@@ -57,7 +65,7 @@ def test_parity_1000_steps_local_gaussian(orc, lat, dims, tau, rho, precision):
 @pytest.mark.parametrize("mode,dist", [(lb.NOISE_GLOBAL, lb.GAUSSIAN), (lb.NOISE_OFF, lb.GAUSSIAN),
                                        (lb.NOISE_LOCAL, lb.UNIFORM), (lb.NOISE_GLOBAL, lb.UNIFORM)])
 @pytest.mark.parametrize("lat,dims,tau,rho", [(lb.D2Q9, (40, 33), 0.6, 20.0), (lb.D3Q19, (9, 10, 7), 1.4, 30.0),
-                                              (lb.D1Q3, (300,), 0.75, 5.0)])
+                                              (lb.D1Q3, (300,), 0.75, 60.0)])
 def test_parity_noise_variants(orc, lat, dims, tau, rho, mode, dist, precision):
     Q, N = lb.Q_OF[lat], int(np.prod(dims))
     f0 = synth.random_populations(Q, N, rho, 0.2, seed=5)
@@ -90,10 +98,11 @@ def test_zero_density_stays_zero(precision):
 
 def test_low_density_local_noise(orc):
     """rho = 0.5 with the zero-density clamp: FP64 follows the oracle pathwise;
-    in FP32 the kink of sqrt(max(rho, 0)) lets a few sites drift, so FP32 is
-    judged by the fraction of sites beyond tolerance and by mass."""
-    lat, dims, rho = lb.D2Q9, (64, 48), 0.5
-    Q, N = 9, 64 * 48
+    FP32 is judged statistically (mass, density variance, share of
+    negative-density sites, mean populations), and the share of sites beyond
+    the pathwise tolerance is reported."""
+    lat, dims, rho = lb.D2Q9, (128, 96), 0.5
+    Q, N = 9, 128 * 96
     f0 = synth.random_populations(Q, N, rho, 0.3, seed=99)
     o = _oracle_run(orc, lat, dims, f0, 200, 0.8, rho_mean=rho, seed=21)
     assert (o.sum(0) < 0).mean() > 0.01  # the clamp is exercised
@@ -101,8 +110,16 @@ def test_low_density_local_noise(orc):
     assert np.max(np.abs(g64 - o)) <= 1e-12 * rho
     g32 = _gpu_run(lat, dims, f0, 200, 0.8, lb.F32, rho_mean=rho, seed=21)
     bad = np.any(np.abs(g32 - o) > 2e-5 * rho, axis=0).mean()
-    assert bad < 0.01
-    assert abs(g32.sum() - o.sum()) < 1e-4 * N * rho
+    print(f"FP32 at rho = 0.5: {100 * bad:.1f}% of sites beyond 2e-5 rho after 200 steps")
+    assert abs(g32.sum() - o.sum()) < 1e-5 * N * rho
+    rg, ro = g32.sum(0), o.sum(0)
+    # the two fields are two samples of the same law; with shared noise they
+    # are strongly correlated, so their statistics agree well within the
+    # sampling error of one field
+    se_var = ro.var() * np.sqrt(2.0 / N)
+    assert abs(rg.var() - ro.var()) < 3 * se_var
+    assert abs((rg < 0).mean() - (ro < 0).mean()) < 3 * np.sqrt((ro < 0).mean() / N)
+    assert np.max(np.abs(g32.mean(1) - o.mean(1))) < 5 * o.std(1).max() / np.sqrt(N)
 
 
 @pytest.mark.parametrize("precision,tol", [(lb.F64, 1e-14), (lb.F32, 3e-6)])
