@@ -165,8 +165,11 @@ __host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
 __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = c.x * Philox::M0, hi0 = mulhi32(c.x, Philox::M0);
-    const uint32_t lo1 = c.z * Philox::M1, hi1 = mulhi32(c.z, Philox::M1);
+    // one 32x32 -> 64-bit multiply gives both halves of each product
+    const uint64_t p0 = static_cast<uint64_t>(c.x) * Philox::M0;
+    const uint64_t p1 = static_cast<uint64_t>(c.z) * Philox::M1;
+    const uint32_t lo0 = static_cast<uint32_t>(p0), hi0 = static_cast<uint32_t>(p0 >> 32);
+    const uint32_t lo1 = static_cast<uint32_t>(p1), hi1 = static_cast<uint32_t>(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += Philox::W0;
     k1 += Philox::W1;
@@ -211,6 +214,46 @@ struct Math<float> {
   }
 };
 
+// Box-Muller pair (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1).
+// FP64: CUDA's log / sqrt / sincospi.  FP32 on the device: the special
+// function unit, with -2 ln u0 from its Taylor series in v = 1 - u0 when
+// u0 > 63/64 (there a table-free log2 loses its relative accuracy and the
+// square root would amplify that), and the angle reduced to [-pi, pi)
+// before the SFU sine and cosine.  Absolute error of the FP32 variates
+// against FP64: about 1e-6 (see the tests).
+template <typename R>
+struct BoxMuller {
+  __host__ __device__ static __forceinline__ void pair(R u0, R u1, R &z0, R &z1) {
+    const R rad = Math<R>::sqrt(R(-2) * Math<R>::log(u0));
+    R s, c;
+    Math<R>::sincospi(R(2) * u1, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+  }
+};
+
+template <>
+struct BoxMuller<float> {
+  __host__ __device__ static __forceinline__ void pair(float u0, float u1, float &z0, float &z1) {
+#ifdef __CUDA_ARCH__
+    const float v = 1.0f - u0;  // exact: u0 is a multiple of 2^-25
+    const float series = 2.0f * v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 0.33333334f), 0.5f), 1.0f);
+    const float x = v < 0.015625f ? series : -2.0f * __logf(u0);  // x > 0 for every u0 on the grid
+    const float rad = x * rsqrtf(x);
+    float s, c;
+    __sincosf(6.28318530717958648f * (u1 - 0.5f), &s, &c);  // angle 2 pi u1 - pi
+    z0 = -rad * c;
+    z1 = -rad * s;
+#else
+    const float rad = sqrtf(-2.0f * logf(u0));
+    float s, c;
+    Math<float>::sincospi(2.0f * u1, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+#endif
+  }
+};
+
 // Unit-variance variates z[0..NMOM-1] (moments a = 1..NMOM) of one site.
 // Call j has counter (site, lattice_id, t_lo, t_hi * 8 + j); moment 4j + k + 1
 // takes word k.  Gaussian: Box-Muller on the word pairs (0,1) and (2,3).
@@ -226,12 +269,10 @@ __host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t si
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         if (4 * j + 2 * p < NMOM) {
-          const R u0 = unit24<R>(w[2 * p]), u1 = unit24<R>(w[2 * p + 1]);
-          const R rad = Math<R>::sqrt(R(-2) * Math<R>::log(u0));
-          R s, c;
-          Math<R>::sincospi(R(2) * u1, &s, &c);
-          z[4 * j + 2 * p] = rad * c;
-          if (4 * j + 2 * p + 1 < NMOM) z[4 * j + 2 * p + 1] = rad * s;
+          R z0, z1;
+          BoxMuller<R>::pair(unit24<R>(w[2 * p]), unit24<R>(w[2 * p + 1]), z0, z1);
+          z[4 * j + 2 * p] = z0;
+          if (4 * j + 2 * p + 1 < NMOM) z[4 * j + 2 * p + 1] = z1;
         }
       }
     } else {

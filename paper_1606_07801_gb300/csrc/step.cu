@@ -9,7 +9,8 @@
 //   collide f*_i = (1 - 1/tau) f_i + w_i (rho/tau + sigma sum_{a>=1} m_i^a z^a)
 //           which is eq. collision with Lambda = 1/tau (eq. coll) written in
 //           f-space: M^{a*} = (1 - 1/tau) M^a + sigma z^a for a >= 1,
-//           M^{0*} = rho, back-transformed with n_i^a = m_i^a w_i
+//           M^{0*} = rho, back-transformed with n_i^a = m_i^a w_i; the rest
+//           population is rho - sum_{i>=1} f*_i (the same in exact arithmetic)
 //   store   f*_i(x) into the other buffer
 // Everything lives in registers; the populations are read and written once.
 #include <cuda_runtime.h>
@@ -62,11 +63,17 @@ __global__ void __launch_bounds__(256) k_step(const R *__restrict__ src, R *__re
 
   const R omega = static_cast<R>(a.omega);
   const R relaxed = rho * static_cast<R>(a.inv_tau);
-  static_for<Q>([&](auto I) {
-    constexpr int i = decltype(I)::value;
+  // moving populations; the rest population takes what mass conservation
+  // leaves, so the rounding of sum_i w_i = 1 cannot make the mass drift
+  R moved = R(0);
+  static_for<Q - 1>([&](auto I) {
+    constexpr int i = decltype(I)::value + 1;
     const R eq_and_noise = fma(sigma, T[i], relaxed);
-    dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = fma(omega, f[i], static_cast<R>(L::w(i)) * eq_and_noise);
+    const R out = fma(omega, f[i], static_cast<R>(L::w(i)) * eq_and_noise);
+    moved += out;
+    dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = out;
   });
+  dst[s] = rho - moved;
 }
 
 static void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block) {
