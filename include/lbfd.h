@@ -191,6 +191,14 @@ int lbfd_lattice_tables(int32_t lattice, int32_t *Q, int32_t *v, double *w, doub
 int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lattice_id, uint64_t t,
                     int64_t site0, int64_t nsites, int32_t nmom, double *z_host);
 
+/* Box-Muller normals the step kernel makes from given Philox words:
+ * (z[2k], z[2k+1]) from (words[2k], words[2k+1]) with u = ((r >> 8) + 1/2) 2^-24,
+ * z0 = sqrt(-2 ln u0) cos(2 pi u1), z1 = sqrt(-2 ln u0) sin(2 pi u1), computed on
+ * the current device in the given precision; host arrays of 2*npairs values.
+ * For checks of the edges of the uniform grid.  Synchronous; allocates
+ * temporary device buffers. */
+int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t npairs, double *z_host);
+
 /* Message for the calling thread's last failure ("" if none). */
 const char *lbfd_last_error(void);
 

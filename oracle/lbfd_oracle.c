@@ -208,7 +208,7 @@ void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
 }
 
 /* Uniform on (0,1): the top 24 bits of a word, centred in their cell.
- * Every value is exact in FP32 and in FP64. */
+ * Every value is an odd multiple of 2^-25, exact in FP64. */
 static double word_to_unit(uint32_t r)
 {
     return ((double)(r >> 8) + 0.5) * (1.0 / 16777216.0);

@@ -441,6 +441,23 @@ int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lat
   return LBFD_OK;
 }
 
+int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t npairs, double *z_host) {
+  if (!words_host || !z_host || npairs < 0) return fail(LBFD_EINVAL, "lbfd_box_muller_probe: bad argument");
+  if (precision != LBFD_F32 && precision != LBFD_F64) return fail(LBFD_EINVAL, "unknown precision");
+  if (npairs == 0) return LBFD_OK;
+  uint32_t *dw = nullptr;
+  double *dz = nullptr;
+  cudaError_t e = cudaMalloc(&dw, sizeof(uint32_t) * 2 * size_t(npairs));
+  if (e == cudaSuccess) e = cudaMalloc(&dz, sizeof(double) * 2 * size_t(npairs));
+  if (e == cudaSuccess) e = cudaMemcpy(dw, words_host, sizeof(uint32_t) * 2 * size_t(npairs), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_box_muller_probe(precision, dw, npairs, dz, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(z_host, dz, sizeof(double) * 2 * size_t(npairs), cudaMemcpyDeviceToHost);
+  cudaFree(dw);
+  cudaFree(dz);
+  if (e != cudaSuccess) return cuda_fail("lbfd_box_muller_probe", e);
+  return LBFD_OK;
+}
+
 const char *lbfd_last_error(void) { return g_err.c_str(); }
 
 int64_t lbfd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -177,7 +177,8 @@ __host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, ui
   return c;
 }
 
-// Top 24 bits of a word as a cell-centred uniform on (0, 1); exact in FP32.
+// Top 24 bits of a word as a cell-centred uniform on (0, 1): exact in FP64,
+// and in FP32 below 1/2.
 template <typename R>
 __host__ __device__ __forceinline__ R unit24(uint32_t r) {
   return (static_cast<R>(r >> 8) + R(0.5)) * R(5.9604644775390625e-08);
@@ -214,16 +215,23 @@ struct Math<float> {
   }
 };
 
-// Box-Muller pair (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1).
-// FP64: CUDA's log / sqrt / sincospi.  FP32 on the device: the special
-// function unit, with -2 ln u0 from its Taylor series in v = 1 - u0 when
-// u0 > 63/64 (there a table-free log2 loses its relative accuracy and the
-// square root would amplify that), and the angle reduced to [-pi, pi)
-// before the SFU sine and cosine.  Absolute error of the FP32 variates
-// against FP64: about 1e-6 (see the tests).
+// Box-Muller pair (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1) from
+// two Philox words, u = ((r >> 8) + 1/2) 2^-24.
+// FP64: the uniforms are exact; CUDA's log / sqrt / sincospi.
+// FP32 on the device: the special-function unit.  An odd multiple of 2^-25
+// above 1/2 has no FP32 representation, so the quantities that need it are
+// formed exactly from the integer word instead:
+//   v  = 1 - u0 = ((~r0 >> 8) + 1/2) 2^-24  (exact below 1/2); when
+//        v < 1/64, -2 ln u0 comes from its Taylor series in v (there the
+//        SFU log has only absolute accuracy, which the square root would
+//        amplify); otherwise from the SFU log of u0
+//   u1 - 1/2 = ((r1 >> 8) - 2^23 + 1/2) 2^-24 (exact), so the SFU sine and
+//        cosine see the angle 2 pi u1 - pi in [-pi, pi)
+// Absolute error of the FP32 variates against FP64: about 1e-6.
 template <typename R>
 struct BoxMuller {
-  __host__ __device__ static __forceinline__ void pair(R u0, R u1, R &z0, R &z1) {
+  __host__ __device__ static __forceinline__ void pair(uint32_t r0, uint32_t r1, R &z0, R &z1) {
+    const R u0 = unit24<R>(r0), u1 = unit24<R>(r1);
     const R rad = Math<R>::sqrt(R(-2) * Math<R>::log(u0));
     R s, c;
     Math<R>::sincospi(R(2) * u1, &s, &c);
@@ -234,20 +242,22 @@ struct BoxMuller {
 
 template <>
 struct BoxMuller<float> {
-  __host__ __device__ static __forceinline__ void pair(float u0, float u1, float &z0, float &z1) {
+  __host__ __device__ static __forceinline__ void pair(uint32_t r0, uint32_t r1, float &z0, float &z1) {
 #ifdef __CUDA_ARCH__
-    const float v = 1.0f - u0;  // exact: u0 is a multiple of 2^-25
+    const float v = unit24<float>(~r0);
     const float series = 2.0f * v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 0.33333334f), 0.5f), 1.0f);
-    const float x = v < 0.015625f ? series : -2.0f * __logf(u0);  // x > 0 for every u0 on the grid
+    const float x = v < 0.015625f ? series : -2.0f * __logf(unit24<float>(r0));  // x >= 2^-24 > 0
     const float rad = x * rsqrtf(x);
+    const float half_turns = (static_cast<float>(static_cast<int32_t>(r1 >> 8) - 8388608) + 0.5f) *
+                             5.9604644775390625e-08f;  // u1 - 1/2, exact
     float s, c;
-    __sincosf(6.28318530717958648f * (u1 - 0.5f), &s, &c);  // angle 2 pi u1 - pi
+    __sincosf(6.28318530717958648f * half_turns, &s, &c);
     z0 = -rad * c;
     z1 = -rad * s;
 #else
-    const float rad = sqrtf(-2.0f * logf(u0));
+    const float rad = sqrtf(-2.0f * logf(unit24<float>(r0)));
     float s, c;
-    Math<float>::sincospi(2.0f * u1, &s, &c);
+    Math<float>::sincospi(2.0f * unit24<float>(r1), &s, &c);
     z0 = rad * c;
     z1 = rad * s;
 #endif
@@ -270,7 +280,7 @@ __host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t si
       for (int p = 0; p < 2; ++p) {
         if (4 * j + 2 * p < NMOM) {
           R z0, z1;
-          BoxMuller<R>::pair(unit24<R>(w[2 * p]), unit24<R>(w[2 * p + 1]), z0, z1);
+          BoxMuller<R>::pair(w[2 * p], w[2 * p + 1], z0, z1);
           z[4 * j + 2 * p] = z0;
           if (4 * j + 2 * p + 1 < NMOM) z[4 * j + 2 * p + 1] = z1;
         }

@@ -45,6 +45,10 @@ cudaError_t launch_noise_draw(int precision, int dist, uint32_t key0, uint32_t k
                               uint32_t t_lo, uint32_t t_hi8, int64_t site0, int64_t nsites, int nmom, double *z,
                               cudaStream_t stream);
 
+// Box-Muller pairs of given Philox words: words[2k], words[2k+1] -> z[2k], z[2k+1].
+cudaError_t launch_box_muller_probe(int precision, const uint32_t *words, int64_t npairs, double *z,
+                                    cudaStream_t stream);
+
 // Deterministic FP64 reductions.
 //   Stage 1 writes per-block partials of `nq` quantities to partials[block][nq];
 //   stage 2 sums them in block order and adds the totals into acc[nq] (or

@@ -306,6 +306,29 @@ cudaError_t launch_noise_draw(int precision, int dist, uint32_t key0, uint32_t k
                         : noise_p<float>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, nmom, z, stream);
 }
 
+// Box-Muller on given word pairs (edge cases of the uniform grid)
+template <typename R>
+__global__ void k_box_muller_probe(const uint32_t *__restrict__ words, int64_t npairs, double *__restrict__ z) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < npairs;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    R z0, z1;
+    BoxMuller<R>::pair(words[2 * k], words[2 * k + 1], z0, z1);
+    z[2 * k] = static_cast<double>(z0);
+    z[2 * k + 1] = static_cast<double>(z1);
+  }
+}
+
+cudaError_t launch_box_muller_probe(int precision, const uint32_t *words, int64_t npairs, double *z,
+                                    cudaStream_t stream) {
+  const int64_t blocks = (npairs + 255) / 256;
+  const int grid = static_cast<int>(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
+  if (precision == 1)
+    k_box_muller_probe<double><<<grid, 256, 0, stream>>>(words, npairs, z);
+  else
+    k_box_muller_probe<float><<<grid, 256, 0, stream>>>(words, npairs, z);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Host copies of the tables the kernels are compiled with
 // ---------------------------------------------------------------------------

@@ -81,6 +81,7 @@ SIGNATURES = {
     "lbfd_lattice_tables": (c_int32, [c_int32, P(c_int32), c_void_p, c_void_p, c_void_p]),
     "lbfd_noise_draw": (c_int32, [c_int32, c_int32, c_uint64, c_uint32, c_uint64, c_int64, c_int64, c_int32,
                                   c_void_p]),
+    "lbfd_box_muller_probe": (c_int32, [c_int32, c_void_p, c_int64, c_void_p]),
     "lbfd_last_error": (ctypes.c_char_p, []),
     "lbfd_kernel_launches": (c_int64, []),
     "lbfd_struct_sizes": (c_int32, [P(c_int64), P(c_int64)]),
@@ -258,6 +259,15 @@ def lbfd_noise_draw(precision: int, dist: int, seed: int, lattice_id: int, t: in
     z = np.empty((nsites, nmom), dtype=np.float64)
     _check(load().lbfd_noise_draw(precision, dist, seed, lattice_id, t, site0, nsites, nmom, _ptr(z)),
            "lbfd_noise_draw")
+    return z
+
+
+def lbfd_box_muller_probe(precision: int, words: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(words, dtype=np.uint32).ravel()
+    if w.size % 2:
+        raise ValueError("words must come in pairs")
+    z = np.empty(w.size, dtype=np.float64)
+    _check(load().lbfd_box_muller_probe(precision, _ptr(w), w.size // 2, _ptr(z)), "lbfd_box_muller_probe")
     return z
 
 
