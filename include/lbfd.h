@@ -199,6 +199,28 @@ int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lat
  * temporary device buffers. */
 int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t npairs, double *z_host);
 
+/* Total mass sum_x sum_i f_i, like lbfd_mass, for callers that cannot
+ * allocate device memory: a host framework that reserved the GPU for its own
+ * allocator and forbids libraries to allocate, a service under a fixed
+ * device-memory budget, or a loop that cannot afford cudaMalloc/cudaFree
+ * (they can synchronise the device).  The paper has no counterpart; this is
+ * a library service.
+ *   f_dev    device array of Q*n_sites values (float for LBFD_F32, double for
+ *            LBFD_F64), layout [i][site]; any storage order of the sites works
+ *            (the sum is over all of them)
+ *   mass_dev caller-owned device double that receives the sum
+ *   stream   cudaStream_t to launch on (NULL: legacy default stream)
+ * Asynchronous; calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its partial sums live in a fixed 128 KiB device array that every GPU
+ * loading the library holds until exit, so n_sites is limited to 16,777,216
+ * (LBFD_EINVAL beyond).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call overwrites the partials it reads, so no state
+ * carries over, but all calls share the array: calls whose kernels overlap
+ * on the GPU race and may return wrong sums; order them on one stream. */
+int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void *f_dev, int64_t n_sites, double *mass_dev,
+                      void *stream);
+
 /* Message for the calling thread's last failure ("" if none). */
 const char *lbfd_last_error(void);
 

@@ -54,6 +54,8 @@ int lattice_q(int lattice) { return lattice == LBFD_D1Q3 ? 3 : (lattice == LBFD_
 
 }  // namespace
 
+int lbfd::set_last_error(int code, const std::string &msg) { return fail(code, msg); }
+
 struct lbfd_sim {
   lbfd_options opt{};
   int Q = 0, D = 0, elem = 0;

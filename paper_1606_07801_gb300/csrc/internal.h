@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #define LBFD_MAX_MODES_DEV 16
 
 namespace lbfd {
@@ -65,6 +67,9 @@ cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, do
 cudaError_t launch_observables(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
                                double rho_mean, int n_modes, const int32_t *modes /*device, n_modes*3*/,
                                double *partials, double *acc, cudaStream_t stream);
+
+// Records msg as the calling thread's lbfd_last_error() and returns code.
+int set_last_error(int code, const std::string &msg);
 
 // Host copy of the moment matrix the kernels use, m[a*Q + i].
 int basis_table(int lattice, double *m);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "lbfd_noise_draw": (c_int32, [c_int32, c_int32, c_uint64, c_uint32, c_uint64, c_int64, c_int64, c_int32,
                                   c_void_p]),
     "lbfd_box_muller_probe": (c_int32, [c_int32, c_void_p, c_int64, c_void_p]),
+    "lbfd_mass_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p]),
     "lbfd_last_error": (ctypes.c_char_p, []),
     "lbfd_kernel_launches": (c_int64, []),
     "lbfd_struct_sizes": (c_int32, [P(c_int64), P(c_int64)]),
@@ -269,6 +270,14 @@ def lbfd_box_muller_probe(precision: int, words: np.ndarray) -> np.ndarray:
     z = np.empty(w.size, dtype=np.float64)
     _check(load().lbfd_box_muller_probe(precision, _ptr(w), w.size // 2, _ptr(z)), "lbfd_box_muller_probe")
     return z
+
+
+def lbfd_mass_noalloc(lattice: int, precision: int, f_dev_ptr: int, n_sites: int, mass_dev_ptr: int,
+                      stream: int | None = None) -> None:
+    """Mass of a caller-owned device array into a caller-owned device double,
+    with no device allocation (fixed internal scratch; see include/lbfd.h)."""
+    _check(load().lbfd_mass_noalloc(lattice, precision, f_dev_ptr, n_sites, mass_dev_ptr, stream),
+           "lbfd_mass_noalloc")
 
 
 def lbfd_kernel_launches() -> int:
