@@ -239,13 +239,8 @@ int lbfd_step(lbfd_t h, int64_t n) {
   a.rho_eq = o.rho_mean;
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
-  a.key0 = uint32_t(o.seed);
-  a.key1 = uint32_t(o.seed >> 32);
-  a.lattice_id = o.lattice_id;
   for (int64_t k = 0; k < n; ++k) {
-    const uint64_t t = uint64_t(h->t);
-    a.t_lo = uint32_t(t);
-    a.t_hi8 = uint32_t(t >> 32) << 3;
+    a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
     cudaError_t e = launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream);
     if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
     h->cur ^= 1;
@@ -435,8 +430,8 @@ int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lat
   double *d = nullptr;
   const size_t bytes = sizeof(double) * size_t(nsites) * nmom;
   LBFD_CU(cudaMalloc(&d, bytes));
-  cudaError_t e = launch_noise_draw(precision, dist, uint32_t(seed), uint32_t(seed >> 32), lattice_id, uint32_t(t),
-                                    uint32_t(t >> 32) << 3, site0, nsites, nmom, d, nullptr);
+  cudaError_t e = launch_noise_draw(precision, dist, make_philox_step(seed, lattice_id, t), site0, nsites, nmom, d,
+                                    nullptr);
   if (e == cudaSuccess) e = cudaMemcpy(z_host, d, bytes, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail("lbfd_noise_draw", e);

@@ -215,6 +215,21 @@ struct Math<float> {
   }
 };
 
+// Noise amplitude sqrt(x), x = rho_n (2 tau - 1)/tau^2 >= 0.  FP32 on the
+// device: x * rsqrt(x) on the special-function unit (about 2 ulp).
+template <typename R>
+__host__ __device__ __forceinline__ R noise_amplitude(R x) {
+  return Math<R>::sqrt(x);
+}
+template <>
+__host__ __device__ __forceinline__ float noise_amplitude<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+  return sqrtf(x);
+#endif
+}
+
 // Box-Muller pair (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1) from
 // two Philox words, u = ((r >> 8) + 1/2) 2^-24.
 // FP64: the uniforms are exact; CUDA's log / sqrt / sincospi.
@@ -264,16 +279,74 @@ struct BoxMuller<float> {
   }
 };
 
+// Philox4x32-10 for the step kernel.  In one step every thread's counter is
+// (site, lattice id, t_lo, t_hi*8 + j): only the site differs between
+// threads and only j between the calls of a site.  The parts of rounds 0-2
+// that depend on the uniform words alone, and all round keys, are computed
+// once per step on the host (make_philox_step); per thread and call the
+// first two rounds then cost one 32x32 -> 64-bit multiply and three XORs.
+// philox_site(...) equals philox4x32_10(make_uint4(site, lid, t_lo,
+// t_hi*8 + j), k0, k1) for every input (checked by the tests).
+struct PhiloxStep {
+  uint32_t e[8];   // round 0: (t_hi*8 + j) ^ K1[0], per call j
+  uint32_t f;      // round 1: lo(t_lo M1) ^ K0[1]
+  uint32_t g;      // round 1: hi(a1 M0) ^ K1[1], a1 = hi(t_lo M1) ^ lid ^ K0[0]
+  uint32_t q;      // round 2: lo(a1 M0) ^ K1[2]
+  uint32_t k0[10], k1[10];  // round keys K0[r] = k0 + r W0, K1[r] = k1 + r W1
+};
+
+__host__ __device__ inline PhiloxStep make_philox_step(uint64_t seed, uint32_t lattice_id, uint64_t t) {
+  PhiloxStep P{};
+  const uint32_t key0 = static_cast<uint32_t>(seed), key1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    P.k0[r] = key0 + static_cast<uint32_t>(r) * Philox::W0;
+    P.k1[r] = key1 + static_cast<uint32_t>(r) * Philox::W1;
+  }
+  const uint32_t t_lo = static_cast<uint32_t>(t), t_hi8 = static_cast<uint32_t>(t >> 32) << 3;
+  for (int j = 0; j < 8; ++j) P.e[j] = (t_hi8 | static_cast<uint32_t>(j)) ^ P.k1[0];
+  const uint64_t u = static_cast<uint64_t>(t_lo) * Philox::M1;
+  const uint32_t a1 = static_cast<uint32_t>(u >> 32) ^ lattice_id ^ P.k0[0];
+  const uint32_t b1 = static_cast<uint32_t>(u);
+  const uint64_t v = static_cast<uint64_t>(a1) * Philox::M0;
+  P.f = b1 ^ P.k0[1];
+  P.g = static_cast<uint32_t>(v >> 32) ^ P.k1[1];
+  P.q = static_cast<uint32_t>(v) ^ P.k1[2];
+  return P;
+}
+
+// Call j of a site whose product site * M0 is (s_hi, s_lo).
+__host__ __device__ __forceinline__ uint4 philox_site(uint32_t s_hi, uint32_t s_lo, const PhiloxStep &P, int j) {
+  // rounds 0 and 1
+  const uint64_t p = static_cast<uint64_t>(s_hi ^ P.e[j]) * Philox::M1;
+  uint4 c = make_uint4(static_cast<uint32_t>(p >> 32) ^ P.f, static_cast<uint32_t>(p), s_lo ^ P.g, 0u);
+  // round 2 (its third word takes the uniform q)
+  {
+    const uint64_t p0 = static_cast<uint64_t>(c.x) * Philox::M0;
+    const uint64_t p1 = static_cast<uint64_t>(c.z) * Philox::M1;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ P.k0[2], static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ P.q, static_cast<uint32_t>(p0));
+  }
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    const uint64_t p0 = static_cast<uint64_t>(c.x) * Philox::M0;
+    const uint64_t p1 = static_cast<uint64_t>(c.z) * Philox::M1;
+    c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ P.k0[r], static_cast<uint32_t>(p1),
+                   static_cast<uint32_t>(p0 >> 32) ^ c.w ^ P.k1[r], static_cast<uint32_t>(p0));
+  }
+  return c;
+}
+
 // Unit-variance variates z[0..NMOM-1] (moments a = 1..NMOM) of one site.
 // Call j has counter (site, lattice_id, t_lo, t_hi * 8 + j); moment 4j + k + 1
 // takes word k.  Gaussian: Box-Muller on the word pairs (0,1) and (2,3).
 template <typename R, int NMOM>
-__host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, uint32_t lattice_id, uint32_t t_lo,
-                                              uint32_t t_hi8, uint32_t key0, uint32_t key1, int dist) {
+__host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, const PhiloxStep &P, int dist) {
   constexpr int NCALL = (NMOM + 3) / 4;
+  const uint64_t sp = static_cast<uint64_t>(site) * Philox::M0;
+  const uint32_t s_hi = static_cast<uint32_t>(sp >> 32), s_lo = static_cast<uint32_t>(sp);
 #pragma unroll
   for (int j = 0; j < NCALL; ++j) {
-    const uint4 r = philox4x32_10(make_uint4(site, lattice_id, t_lo, t_hi8 | uint32_t(j)), key0, key1);
+    const uint4 r = philox_site(s_hi, s_lo, P, j);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
     if (dist == kGaussian) {
 #pragma unroll

@@ -6,6 +6,8 @@
 
 #include <string>
 
+#include "device.cuh"
+
 #define LBFD_MAX_MODES_DEV 16
 
 namespace lbfd {
@@ -20,9 +22,7 @@ struct StepArgs {
   double rho_eq;       // density of the global-noise variant
   int32_t noise_mode;  // kNoiseLocal / kNoiseGlobal / kNoiseOff
   int32_t noise_dist;  // kGaussian / kUniform
-  uint32_t key0, key1; // Philox key (seed)
-  uint32_t lattice_id; // Philox counter word 1
-  uint32_t t_lo, t_hi8; // Philox counter words 2 and 3 (t_hi * 8; the call index is OR-ed in)
+  PhiloxStep ph;       // Philox key and counter words of this step (seed, lattice id, t)
 };
 
 // One step of eq. LB from src to dst (pull streaming, two buffers).
@@ -43,9 +43,8 @@ cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx
                            double *j, cudaStream_t stream);
 
 // Noise variates of sites [site0, site0 + nsites) at step t into z[site][moment] (FP64).
-cudaError_t launch_noise_draw(int precision, int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id,
-                              uint32_t t_lo, uint32_t t_hi8, int64_t site0, int64_t nsites, int nmom, double *z,
-                              cudaStream_t stream);
+cudaError_t launch_noise_draw(int precision, int dist, const PhiloxStep &ph, int64_t site0, int64_t nsites, int nmom,
+                              double *z, cudaStream_t stream);
 
 // Box-Muller pairs of given Philox words: words[2k], words[2k+1] -> z[2k], z[2k+1].
 cudaError_t launch_box_muller_probe(int precision, const uint32_t *words, int64_t npairs, double *z,

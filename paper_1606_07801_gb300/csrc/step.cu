@@ -55,9 +55,9 @@ __global__ void __launch_bounds__(256) k_step(const R *__restrict__ src, R *__re
   static_for<Q>([&](auto I) { T[decltype(I)::value] = R(0); });
   if (a.noise_mode != kNoiseOff) {
     const R rho_n = a.noise_mode == kNoiseLocal ? (rho > R(0) ? rho : R(0)) : static_cast<R>(a.rho_eq);
-    sigma = Math<R>::sqrt(rho_n * static_cast<R>(a.noise_var));
+    sigma = noise_amplitude<R>(rho_n * static_cast<R>(a.noise_var));
     R zz[Q - 1];
-    draw_variates<R, Q - 1>(zz, s, a.lattice_id, a.t_lo, a.t_hi8, a.key0, a.key1, a.noise_dist);
+    draw_variates<R, Q - 1>(zz, s, a.ph, a.noise_dist);
     NoiseTransform<LAT, R>::apply(zz, T);
   }
 
@@ -267,43 +267,41 @@ cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx
 // Noise probe: the variates the step kernel draws, for checks of the RNG
 // ---------------------------------------------------------------------------
 template <typename R, int NMOM>
-__global__ void k_noise_draw(int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id, uint32_t t_lo, uint32_t t_hi8,
-                             int64_t site0, int64_t nsites, double *__restrict__ out) {
+__global__ void k_noise_draw(int dist, const PhiloxStep ph, int64_t site0, int64_t nsites, double *__restrict__ out) {
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nsites;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     R z[NMOM];
-    draw_variates<R, NMOM>(z, static_cast<uint32_t>(site0 + k), lattice_id, t_lo, t_hi8, key0, key1, dist);
+    draw_variates<R, NMOM>(z, static_cast<uint32_t>(site0 + k), ph, dist);
 #pragma unroll
     for (int a = 0; a < NMOM; ++a) out[k * NMOM + a] = static_cast<double>(z[a]);
   }
 }
 
 template <typename R, int NMOM>
-static cudaError_t noise_t(int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id, uint32_t t_lo, uint32_t t_hi8,
-                           int64_t site0, int64_t nsites, double *z, cudaStream_t stream) {
+static cudaError_t noise_t(int dist, const PhiloxStep &ph, int64_t site0, int64_t nsites, double *z,
+                           cudaStream_t stream) {
   const int64_t blocks = (nsites + 255) / 256;
   const int grid = static_cast<int>(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
-  k_noise_draw<R, NMOM><<<grid, 256, 0, stream>>>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z);
+  k_noise_draw<R, NMOM><<<grid, 256, 0, stream>>>(dist, ph, site0, nsites, z);
   return cudaGetLastError();
 }
 
 template <typename R>
-static cudaError_t noise_p(int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id, uint32_t t_lo, uint32_t t_hi8,
-                           int64_t site0, int64_t nsites, int nmom, double *z, cudaStream_t stream) {
+static cudaError_t noise_p(int dist, const PhiloxStep &ph, int64_t site0, int64_t nsites, int nmom, double *z,
+                           cudaStream_t stream) {
   switch (nmom) {
-    case 2: return noise_t<R, 2>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
-    case 4: return noise_t<R, 4>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
-    case 8: return noise_t<R, 8>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
-    case 18: return noise_t<R, 18>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, z, stream);
+    case 2: return noise_t<R, 2>(dist, ph, site0, nsites, z, stream);
+    case 4: return noise_t<R, 4>(dist, ph, site0, nsites, z, stream);
+    case 8: return noise_t<R, 8>(dist, ph, site0, nsites, z, stream);
+    case 18: return noise_t<R, 18>(dist, ph, site0, nsites, z, stream);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_noise_draw(int precision, int dist, uint32_t key0, uint32_t key1, uint32_t lattice_id,
-                              uint32_t t_lo, uint32_t t_hi8, int64_t site0, int64_t nsites, int nmom, double *z,
-                              cudaStream_t stream) {
-  return precision == 1 ? noise_p<double>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, nmom, z, stream)
-                        : noise_p<float>(dist, key0, key1, lattice_id, t_lo, t_hi8, site0, nsites, nmom, z, stream);
+cudaError_t launch_noise_draw(int precision, int dist, const PhiloxStep &ph, int64_t site0, int64_t nsites, int nmom,
+                              double *z, cudaStream_t stream) {
+  return precision == 1 ? noise_p<double>(dist, ph, site0, nsites, nmom, z, stream)
+                        : noise_p<float>(dist, ph, site0, nsites, nmom, z, stream);
 }
 
 // Box-Muller on given word pairs (edge cases of the uniform grid)

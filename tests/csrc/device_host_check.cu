@@ -19,7 +19,8 @@ static void transform_t(const double *z, double *T) {
 template <typename R, int NMOM>
 static void variates_t(int dist, uint64_t seed, uint32_t lid, uint32_t site, uint64_t t, double *z) {
   R zz[NMOM];
-  draw_variates<R, NMOM>(zz, site, lid, uint32_t(t), uint32_t(t >> 32) << 3, uint32_t(seed), uint32_t(seed >> 32), dist);
+  const PhiloxStep P = make_philox_step(seed, lid, t);
+  draw_variates<R, NMOM>(zz, site, P, dist);
   for (int a = 0; a < NMOM; ++a) z[a] = static_cast<double>(zz[a]);
 }
 
@@ -39,6 +40,15 @@ int dhc_variates(int f64, int nmom, int dist, uint64_t seed, uint32_t lid, uint3
   if (nmom == 8) { f64 ? variates_t<double, 8>(dist, seed, lid, site, t, z) : variates_t<float, 8>(dist, seed, lid, site, t, z); return 0; }
   if (nmom == 18) { f64 ? variates_t<double, 18>(dist, seed, lid, site, t, z) : variates_t<float, 18>(dist, seed, lid, site, t, z); return 0; }
   return -1;
+}
+
+// The step kernel's per-site Philox (host-precomputed uniform parts).
+int dhc_philox_site(uint64_t seed, uint32_t lid, uint64_t t, uint32_t site, int j, uint32_t *out) {
+  const PhiloxStep P = make_philox_step(seed, lid, t);
+  const uint64_t sp = uint64_t(site) * Philox::M0;
+  uint4 r = philox_site(uint32_t(sp >> 32), uint32_t(sp), P, j);
+  out[0] = r.x; out[1] = r.y; out[2] = r.z; out[3] = r.w;
+  return 0;
 }
 
 int dhc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {

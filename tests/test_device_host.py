@@ -30,7 +30,26 @@ def dhc(tmp_path_factory):
     lib.dhc_variates.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32,
                                  ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p]
     lib.dhc_philox.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.dhc_philox_site.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                    ctypes.c_void_p]
     return lib
+
+
+def test_step_philox_equals_the_definition(orc, dhc):
+    """The kernel's Philox (rounds 0-2 partly precomputed per step) equals
+    Philox4x32-10 on the counter (site, lattice id, t_lo, t_hi*8 + j)."""
+    g = np.random.default_rng(11)
+    for _ in range(400):
+        seed = int(g.integers(0, 2**64, dtype=np.uint64))
+        lid = int(g.integers(0, 2**32))
+        t = int(g.integers(0, 2**40))
+        site = int(g.integers(0, 2**32))
+        j = int(g.integers(0, 8))
+        out = np.zeros(4, dtype=np.uint32)
+        dhc.dhc_philox_site(seed, lid, t, site, j, out.ctypes.data)
+        ctr = [site, lid, t & 0xFFFFFFFF, (((t >> 32) << 3) | j) & 0xFFFFFFFF]
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        assert out.tolist() == orc.philox4x32_10(ctr, key).tolist()
 
 
 def test_device_philox_known_answers(dhc):
