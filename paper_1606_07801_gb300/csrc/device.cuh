@@ -368,30 +368,73 @@ __host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t si
 
 // ---------------------------------------------------------------------------
 // Noise back-transform T_i = sum_{a >= 1} m_i^a z^a (the f-space noise is
-// xi_i = w_i sigma T_i).
+// xi_i = w_i sigma T_i).  kWeighted tells whether apply() returns w_i T_i.
 // ---------------------------------------------------------------------------
+// Index of the velocity -v_i, and the parity of basis row a under v -> -v
+// (the parity of its seed monomial's degree; Gram-Schmidt over a symmetric
+// velocity set never mixes the two parities, which make_basis's table obeys
+// exactly: checked below).
+template <int LAT>
+__host__ __device__ constexpr int partner(int i) {
+  using L = Lattice<LAT>;
+  for (int j = 0; j < L::Q; ++j)
+    if (L::v(j, 0) == -L::v(i, 0) && L::v(j, 1) == -L::v(i, 1) && L::v(j, 2) == -L::v(i, 2)) return j;
+  return -1;
+}
+template <int LAT>
+__host__ __device__ constexpr int row_parity(int a) {
+  using L = Lattice<LAT>;
+  return (L::mono(a, 0) + L::mono(a, 1) + L::mono(a, 2)) & 1;
+}
+template <int LAT>
+constexpr bool basis_has_parity() {
+  constexpr int Q = Lattice<LAT>::Q;
+  for (int a = 0; a < Q; ++a)
+    for (int i = 0; i < Q; ++i) {
+      const double m = kBasisTable<LAT>.m[a][i], mp = kBasisTable<LAT>.m[a][partner<LAT>(i)];
+      if (partner<LAT>(i) < 0 || mp != (row_parity<LAT>(a) ? -m : m)) return false;
+    }
+  return true;
+}
+
+// Generic transform, weighted: wT_i = w_i sum_{a>=1} m_i^a z^a.  The
+// constants w_i m_i^a are folded at compile time and zeros skipped; each pair
+// (i, -i) shares its even part E and odd part O: wT_i = E + O, wT_-i = E - O.
 template <int LAT, typename R>
 struct NoiseTransform {
-  // generic: the compile-time basis with its zeros skipped
-  __host__ __device__ static __forceinline__ void apply(const R (&z)[Lattice<LAT>::Q - 1], R (&T)[Lattice<LAT>::Q]) {
+  static constexpr bool kWeighted = true;
+  static_assert(basis_has_parity<LAT>(), "basis rows must have definite parity");
+  template <int I, int PAR>
+  __host__ __device__ static __forceinline__ R part(const R (&z)[Lattice<LAT>::Q - 1]) {
+    constexpr int Q = Lattice<LAT>::Q;
+    R acc = R(0);
+    bool first = true;
+    static_for<Q - 1>([&](auto A) {
+      constexpr int a = decltype(A)::value + 1;
+      constexpr double c = kBasis<LAT, a, I> * Lattice<LAT>::w(I);
+      if constexpr (c != 0.0 && (PAR < 0 || row_parity<LAT>(a) == PAR)) {
+        if (first) {
+          acc = R(c) * z[a - 1];
+          first = false;
+        } else {
+          acc = fma(R(c), z[a - 1], acc);
+        }
+      }
+    });
+    return acc;
+  }
+  __host__ __device__ static __forceinline__ void apply(const R (&z)[Lattice<LAT>::Q - 1], R (&wT)[Lattice<LAT>::Q]) {
     constexpr int Q = Lattice<LAT>::Q;
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      R acc = R(0);
-      bool first = true;
-      static_for<Q - 1>([&](auto A) {
-        constexpr int a = decltype(A)::value + 1;
-        constexpr double c = kBasis<LAT, a, i>;
-        if constexpr (c != 0.0) {
-          if (first) {
-            acc = R(c) * z[a - 1];
-            first = false;
-          } else {
-            acc = fma(R(c), z[a - 1], acc);
-          }
-        }
-      });
-      T[i] = acc;
+      constexpr int ip = partner<LAT>(i);
+      if constexpr (ip == i) {
+        wT[i] = part<i, -1>(z);
+      } else if constexpr (i < ip) {
+        const R E = part<i, 0>(z), O = part<i, 1>(z);
+        wT[i] = E + O;
+        wT[ip] = E - O;
+      }
     });
   }
 };
@@ -400,6 +443,7 @@ struct NoiseTransform {
 // 3x3 pass over q followed by a 3x3 pass over p (24 multiply-adds).
 template <typename R>
 struct NoiseTransform<kD2Q9, R> {
+  static constexpr bool kWeighted = false;  // returns T_i; the caller applies w_i
   __host__ __device__ static __forceinline__ void apply(const R (&z)[8], R (&T)[9]) {
     // zeta[p][q] = z^{3p+q}, zeta[0][0] = 0
     const R zeta[3][3] = {{R(0), z[0], z[1]}, {z[2], z[3], z[4]}, {z[5], z[6], z[7]}};
@@ -435,6 +479,7 @@ struct NoiseTransform<kD2Q9, R> {
 // D1Q3: T(0) = -z^2/sqrt2, T(+-1) = +-sqrt3 z^1 + sqrt2 z^2.
 template <typename R>
 struct NoiseTransform<kD1Q3, R> {
+  static constexpr bool kWeighted = false;
   __host__ __device__ static __forceinline__ void apply(const R (&z)[2], R (&T)[3]) {
     T[0] = R(-kInvSqrt2) * z[1];
     const R even = R(kSqrt2) * z[1];

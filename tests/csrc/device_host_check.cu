@@ -7,13 +7,15 @@
 
 using namespace lbfd;
 
+// Returns 1 when the transform folds the weights in (T_i = w_i sum_a ...).
 template <int LAT, typename R>
-static void transform_t(const double *z, double *T) {
+static int transform_t(const double *z, double *T) {
   constexpr int Q = Lattice<LAT>::Q;
   R zz[Q - 1], TT[Q];
   for (int a = 0; a < Q - 1; ++a) zz[a] = static_cast<R>(z[a]);
   NoiseTransform<LAT, R>::apply(zz, TT);
   for (int i = 0; i < Q; ++i) T[i] = static_cast<double>(TT[i]);
+  return NoiseTransform<LAT, R>::kWeighted ? 1 : 0;
 }
 
 template <typename R, int NMOM>
@@ -28,9 +30,9 @@ extern "C" {
 
 int dhc_transform(int lattice, int f64, const double *z, double *T) {
   switch (lattice) {
-    case kD1Q3: f64 ? transform_t<kD1Q3, double>(z, T) : transform_t<kD1Q3, float>(z, T); return 0;
-    case kD2Q9: f64 ? transform_t<kD2Q9, double>(z, T) : transform_t<kD2Q9, float>(z, T); return 0;
-    case kD3Q19: f64 ? transform_t<kD3Q19, double>(z, T) : transform_t<kD3Q19, float>(z, T); return 0;
+    case kD1Q3: return f64 ? transform_t<kD1Q3, double>(z, T) : transform_t<kD1Q3, float>(z, T);
+    case kD2Q9: return f64 ? transform_t<kD2Q9, double>(z, T) : transform_t<kD2Q9, float>(z, T);
+    case kD3Q19: return f64 ? transform_t<kD3Q19, double>(z, T) : transform_t<kD3Q19, float>(z, T);
   }
   return -1;
 }

@@ -64,16 +64,19 @@ def test_device_philox_known_answers(dhc):
 @pytest.mark.parametrize("lat", [lb.D1Q3, lb.D2Q9, lb.D3Q19])
 @pytest.mark.parametrize("f64,tol", [(1, 1e-15), (0, 1e-6)])
 def test_noise_transform_is_the_basis(orc, dhc, lat, f64, tol):
-    """T_i = sum_{a>=1} m_i^a z^a for unit z: the kernel's (factorised or
-    sparse) transform reproduces the oracle's Gram-Schmidt basis."""
+    """T_i = sum_{a>=1} m_i^a z^a for unit z: the kernel's (factorised, or
+    sparse, weighted and parity-split) transform reproduces the oracle's
+    Gram-Schmidt basis (times w_i where the transform folds the weights in)."""
     Q = lb.Q_OF[lat]
     m = orc.basis(lat)
+    _, _, _, w = orc.lattice(lat)
     for a in range(Q - 1):
         z = np.zeros(Q - 1)
         z[a] = 1.0
         T = np.zeros(Q)
-        dhc.dhc_transform(lat, f64, z.ctypes.data, T.ctypes.data)
-        assert np.max(np.abs(T - m[a + 1])) < tol * 4
+        weighted = dhc.dhc_transform(lat, f64, z.ctypes.data, T.ctypes.data)
+        expect = m[a + 1] * w if weighted else m[a + 1]
+        assert np.max(np.abs(T - expect)) < tol * 4
 
 
 @pytest.mark.parametrize("nmom", [2, 8, 18])
