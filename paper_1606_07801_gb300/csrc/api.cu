@@ -237,6 +237,10 @@ int lbfd_step(lbfd_t h, int64_t n) {
   a.inv_tau = 1.0 / o.tau;
   a.noise_var = (2.0 * o.tau - 1.0) / (o.tau * o.tau);
   a.rho_eq = o.rho_mean;
+  a.omega_f = float(a.omega);
+  a.inv_tau_f = float(a.inv_tau);
+  a.noise_var_f = float(a.noise_var);
+  a.rho_eq_f = float(a.rho_eq);
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
   for (int64_t k = 0; k < n; ++k) {

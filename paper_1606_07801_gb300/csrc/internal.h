@@ -20,10 +20,21 @@ struct StepArgs {
   double inv_tau;      // 1/tau
   double noise_var;    // (2 tau - 1)/tau^2: noise variance per unit density
   double rho_eq;       // density of the global-noise variant
+  // the same four in FP32, so FP32 kernels never convert from FP64 on the
+  // device (GB300's FP64 unit is narrow)
+  float omega_f, inv_tau_f, noise_var_f, rho_eq_f;
   int32_t noise_mode;  // kNoiseLocal / kNoiseGlobal / kNoiseOff
   int32_t noise_dist;  // kGaussian / kUniform
   PhiloxStep ph;       // Philox key and counter words of this step (seed, lattice id, t)
 };
+
+// The step parameter in the kernel's precision.
+template <typename R>
+__host__ __device__ __forceinline__ R step_param(double d, float f);
+template <>
+__host__ __device__ __forceinline__ double step_param<double>(double d, float) { return d; }
+template <>
+__host__ __device__ __forceinline__ float step_param<float>(double, float f) { return f; }
 
 // One step of eq. LB from src to dst (pull streaming, two buffers).
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,

@@ -36,15 +36,15 @@ __device__ __forceinline__ void collide_site(R (&f)[Lattice<LAT>::Q], uint32_t s
   R T[Q];
   static_for<Q>([&](auto I) { T[decltype(I)::value] = R(0); });
   if (a.noise_mode != kNoiseOff) {
-    const R rho_n = a.noise_mode == kNoiseLocal ? (rho > R(0) ? rho : R(0)) : static_cast<R>(a.rho_eq);
-    sigma = noise_amplitude<R>(rho_n * static_cast<R>(a.noise_var));
+    const R rho_n = a.noise_mode == kNoiseLocal ? (rho > R(0) ? rho : R(0)) : step_param<R>(a.rho_eq, a.rho_eq_f);
+    sigma = noise_amplitude<R>(rho_n * step_param<R>(a.noise_var, a.noise_var_f));
     R zz[Q - 1];
     draw_variates<R, Q - 1>(zz, s, a.ph, a.noise_dist);
     NoiseTransform<LAT, R>::apply(zz, T);
   }
 
-  const R omega = static_cast<R>(a.omega);
-  const R relaxed = rho * static_cast<R>(a.inv_tau);
+  const R omega = step_param<R>(a.omega, a.omega_f);
+  const R relaxed = rho * step_param<R>(a.inv_tau, a.inv_tau_f);
   // f*_i = (1 - 1/tau) f_i + w_i rho/tau + w_i sigma T_i, with w_i rho/tau and
   // w_i sigma formed once per distinct weight.  The moving populations are
   // written first; the rest population takes what mass conservation leaves,
