@@ -124,8 +124,14 @@ struct VecOf<double, 2> {
   __device__ static __forceinline__ T make(const double (&o)[2]) { return make_double2(o[0], o[1]); }
 };
 
+// Minimum resident blocks per SM asked of the register allocator for the
+// vector kernel (a build-time tuning knob; 1 leaves the allocator free).
+#ifndef LBFD_STEP_MIN_BLOCKS
+#define LBFD_STEP_MIN_BLOCKS 1
+#endif
+
 template <int LAT, typename R, int VX>
-__global__ void __launch_bounds__(256) k_step_vec(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
+__global__ void __launch_bounds__(256, LBFD_STEP_MIN_BLOCKS) k_step_vec(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
   using L = Lattice<LAT>;
   using V = VecOf<R, VX>;
   constexpr int Q = L::Q;
