@@ -338,9 +338,10 @@ __host__ __device__ __forceinline__ uint4 philox_site(uint32_t s_hi, uint32_t s_
 
 // Unit-variance variates z[0..NMOM-1] (moments a = 1..NMOM) of one site.
 // Call j has counter (site, lattice_id, t_lo, t_hi * 8 + j); moment 4j + k + 1
-// takes word k.  Gaussian: Box-Muller on the word pairs (0,1) and (2,3).
-template <typename R, int NMOM>
-__host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, const PhiloxStep &P, int dist) {
+// takes word k.  GAUSS: Box-Muller on the word pairs (0,1) and (2,3);
+// otherwise flat variates sqrt(3) (2u - 1).
+template <typename R, int NMOM, bool GAUSS>
+__host__ __device__ __forceinline__ void draw_variates_t(R (&z)[NMOM], uint32_t site, const PhiloxStep &P) {
   constexpr int NCALL = (NMOM + 3) / 4;
   const uint64_t sp = static_cast<uint64_t>(site) * Philox::M0;
   const uint32_t s_hi = static_cast<uint32_t>(sp >> 32), s_lo = static_cast<uint32_t>(sp);
@@ -348,7 +349,7 @@ __host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t si
   for (int j = 0; j < NCALL; ++j) {
     const uint4 r = philox_site(s_hi, s_lo, P, j);
     const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-    if (dist == kGaussian) {
+    if constexpr (GAUSS) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         if (4 * j + 2 * p < NMOM) {
@@ -364,6 +365,14 @@ __host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t si
         if (4 * j + k < NMOM) z[4 * j + k] = R(kSqrt3) * (R(2) * unit24<R>(w[k]) - R(1));
     }
   }
+}
+
+template <typename R, int NMOM>
+__host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, const PhiloxStep &P, int dist) {
+  if (dist == kGaussian)
+    draw_variates_t<R, NMOM, true>(z, site, P);
+  else
+    draw_variates_t<R, NMOM, false>(z, site, P);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,11 @@ __host__ __device__ __forceinline__ double step_param<double>(double d, float) {
 template <>
 __host__ __device__ __forceinline__ float step_param<float>(double, float f) { return f; }
 
+// Per-lattice step launchers (one translation unit each).
+cudaError_t launch_step_d1q3(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream);
+cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream);
+cudaError_t launch_step_d3q19(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream);
+
 // One step of eq. LB from src to dst (pull streaming, two buffers).
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
                         cudaStream_t stream);
