@@ -117,14 +117,21 @@ struct VecOf<double, 2> {
   __device__ static __forceinline__ T make(const double (&o)[2]) { return make_double2(o[0], o[1]); }
 };
 
-// Minimum resident blocks per SM asked of the register allocator for the
-// vector kernel (a build-time tuning knob; 1 leaves the allocator free).
-#ifndef LBFD_STEP_MIN_BLOCKS
-#define LBFD_STEP_MIN_BLOCKS 1
+// Minimum resident 256-thread blocks per SM asked of the register allocator
+// for the vector kernel.  Measured on GB300 (D2Q9 2048^2 and D3Q19 256^3,
+// FP32, local Gaussian noise): 4 blocks (<= 64 registers) beats both the
+// unconstrained allocation, which drops D3Q19 to one block per SM, and
+// tighter caps, which spill.  FP64 kernels need more registers: 2.
+template <int LAT, typename R>
+constexpr int step_min_blocks() {
+#ifdef LBFD_STEP_MIN_BLOCKS_D3Q19
+  if (LAT == kD3Q19 && sizeof(R) == 4) return LBFD_STEP_MIN_BLOCKS_D3Q19;
 #endif
+  return sizeof(R) == 4 ? 4 : 2;
+}
 
 template <int LAT, typename R, int VX, int NOISE>
-__global__ void __launch_bounds__(256, LBFD_STEP_MIN_BLOCKS) k_step_vec(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
+__global__ void __launch_bounds__(256, step_min_blocks<LAT, R>()) k_step_vec(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
   using L = Lattice<LAT>;
   using V = VecOf<R, VX>;
   constexpr int Q = L::Q;
@@ -184,8 +191,8 @@ inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &blo
 }
 
 // Sites per thread of the step kernel (a tuning knob; results do not depend
-// on it).  LBFD_STEP_VX = 1, 2 or 4 overrides the default: 4 for FP32 and
-// 2 for FP64 when Lx allows, else 1.
+// on it).  LBFD_STEP_VX = 1, 2 or 4 overrides the default of 2 when Lx
+// allows (else 1).
 inline int step_vx_override() {
   static int v = [] {
     const char *e = getenv("LBFD_STEP_VX");
@@ -198,7 +205,7 @@ inline int step_vx_override() {
 template <int LAT, typename R, int NOISE>
 cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
   int vx = step_vx_override();
-  if (vx == 0) vx = sizeof(R) == 4 ? 4 : 2;
+  if (vx == 0) vx = 2;
   if (sizeof(R) == 8 && vx == 4) vx = 2;
   while (vx > 1 && a.Lx % vx != 0) vx /= 2;
   dim3 grid, block;
