@@ -118,16 +118,15 @@ struct VecOf<double, 2> {
 };
 
 // Minimum resident 256-thread blocks per SM asked of the register allocator
-// for the vector kernel.  Measured on GB300 (D2Q9 2048^2 and D3Q19 256^3,
-// FP32, local Gaussian noise): 4 blocks (<= 64 registers) beats both the
-// unconstrained allocation, which drops D3Q19 to one block per SM, and
-// tighter caps, which spill.  FP64 kernels need more registers: 2.
+// for the vector kernel.  Measured on GB300 (FP32, local Gaussian noise,
+// two sites per thread): D2Q9 2048^2 is fastest at 4 blocks (<= 64
+// registers), D3Q19 256^3 at 3 (<= 85 registers); the unconstrained
+// allocation leaves D3Q19 one block per SM, and tighter caps spill.  FP64
+// kernels need more registers: 2.
 template <int LAT, typename R>
 constexpr int step_min_blocks() {
-#ifdef LBFD_STEP_MIN_BLOCKS_D3Q19
-  if (LAT == kD3Q19 && sizeof(R) == 4) return LBFD_STEP_MIN_BLOCKS_D3Q19;
-#endif
-  return sizeof(R) == 4 ? 4 : 2;
+  if (sizeof(R) != 4) return 2;
+  return LAT == kD3Q19 ? 3 : 4;
 }
 
 template <int LAT, typename R, int VX, int NOISE>
