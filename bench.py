@@ -40,7 +40,18 @@ WORKLOADS = {
                   name="D3Q19 FP32 periodic 256^3, tau=1.0, rho_mean=50, local Gaussian noise, uniform start"),
     "d1q3": dict(lattice=0, dims=(256,), tau=1.0, rho=10.0, precision=1,
                  name="D1Q3 FP64 periodic L=256, tau=1.0, rho_mean=10, local Gaussian noise, sine start"),
+    "d3q19_f16": dict(lattice=2, dims=(256, 256, 256), tau=1.0, rho=50.0, precision=2,
+                      name="D3Q19 periodic 256^3, tau=1.0, rho_mean=50, FP32 arithmetic, FP16 storage of "
+                           "f_i - w_i rho_mean, local Gaussian noise, uniform start"),
+    "d3q19_bf16": dict(lattice=2, dims=(256, 256, 256), tau=1.0, rho=50.0, precision=3,
+                       name="D3Q19 periodic 256^3, tau=1.0, rho_mean=50, FP32 arithmetic, BF16 storage of "
+                            "f_i - w_i rho_mean, local Gaussian noise, uniform start"),
+    "d2q9_f16": dict(lattice=1, dims=(2048, 2048), tau=0.8, rho=100.0, precision=2,
+                     name="D2Q9 periodic 2048x2048, tau=0.8, rho_mean=100, FP32 arithmetic, FP16 storage of "
+                          "f_i - w_i rho_mean, local Gaussian noise, uniform start"),
 }
+ELEM_BYTES = {0: 4, 1: 8, 2: 2, 3: 2}
+DTYPE_NAME = {0: "f32", 1: "f64", 2: "f32 (f16 storage)", 3: "f32 (bf16 storage)"}
 Q_OF = {0: 3, 1: 9, 2: 19}
 KERNEL_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_07801_gb300/csrc/device.cuh",
                   "paper_1606_07801_gb300/csrc/step_d2q9.cu", "paper_1606_07801_gb300/csrc/step_d3q19.cu"]
@@ -239,7 +250,7 @@ def main():
 
     lat, dims, tau, rho, prec = wl["lattice"], wl["dims"], wl["tau"], wl["rho"], wl["precision"]
     Q, N = Q_OF[lat], int(np.prod(dims))
-    elem = 8 if prec == 1 else 4
+    elem = ELEM_BYTES[prec]
     stream = torch.cuda.Stream()
     init = lb.INIT_SINE if args.workload == "d1q3" else lb.INIT_UNIFORM
     sim = lb.Simulation(lat, dims, tau, rho, 1 + rank, precision=prec, lattice_id=rank, stream=stream,
@@ -279,7 +290,7 @@ def main():
 
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device (pinned), one step runs, the density comes back
-    h_f = torch.empty(Q * N, dtype=torch.float64 if prec == 1 else torch.float32).pin_memory()
+    h_f = torch.empty(Q * N * elem, dtype=torch.uint8).pin_memory()
     h_rho = torch.empty(N, dtype=torch.float64).pin_memory()
     lb.abi.lbfd_get_f_raw(sim.h, h_f.data_ptr())
     barrier()
@@ -303,7 +314,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == 1 else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": DTYPE_NAME[prec], "data": "synthetic",
             "config": {"workload": wl["name"], "sites": N, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2: %.0f MB per population buffer vs 129 MB L2" % (Q * N * elem / 1e6),
                        "per_sim": "one lattice per GPU, one k_step launch per time step"},

@@ -53,8 +53,10 @@ extern "C" {
                         (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1);  w = 1/3, 1/18 x6, 1/36 x12 */
 
 /* ---- arithmetic and storage ------------------------------------------ */
-#define LBFD_F32 0 /* FP32 arithmetic and storage (default) */
-#define LBFD_F64 1 /* FP64 arithmetic and storage */
+#define LBFD_F32 0      /* FP32 arithmetic and storage (default) */
+#define LBFD_F64 1      /* FP64 arithmetic and storage */
+#define LBFD_F32_F16 2  /* FP32 arithmetic; f_i - w_i rho_mean stored as IEEE binary16 (round to nearest even) */
+#define LBFD_F32_BF16 3 /* FP32 arithmetic; f_i - w_i rho_mean stored as bfloat16 (round to nearest even) */
 
 /* ---- noise ------------------------------------------------------------- */
 #define LBFD_NOISE_LOCAL 0  /* variance from the local density, clamped at 0 (eq. xilocal) */
@@ -74,7 +76,7 @@ extern "C" {
 /* Options of lbfd_create_ex.  Fill with lbfd_options_init, then override. */
 typedef struct lbfd_options {
     int32_t lattice;    /* LBFD_D1Q3 / LBFD_D2Q9 / LBFD_D3Q19 */
-    int32_t precision;  /* LBFD_F32 / LBFD_F64 */
+    int32_t precision;  /* LBFD_F32 / LBFD_F64 / LBFD_F32_F16 / LBFD_F32_BF16 */
     int32_t noise_mode; /* LBFD_NOISE_* */
     int32_t noise_dist; /* LBFD_GAUSSIAN / LBFD_UNIFORM */
     int32_t init;       /* LBFD_INIT_* */
@@ -88,7 +90,7 @@ typedef struct lbfd_options {
     uint64_t seed;      /* Philox key */
     void *stream;       /* cudaStream_t the handle works on; NULL = legacy default stream */
     void *f_dev[2];     /* optional caller-owned device buffers, each Q*N values of the
-                           precision's type; both or neither.  Never freed by the library. */
+                           storage format; both or neither.  Never freed by the library. */
     int32_t n_modes;    /* structure-factor wave vectors sampled by lbfd_sample */
     int32_t modes[LBFD_MAX_MODES][3];
     int32_t reserved[8];
@@ -143,7 +145,8 @@ int lbfd_set_t(lbfd_t h, int64_t t);
 int lbfd_get_f(lbfd_t h, double *f_host);
 int lbfd_set_f(lbfd_t h, const double *f_host);
 
-/* Same in the storage type (float for LBFD_F32, double for LBFD_F64), with
+/* Same in the storage format (float for LBFD_F32, double for LBFD_F64, the
+ * 16-bit deviation f_i - w_i rho_mean for LBFD_F32_F16 / LBFD_F32_BF16), with
  * no conversion: one cudaMemcpyAsync of Q*N values, then a stream sync.
  * Pinned host memory makes these run at full link speed. */
 int lbfd_get_f_raw(lbfd_t h, void *f_host);
@@ -169,7 +172,7 @@ int lbfd_reset_obs(lbfd_t h);
 /* Reads the accumulators and the current mass.  Synchronous. */
 int lbfd_observables(lbfd_t h, lbfd_obs *obs);
 
-/* Static facts of a handle: Q, D, N (sites), bytes per stored value. */
+/* Static facts of a handle: Q, D, N (sites), bytes per stored value (8, 4 or 2). */
 int lbfd_query(lbfd_t h, int32_t *Q, int32_t *D, int64_t *N, int32_t *value_bytes);
 
 /* Device buffer holding the stored state g_i(x) = f_i(x + v_i, t) (layout

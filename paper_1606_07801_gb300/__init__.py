@@ -13,12 +13,14 @@ import ctypes
 import numpy as np
 
 from . import build as _build_mod
-from .lbfd import (D1Q3, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F64, GAUSSIAN,
+from .lbfd import (D1Q3, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
+                   F64, GAUSSIAN,
                    INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL, NOISE_LOCAL, NOISE_OFF, OK,
                    Q_OF, UNIFORM, LbfdError, Options, load)
 from . import lbfd as abi
 
 __all__ = ["Simulation", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
+           "F32_F16", "F32_BF16",
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
            "INIT_NONE", "Q_OF", "D_OF"]
 
@@ -64,7 +66,7 @@ class Simulation:
             import torch
 
             q, n = Q_OF[lattice], int(np.prod(d))
-            dt = torch.float64 if precision == F64 else torch.float32
+            dt = {F64: torch.float64, F32: torch.float32, F32_F16: torch.float16, F32_BF16: torch.bfloat16}[precision]
             dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
             bufs = [torch.empty(q * n, dtype=dt, device=dev) for _ in range(2)]
             o.f_dev[0], o.f_dev[1] = bufs[0].data_ptr(), bufs[1].data_ptr()

@@ -91,6 +91,25 @@ static cudaError_t store_f_from_spare(lbfd_sim *h) {
                       int32_t(o.dims[2]), -1, h->stream);
 }
 
+// Host conversion between FP64 populations and the storage format (16-bit
+// formats hold f_i - w_i rho_mean).
+template <typename S>
+static void decode_host(const S *raw, double *f, int lattice, int64_t N, double rho_mean) {
+  int Q = 0, D = 0, v[LBFD_MAX_Q * 3];
+  double w[LBFD_MAX_Q];
+  lattice_table(lattice, &Q, &D, v, w);
+  for (int i = 0; i < Q; ++i)
+    for (int64_t s = 0; s < N; ++s) f[i * N + s] = Store<S>::getd(raw[i * N + s], w[i] * rho_mean);
+}
+template <typename S>
+static void encode_host(const double *f, S *raw, int lattice, int64_t N, double rho_mean) {
+  int Q = 0, D = 0, v[LBFD_MAX_Q * 3];
+  double w[LBFD_MAX_Q];
+  lattice_table(lattice, &Q, &D, v, w);
+  for (int i = 0; i < Q; ++i)
+    for (int64_t s = 0; s < N; ++s) raw[i * N + s] = Store<S>::putd(f[i * N + s], w[i] * rho_mean);
+}
+
 extern "C" {
 
 int lbfd_options_init(lbfd_options *o) {
@@ -111,7 +130,7 @@ int lbfd_options_init(lbfd_options *o) {
 
 static int validate(const lbfd_options *o) {
   if (o->lattice < LBFD_D1Q3 || o->lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
-  if (o->precision != LBFD_F32 && o->precision != LBFD_F64) return fail(LBFD_EINVAL, "unknown precision");
+  if (o->precision < LBFD_F32 || o->precision > LBFD_F32_BF16) return fail(LBFD_EINVAL, "unknown precision");
   if (o->noise_mode < LBFD_NOISE_LOCAL || o->noise_mode > LBFD_NOISE_OFF) return fail(LBFD_EINVAL, "unknown noise mode");
   if (o->noise_dist != LBFD_GAUSSIAN && o->noise_dist != LBFD_UNIFORM) return fail(LBFD_EINVAL, "unknown noise distribution");
   if (o->init < LBFD_INIT_UNIFORM || o->init > LBFD_INIT_NONE) return fail(LBFD_EINVAL, "unknown init");
@@ -162,7 +181,7 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   h->Q = lattice_q(opt->lattice);
   h->D = lattice_dims(opt->lattice);
   h->N = opt->dims[0] * opt->dims[1] * opt->dims[2];
-  h->elem = opt->precision == LBFD_F64 ? 8 : 4;
+  h->elem = storage_bytes(opt->precision);
   h->stream = static_cast<cudaStream_t>(opt->stream);
   for (int m = 0; m < opt->n_modes; ++m)
     for (int k = 0; k < 3; ++k) h->modes_host[m][k] = opt->modes[m][k];
@@ -293,29 +312,39 @@ int lbfd_set_f_raw(lbfd_t h, const void *f_host) {
 
 int lbfd_get_f(lbfd_t h, double *f_host) {
   if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_get_f: null argument");
-  if (h->elem == 8) return lbfd_get_f_raw(h, f_host);
-  std::vector<float> tmp;
+  if (h->opt.precision == LBFD_F64) return lbfd_get_f_raw(h, f_host);
+  std::vector<uint8_t> tmp;
   try {
-    tmp.resize(size_t(h->Q) * h->N);
+    tmp.resize(size_t(h->Q) * h->N * h->elem);
   } catch (...) {
     return fail(LBFD_ENOMEM, "lbfd_get_f: host staging allocation failed");
   }
   int rc = lbfd_get_f_raw(h, tmp.data());
   if (rc) return rc;
-  for (size_t k = 0; k < tmp.size(); ++k) f_host[k] = double(tmp[k]);
+  const lbfd_options &o = h->opt;
+  dispatch_storage(o.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    decode_host<S>(reinterpret_cast<const S *>(tmp.data()), f_host, o.lattice, h->N, o.rho_mean);
+    return cudaSuccess;
+  });
   return LBFD_OK;
 }
 
 int lbfd_set_f(lbfd_t h, const double *f_host) {
   if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_set_f: null argument");
-  if (h->elem == 8) return lbfd_set_f_raw(h, f_host);
-  std::vector<float> tmp;
+  if (h->opt.precision == LBFD_F64) return lbfd_set_f_raw(h, f_host);
+  std::vector<uint8_t> tmp;
   try {
-    tmp.resize(size_t(h->Q) * h->N);
+    tmp.resize(size_t(h->Q) * h->N * h->elem);
   } catch (...) {
     return fail(LBFD_ENOMEM, "lbfd_set_f: host staging allocation failed");
   }
-  for (size_t k = 0; k < tmp.size(); ++k) tmp[k] = float(f_host[k]);
+  const lbfd_options &o = h->opt;
+  dispatch_storage(o.precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    encode_host<S>(f_host, reinterpret_cast<S *>(tmp.data()), o.lattice, h->N, o.rho_mean);
+    return cudaSuccess;
+  });
   return lbfd_set_f_raw(h, tmp.data());
 }
 
@@ -325,7 +354,7 @@ int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev) {
   const lbfd_options &o = h->opt;
   LBFD_CU(materialize_f(h));
   LBFD_CU(launch_moments(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                         int32_t(o.dims[2]), rho_dev, j_dev, h->stream));
+                         int32_t(o.dims[2]), o.rho_mean, rho_dev, j_dev, h->stream));
   return LBFD_OK;
 }
 
@@ -346,7 +375,7 @@ int lbfd_mass(lbfd_t h, double *mass) {
   if (!h || !mass) return fail(LBFD_EINVAL, "lbfd_mass: null argument");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
-  LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, h->partials, h->d_mass, h->stream));
+  LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, o.rho_mean, h->partials, h->d_mass, h->stream));
   LBFD_CU(cudaMemcpyAsync(mass, h->d_mass, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   return LBFD_OK;

@@ -9,8 +9,11 @@
 //   - noise xi^a, a >= 1, variance rho (2 tau - 1)/tau^2 (eqs. xiglobal, xilocal)
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace lbfd {
@@ -18,6 +21,68 @@ namespace lbfd {
 enum LatticeId : int { kD1Q3 = 0, kD2Q9 = 1, kD3Q19 = 2 };
 enum NoiseMode : int { kNoiseLocal = 0, kNoiseGlobal = 1, kNoiseOff = 2 };
 enum NoiseDist : int { kGaussian = 0, kUniform = 1 };
+
+// ---------------------------------------------------------------------------
+// Storage formats of the populations.  FP32 and FP64 store f_i itself.  The
+// 16-bit formats store the deviation f_i - w_i rho_mean (rounded to nearest
+// even), and all arithmetic on them is FP32: get() decodes, put() encodes,
+// wr = w_i rho_mean.
+// ---------------------------------------------------------------------------
+enum StorageId : int { kStoreF32 = 0, kStoreF64 = 1, kStoreF16 = 2, kStoreBF16 = 3 };
+
+template <typename S>
+struct Store;
+template <>
+struct Store<float> {
+  using R = float;
+  static constexpr bool kDeviation = false;
+  __host__ __device__ static __forceinline__ float get(float v, float) { return v; }
+  __host__ __device__ static __forceinline__ float put(float f, float) { return f; }
+  __host__ __device__ static __forceinline__ double getd(float v, double) { return v; }
+  __host__ __device__ static __forceinline__ float putd(double f, double) { return static_cast<float>(f); }
+};
+template <>
+struct Store<double> {
+  using R = double;
+  static constexpr bool kDeviation = false;
+  __host__ __device__ static __forceinline__ double get(double v, double) { return v; }
+  __host__ __device__ static __forceinline__ double put(double f, double) { return f; }
+  __host__ __device__ static __forceinline__ double getd(double v, double) { return v; }
+  __host__ __device__ static __forceinline__ double putd(double f, double) { return f; }
+};
+template <>
+struct Store<__half> {
+  using R = float;
+  static constexpr bool kDeviation = true;
+  __host__ __device__ static __forceinline__ float get(__half v, float wr) { return __half2float(v) + wr; }
+  __host__ __device__ static __forceinline__ __half put(float f, float wr) { return __float2half_rn(f - wr); }
+  __host__ __device__ static __forceinline__ double getd(__half v, double wr) {
+    return static_cast<double>(__half2float(v)) + wr;
+  }
+  __host__ __device__ static __forceinline__ __half putd(double f, double wr) {
+    return __float2half_rn(static_cast<float>(f - wr));
+  }
+};
+template <>
+struct Store<__nv_bfloat16> {
+  using R = float;
+  static constexpr bool kDeviation = true;
+  __host__ __device__ static __forceinline__ float get(__nv_bfloat16 v, float wr) { return __bfloat162float(v) + wr; }
+  __host__ __device__ static __forceinline__ __nv_bfloat16 put(float f, float wr) {
+    return __float2bfloat16_rn(f - wr);
+  }
+  __host__ __device__ static __forceinline__ double getd(__nv_bfloat16 v, double wr) {
+    return static_cast<double>(__bfloat162float(v)) + wr;
+  }
+  __host__ __device__ static __forceinline__ __nv_bfloat16 putd(double f, double wr) {
+    return __float2bfloat16_rn(static_cast<float>(f - wr));
+  }
+};
+
+template <typename T>
+struct Tag {
+  using type = T;
+};
 
 // ---------------------------------------------------------------------------
 // Compile-time iteration

@@ -28,6 +28,35 @@ struct StepArgs {
   PhiloxStep ph;       // Philox key and counter words of this step (seed, lattice id, t)
 };
 
+// Calls f(std::integral_constant<int, LAT>, Tag<S>) for a lattice id and a
+// storage id (0 FP32, 1 FP64, 2 FP16 deviations, 3 BF16 deviations).
+template <class F>
+inline cudaError_t dispatch_storage(int precision, F &&f) {
+  switch (precision) {
+    case kStoreF32: return f(Tag<float>{});
+    case kStoreF64: return f(Tag<double>{});
+    case kStoreF16: return f(Tag<__half>{});
+    case kStoreBF16: return f(Tag<__nv_bfloat16>{});
+  }
+  return cudaErrorInvalidValue;
+}
+template <class F>
+inline cudaError_t dispatch_lattice(int lattice, F &&f) {
+  switch (lattice) {
+    case kD1Q3: return f(std::integral_constant<int, kD1Q3>{});
+    case kD2Q9: return f(std::integral_constant<int, kD2Q9>{});
+    case kD3Q19: return f(std::integral_constant<int, kD3Q19>{});
+  }
+  return cudaErrorInvalidValue;
+}
+template <class F>
+inline cudaError_t dispatch_lattice_storage(int lattice, int precision, F &&f) {
+  return dispatch_lattice(lattice, [&](auto lat) { return dispatch_storage(precision, [&](auto tag) { return f(lat, tag); }); });
+}
+
+// Bytes of one stored value for a storage id.
+inline int storage_bytes(int precision) { return precision == kStoreF64 ? 8 : (precision == kStoreF32 ? 4 : 2); }
+
 // The step parameter in the kernel's precision.
 template <typename R>
 __host__ __device__ __forceinline__ R step_param(double d, float f);
@@ -55,8 +84,9 @@ cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t
                         double amp, const int32_t *k, cudaStream_t stream);
 
 // rho(x) = sum_i f_i, j_a(x) = sum_i f_i v_ia (FP64 outputs; j may be null).
-cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz, double *rho,
-                           double *j, cudaStream_t stream);
+// rho_mean decodes the 16-bit deviation formats.
+cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
+                           double rho_mean, double *rho, double *j, cudaStream_t stream);
 
 // Noise variates of sites [site0, site0 + nsites) at step t into z[site][moment] (FP64).
 cudaError_t launch_noise_draw(int precision, int dist, const PhiloxStep &ph, int64_t site0, int64_t nsites, int nmom,
@@ -76,8 +106,8 @@ constexpr int kReduceThreads = 256;
 // Number of FP64 quantities the observable pass produces for a lattice and mode count.
 int obs_quantities(int Q, int n_modes);
 
-cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double *partials, double *out,
-                        cudaStream_t stream);
+cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double rho_mean, double *partials,
+                        double *out, cudaStream_t stream);
 
 cudaError_t launch_observables(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
                                double rho_mean, int n_modes, const int32_t *modes /*device, n_modes*3*/,

@@ -24,8 +24,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // ---------------------------------------------------------------------------
 // Mass
 // ---------------------------------------------------------------------------
-template <int LAT, typename R>
-__global__ void __launch_bounds__(kReduceThreads) k_mass_partials(const R *__restrict__ f, int64_t N,
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kReduceThreads) k_mass_partials(const S *__restrict__ f, int64_t N, double rho_mean,
                                                                  double *__restrict__ partials) {
   using L = Lattice<LAT>;
   __shared__ double warp_tot[kReduceThreads / 32];
@@ -33,7 +33,10 @@ __global__ void __launch_bounds__(kReduceThreads) k_mass_partials(const R *__res
   for (int64_t s = blockIdx.x * static_cast<int64_t>(kReduceThreads) + threadIdx.x; s < N;
        s += static_cast<int64_t>(gridDim.x) * kReduceThreads) {
     double r = 0.0;
-    static_for<L::Q>([&](auto I) { r += static_cast<double>(f[decltype(I)::value * N + s]); });
+    static_for<L::Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      r += Store<S>::getd(f[i * N + s], L::w(i) * rho_mean);
+    });
     acc += r;
   }
   acc = warp_sum(acc);
@@ -54,23 +57,16 @@ __global__ void k_sum_partials(const double *__restrict__ partials, int nblocks,
   }
 }
 
-template <int LAT, typename R>
-static cudaError_t mass_t(const void *f, int64_t N, double *partials, double *out, cudaStream_t stream) {
-  k_mass_partials<LAT, R><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const R *>(f), N, partials);
-  k_sum_partials<<<1, 32, 0, stream>>>(partials, kReduceBlocks, out);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double *partials, double *out,
-                        cudaStream_t stream) {
-  const bool f64 = precision == 1;
-  switch (lattice) {
-    case kD1Q3: return f64 ? mass_t<kD1Q3, double>(f, N, partials, out, stream) : mass_t<kD1Q3, float>(f, N, partials, out, stream);
-    case kD2Q9: return f64 ? mass_t<kD2Q9, double>(f, N, partials, out, stream) : mass_t<kD2Q9, float>(f, N, partials, out, stream);
-    case kD3Q19:
-      return f64 ? mass_t<kD3Q19, double>(f, N, partials, out, stream) : mass_t<kD3Q19, float>(f, N, partials, out, stream);
-  }
-  return cudaErrorInvalidValue;
+cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double rho_mean, double *partials,
+                        double *out, cudaStream_t stream) {
+  return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
+    constexpr int LAT = decltype(lat)::value;
+    using S = typename decltype(tag)::type;
+    k_mass_partials<LAT, S><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const S *>(f), N, rho_mean,
+                                                                          partials);
+    k_sum_partials<<<1, 32, 0, stream>>>(partials, kReduceBlocks, out);
+    return cudaGetLastError();
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -84,8 +80,8 @@ struct ModeArgs {
 // partial layout per block: [rho, rho2, f_0..f_{Q-1}, re_0, im_0, .., re_{K-1}, im_{K-1}, ff pairs (i <= j)]
 int obs_quantities(int Q, int n_modes) { return 2 + Q + 2 * n_modes + Q * (Q + 1) / 2; }
 
-template <int LAT, typename R>
-__global__ void __launch_bounds__(kReduceThreads) k_obs_partials(const R *__restrict__ f, int32_t Lx, int32_t Ly,
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kReduceThreads) k_obs_partials(const S *__restrict__ f, int32_t Lx, int32_t Ly,
                                                                 int32_t Lz, double rho_mean, const ModeArgs modes,
                                                                 double *__restrict__ partials) {
   using L = Lattice<LAT>;
@@ -120,7 +116,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_obs_partials(const R *__rest
       double r = 0.0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        const double fi = static_cast<double>(f[i * N + s]);
+        const double fi = Store<S>::getd(f[i * N + s], L::w(i) * rho_mean);
         tile[i][threadIdx.x] = fi;
         a_f[i] += fi;
         r += fi;
@@ -206,11 +202,11 @@ __global__ void k_obs_finalize(const double *__restrict__ partials, int nblocks,
   }
 }
 
-template <int LAT, typename R>
+template <int LAT, typename S>
 static cudaError_t obs_t(const void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, const ModeArgs &ma,
                          double *partials, double *acc, cudaStream_t stream) {
   constexpr int Q = Lattice<LAT>::Q;
-  k_obs_partials<LAT, R><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const R *>(f), Lx, Ly, Lz, rho_mean,
+  k_obs_partials<LAT, S><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const S *>(f), Lx, Ly, Lz, rho_mean,
                                                                        ma, partials);
   const int nq = obs_quantities(Q, ma.n);
   k_obs_finalize<<<1, 256, nq * sizeof(double), stream>>>(partials, kReduceBlocks, Q, ma.n, acc);
@@ -225,19 +221,11 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
   ma.n = n_modes;
   for (int m = 0; m < n_modes; ++m)
     for (int k = 0; k < 3; ++k) ma.k[m][k] = modes[3 * m + k];
-  const bool f64 = precision == 1;
-  switch (lattice) {
-    case kD1Q3:
-      return f64 ? obs_t<kD1Q3, double>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream)
-                 : obs_t<kD1Q3, float>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream);
-    case kD2Q9:
-      return f64 ? obs_t<kD2Q9, double>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream)
-                 : obs_t<kD2Q9, float>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream);
-    case kD3Q19:
-      return f64 ? obs_t<kD3Q19, double>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream)
-                 : obs_t<kD3Q19, float>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream);
-  }
-  return cudaErrorInvalidValue;
+  return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
+    constexpr int LAT = decltype(lat)::value;
+    using S = typename decltype(tag)::type;
+    return obs_t<LAT, S>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream);
+  });
 }
 
 }  // namespace lbfd

@@ -75,26 +75,20 @@ static cudaError_t shift_t(const void *src, void *dst, int32_t Lx, int32_t Ly, i
 
 cudaError_t launch_shift(int lattice, int value_bytes, const void *src, void *dst, int32_t Lx, int32_t Ly, int32_t Lz,
                          int dir, cudaStream_t stream) {
-  const bool b8 = value_bytes == 8;
-  switch (lattice) {
-    case kD1Q3:
-      return b8 ? shift_t<kD1Q3, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream)
-                : shift_t<kD1Q3, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
-    case kD2Q9:
-      return b8 ? shift_t<kD2Q9, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream)
-                : shift_t<kD2Q9, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
-    case kD3Q19:
-      return b8 ? shift_t<kD3Q19, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream)
-                : shift_t<kD3Q19, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
-  }
-  return cudaErrorInvalidValue;
+  return dispatch_lattice(lattice, [&](auto lat) -> cudaError_t {
+    constexpr int LAT = decltype(lat)::value;
+    if (value_bytes == 8) return shift_t<LAT, uint64_t>(src, dst, Lx, Ly, Lz, dir, stream);
+    if (value_bytes == 4) return shift_t<LAT, uint32_t>(src, dst, Lx, Ly, Lz, dir, stream);
+    if (value_bytes == 2) return shift_t<LAT, uint16_t>(src, dst, Lx, Ly, Lz, dir, stream);
+    return cudaErrorInvalidValue;
+  });
 }
 
 // ---------------------------------------------------------------------------
 // Initial state f_i = w_i rho(x) (local equilibrium, eq. f0def)
 // ---------------------------------------------------------------------------
-template <int LAT, typename R>
-__global__ void k_init(R *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, int32_t kx,
+template <int LAT, typename S>
+__global__ void k_init(S *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, int32_t kx,
                        int32_t ky, int32_t kz) {
   using L = Lattice<LAT>;
   const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
@@ -112,50 +106,37 @@ __global__ void k_init(R *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, do
     }
     static_for<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      f[i * N + s] = static_cast<R>(L::w(i) * rho);
+      f[i * N + s] = Store<S>::putd(L::w(i) * rho, L::w(i) * rho_mean);
     });
   }
 }
 
-template <int LAT, typename R>
-static cudaError_t init_t(void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, const int32_t *k,
-                          cudaStream_t stream) {
-  const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
-  const int64_t blocks = (N + 255) / 256;
-  const int grid = static_cast<int>(blocks < 152 * 64 ? blocks : 152 * 64);
-  k_init<LAT, R><<<grid, 256, 0, stream>>>(static_cast<R *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2]);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
                         double amp, const int32_t *k, cudaStream_t stream) {
-  const bool f64 = precision == 1;
-  switch (lattice) {
-    case kD1Q3:
-      return f64 ? init_t<kD1Q3, double>(f, Lx, Ly, Lz, rho_mean, amp, k, stream)
-                 : init_t<kD1Q3, float>(f, Lx, Ly, Lz, rho_mean, amp, k, stream);
-    case kD2Q9:
-      return f64 ? init_t<kD2Q9, double>(f, Lx, Ly, Lz, rho_mean, amp, k, stream)
-                 : init_t<kD2Q9, float>(f, Lx, Ly, Lz, rho_mean, amp, k, stream);
-    case kD3Q19:
-      return f64 ? init_t<kD3Q19, double>(f, Lx, Ly, Lz, rho_mean, amp, k, stream)
-                 : init_t<kD3Q19, float>(f, Lx, Ly, Lz, rho_mean, amp, k, stream);
-  }
-  return cudaErrorInvalidValue;
+  return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
+    constexpr int LAT = decltype(lat)::value;
+    using S = typename decltype(tag)::type;
+    const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
+    const int64_t blocks = (N + 255) / 256;
+    const int grid = static_cast<int>(blocks < 152 * 64 ? blocks : 152 * 64);
+    k_init<LAT, S><<<grid, 256, 0, stream>>>(static_cast<S *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2]);
+    return cudaGetLastError();
+  });
 }
 
 // ---------------------------------------------------------------------------
 // Density and flux (FP64 outputs)
 // ---------------------------------------------------------------------------
-template <int LAT, typename R>
-__global__ void k_moments(const R *__restrict__ f, int64_t N, double *__restrict__ rho, double *__restrict__ j) {
+template <int LAT, typename S>
+__global__ void k_moments(const S *__restrict__ f, int64_t N, double rho_mean, double *__restrict__ rho,
+                          double *__restrict__ j) {
   using L = Lattice<LAT>;
   for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < N;
        s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
     static_for<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const double fi = static_cast<double>(f[i * N + s]);
+      const double fi = Store<S>::getd(f[i * N + s], L::w(i) * rho_mean);
       r += fi;
       if constexpr (L::v(i, 0) != 0) jx += L::v(i, 0) * fi;
       if constexpr (L::v(i, 1) != 0) jy += L::v(i, 1) * fi;
@@ -170,25 +151,17 @@ __global__ void k_moments(const R *__restrict__ f, int64_t N, double *__restrict
   }
 }
 
-template <int LAT, typename R>
-static cudaError_t moments_t(const void *f, int64_t N, double *rho, double *j, cudaStream_t stream) {
-  const int64_t blocks = (N + 255) / 256;
-  const int grid = static_cast<int>(blocks < 152 * 32 ? blocks : 152 * 32);
-  k_moments<LAT, R><<<grid, 256, 0, stream>>>(static_cast<const R *>(f), N, rho, j);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz, double *rho,
-                           double *j, cudaStream_t stream) {
-  const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
-  const bool f64 = precision == 1;
-  switch (lattice) {
-    case kD1Q3: return f64 ? moments_t<kD1Q3, double>(f, N, rho, j, stream) : moments_t<kD1Q3, float>(f, N, rho, j, stream);
-    case kD2Q9: return f64 ? moments_t<kD2Q9, double>(f, N, rho, j, stream) : moments_t<kD2Q9, float>(f, N, rho, j, stream);
-    case kD3Q19:
-      return f64 ? moments_t<kD3Q19, double>(f, N, rho, j, stream) : moments_t<kD3Q19, float>(f, N, rho, j, stream);
-  }
-  return cudaErrorInvalidValue;
+cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
+                           double rho_mean, double *rho, double *j, cudaStream_t stream) {
+  return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
+    constexpr int LAT = decltype(lat)::value;
+    using S = typename decltype(tag)::type;
+    const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
+    const int64_t blocks = (N + 255) / 256;
+    const int grid = static_cast<int>(blocks < 152 * 32 ? blocks : 152 * 32);
+    k_moments<LAT, S><<<grid, 256, 0, stream>>>(static_cast<const S *>(f), N, rho_mean, rho, j);
+    return cudaGetLastError();
+  });
 }
 
 // ---------------------------------------------------------------------------

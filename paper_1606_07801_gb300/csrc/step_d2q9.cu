@@ -5,7 +5,10 @@
 namespace lbfd {
 
 cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
-  return precision == 1 ? step_t<kD2Q9, double>(src, dst, a, stream) : step_t<kD2Q9, float>(src, dst, a, stream);
+  return dispatch_storage(precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    return step_t<kD2Q9, S>(src, dst, a, stream);
+  });
 }
 
 }  // namespace lbfd

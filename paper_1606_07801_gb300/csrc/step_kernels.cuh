@@ -57,10 +57,23 @@ __device__ __forceinline__ void collide_site(R (&f)[Lattice<LAT>::Q], uint32_t s
   f[0] = rho - moved;
 }
 
-// Scalar kernel: one site per thread, any lattice shape.
-template <int LAT, typename R, int NOISE>
-__global__ void __launch_bounds__(256) k_step(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
+// w_i rho_mean in the compute type: the offset that the 16-bit formats store
+// the deviation from (zero for FP32/FP64 storage).
+template <int LAT, typename S>
+__device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepArgs &a) {
+  using R = typename Store<S>::R;
+  if constexpr (Store<S>::kDeviation)
+    return static_cast<R>(Lattice<LAT>::w(i)) * step_param<R>(a.rho_eq, a.rho_eq_f);
+  else
+    return R(0);
+}
+
+// Scalar kernel: one site per thread, any lattice shape.  S is the storage
+// type (float, double, or a 16-bit deviation format with FP32 arithmetic).
+template <int LAT, typename S, int NOISE>
+__global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   using L = Lattice<LAT>;
+  using R = typename Store<S>::R;
   constexpr int Q = L::Q;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -82,12 +95,12 @@ __global__ void __launch_bounds__(256) k_step(const R *__restrict__ src, R *__re
     const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
     const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
     const uint32_t so = static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
-    f[i] = __ldg(src + static_cast<size_t>(i) * static_cast<size_t>(a.N) + so);
+    f[i] = Store<S>::get(src[static_cast<size_t>(i) * static_cast<size_t>(a.N) + so], store_offset<LAT, S>(i, a));
   });
   collide_site<LAT, R, NOISE>(f, s, a);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = f[i];
+    dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = Store<S>::put(f[i], store_offset<LAT, S>(i, a));
   });
 }
 
@@ -96,25 +109,9 @@ __global__ void __launch_bounds__(256) k_step(const R *__restrict__ src, R *__re
 // v_x = 0), plus, for v_x = +1 / -1, one scalar load of the column left of
 // x0 / right of x0 + VX - 1 (wrapped); stores are VX-wide.  This cuts the
 // address arithmetic and memory instructions per site by about VX.
-template <typename R, int VX>
-struct VecOf;
-template <>
-struct VecOf<float, 4> {
-  using T = float4;
-  __device__ static __forceinline__ void get(const T &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
-  __device__ static __forceinline__ T make(const float (&o)[4]) { return make_float4(o[0], o[1], o[2], o[3]); }
-};
-template <>
-struct VecOf<float, 2> {
-  using T = float2;
-  __device__ static __forceinline__ void get(const T &v, float (&o)[2]) { o[0] = v.x; o[1] = v.y; }
-  __device__ static __forceinline__ T make(const float (&o)[2]) { return make_float2(o[0], o[1]); }
-};
-template <>
-struct VecOf<double, 2> {
-  using T = double2;
-  __device__ static __forceinline__ void get(const T &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
-  __device__ static __forceinline__ T make(const double (&o)[2]) { return make_double2(o[0], o[1]); }
+template <typename S, int VX>
+struct alignas(sizeof(S) * VX) Pack {
+  S v[VX];
 };
 
 // Minimum resident 256-thread blocks per SM asked of the register allocator
@@ -123,16 +120,18 @@ struct VecOf<double, 2> {
 // registers), D3Q19 256^3 at 3 (<= 85 registers); the unconstrained
 // allocation leaves D3Q19 one block per SM, and tighter caps spill.  FP64
 // kernels need more registers: 2.
-template <int LAT, typename R>
+template <int LAT, typename S>
 constexpr int step_min_blocks() {
-  if (sizeof(R) != 4) return 2;
+  if (sizeof(typename Store<S>::R) != 4) return 2;
   return LAT == kD3Q19 ? 3 : 4;
 }
 
-template <int LAT, typename R, int VX, int NOISE>
-__global__ void __launch_bounds__(256, step_min_blocks<LAT, R>()) k_step_vec(const R *__restrict__ src, R *__restrict__ dst, const StepArgs a) {
+template <int LAT, typename S, int VX, int NOISE>
+__global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
+    k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   using L = Lattice<LAT>;
-  using V = VecOf<R, VX>;
+  using R = typename Store<S>::R;
+  using P = Pack<S, VX>;
   constexpr int Q = L::Q;
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -152,30 +151,34 @@ __global__ void __launch_bounds__(256, step_min_blocks<LAT, R>()) k_step_vec(con
     const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
     const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
     const uint32_t srow = Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
-    const R *pop = src + static_cast<size_t>(i) * static_cast<size_t>(a.N) + srow;
+    const S *pop = src + static_cast<size_t>(i) * static_cast<size_t>(a.N) + srow;
+    const R wr = store_offset<LAT, S>(i, a);
+    const P pk = *reinterpret_cast<const P *>(pop + x0);
     R v[VX];
-    V::get(__ldg(reinterpret_cast<const typename V::T *>(pop + x0)), v);
+#pragma unroll
+    for (int k = 0; k < VX; ++k) v[k] = Store<S>::get(pk.v[k], wr);
     if constexpr (vx == 0) {
 #pragma unroll
       for (int k = 0; k < VX; ++k) f[k][i] = v[k];
     } else if constexpr (vx > 0) {  // site x0 + k pulls from x0 + k - 1
-      f[0][i] = __ldg(pop + xl);
+      f[0][i] = Store<S>::get(pop[xl], wr);
 #pragma unroll
       for (int k = 1; k < VX; ++k) f[k][i] = v[k - 1];
     } else {  // site x0 + k pulls from x0 + k + 1
 #pragma unroll
       for (int k = 0; k < VX - 1; ++k) f[k][i] = v[k + 1];
-      f[VX - 1][i] = __ldg(pop + xr);
+      f[VX - 1][i] = Store<S>::get(pop[xr], wr);
     }
   });
 #pragma unroll
   for (int k = 0; k < VX; ++k) collide_site<LAT, R, NOISE>(f[k], row + static_cast<uint32_t>(x0 + k), a);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    R o[VX];
+    const R wr = store_offset<LAT, S>(i, a);
+    P pk;
 #pragma unroll
-    for (int k = 0; k < VX; ++k) o[k] = f[k][i];
-    *reinterpret_cast<typename V::T *>(dst + static_cast<size_t>(i) * static_cast<size_t>(a.N) + row + x0) = V::make(o);
+    for (int k = 0; k < VX; ++k) pk.v[k] = Store<S>::put(f[k][i], wr);
+    *reinterpret_cast<P *>(dst + static_cast<size_t>(i) * static_cast<size_t>(a.N) + row + x0) = pk;
   });
 }
 
@@ -201,38 +204,38 @@ inline int step_vx_override() {
   return v;
 }
 
-template <int LAT, typename R, int NOISE>
+template <int LAT, typename S, int NOISE>
 cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
+  using R = typename Store<S>::R;
   int vx = step_vx_override();
   if (vx == 0) vx = 2;
   if (sizeof(R) == 8 && vx == 4) vx = 2;
   while (vx > 1 && a.Lx % vx != 0) vx /= 2;
   dim3 grid, block;
   step_shape(a.Lx, a.Ly, a.Lz, grid, block, vx);
-  const R *s = static_cast<const R *>(src);
-  R *d = static_cast<R *>(dst);
+  const S *s = static_cast<const S *>(src);
+  S *d = static_cast<S *>(dst);
   if constexpr (sizeof(R) == 4) {
     if (vx == 4) {
-      k_step_vec<LAT, R, 4, NOISE><<<grid, block, 0, stream>>>(s, d, a);
+      k_step_vec<LAT, S, 4, NOISE><<<grid, block, 0, stream>>>(s, d, a);
       return cudaGetLastError();
     }
   }
   if (vx == 2) {
-    k_step_vec<LAT, R, 2, NOISE><<<grid, block, 0, stream>>>(s, d, a);
+    k_step_vec<LAT, S, 2, NOISE><<<grid, block, 0, stream>>>(s, d, a);
     return cudaGetLastError();
   }
-  k_step<LAT, R, NOISE><<<grid, block, 0, stream>>>(s, d, a);
+  k_step<LAT, S, NOISE><<<grid, block, 0, stream>>>(s, d, a);
   return cudaGetLastError();
 }
 
 // Kernel selection by noise configuration: each variant is branch-free in
 // its per-site code, so the compiler can interleave the sites of a thread.
-template <int LAT, typename R>
+template <int LAT, typename S>
 cudaError_t step_t(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
-  if (a.noise_mode == kNoiseOff) return step_noise<LAT, R, kStepNoiseOff>(src, dst, a, stream);
-  if (a.noise_dist == kGaussian) return step_noise<LAT, R, kStepNoiseGauss>(src, dst, a, stream);
-  return step_noise<LAT, R, kStepNoiseFlat>(src, dst, a, stream);
+  if (a.noise_mode == kNoiseOff) return step_noise<LAT, S, kStepNoiseOff>(src, dst, a, stream);
+  if (a.noise_dist == kGaussian) return step_noise<LAT, S, kStepNoiseGauss>(src, dst, a, stream);
+  return step_noise<LAT, S, kStepNoiseFlat>(src, dst, a, stream);
 }
-
 
 }  // namespace lbfd

@@ -20,7 +20,7 @@ P = ctypes.POINTER
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 D1Q3, D2Q9, D3Q19 = 0, 1, 2
-F32, F64 = 0, 1
+F32, F64, F32_F16, F32_BF16 = 0, 1, 2, 3
 NOISE_LOCAL, NOISE_GLOBAL, NOISE_OFF = 0, 1, 2
 GAUSSIAN, UNIFORM = 0, 1
 INIT_UNIFORM, INIT_SINE, INIT_NONE = 0, 1, 2

@@ -51,7 +51,7 @@ def test_options_defaults():
     (dict(tau=float("nan")), "tau"),
     (dict(rho_mean=-1.0), "rho_mean"),
     (dict(lattice=7), "lattice"),
-    (dict(precision=3), "precision"),
+    (dict(precision=7), "precision"),
     (dict(noise_mode=9), "noise"),
     (dict(noise_dist=5), "distribution"),
     (dict(init=4), "init"),
