@@ -65,18 +65,24 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """dram bytes per launch of k_step from the committed ncu summary, or None
-    if none exists or the kernel changed since it was taken."""
+def profiled(workload: str, key: str):
+    """A figure of the committed ncu summary of k_step on this workload
+    (traffic_bytes_per_launch, instructions_per_site), or None if there is
+    none or the kernel sources changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"k_step_{workload}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
-    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_tr or m_hash.group(1) != kernel_hash():
+    m_val = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_val or m_hash.group(1) != kernel_hash():
         return None
-    return float(m_tr.group(1))
+    return float(m_val.group(1))
+
+
+# Instruction-issue ceiling of GB300: 152 SMs x 4 schedulers x 32 lanes, one
+# warp instruction per scheduler and cycle, at the 2070 MHz maximum SM clock.
+ISSUE_PEAK = 152 * 4 * 32 * 2.070e9
 
 
 def measured_peaks():
@@ -286,7 +292,14 @@ def main():
     bytes_per_launch = 2 * Q * elem * N
     achieved = bytes_per_launch / (ms_per_step * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(args.workload)
+    traffic = profiled(args.workload, "traffic_bytes_per_launch")
+    ipsite = profiled(args.workload, "instructions_per_site")
+    alu = None
+    if ipsite is not None:
+        a_alu = ipsite * N / (ms_per_step * 1e-3)
+        alu = {"bound": "alu", "achieved": a_alu, "peak": ISSUE_PEAK, "unit": "thread-instructions/s",
+               "frac": a_alu / ISSUE_PEAK, "instructions_per_site": ipsite,
+               "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz"}
 
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device (pinned), one step runs, the density comes back
@@ -322,10 +335,16 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_per_launch, "kernel": "k_step",
                          "peak_source": f"{peak_kind} hbm_gbs"},
+            "roofline_alu": alu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        if prec in (2, 3) and alu is not None:
+            # 16-bit storage halves the bytes but not the arithmetic: the
+            # issue ceiling binds, so it is the primary roofline here
+            line["roofline_hbm"], line["roofline"] = line["roofline"], alu
+            del line["roofline_alu"]
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

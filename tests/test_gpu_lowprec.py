@@ -22,7 +22,7 @@ FORMATS = [(lb.F32_F16, 1e-3, 2.0**-11), (lb.F32_BF16, 1e-2, 2.0**-8)]
 def test_storage_round_trip(precision, tol, ulp):
     Q, dims, rho = 19, (12, 10, 8), 50.0
     N = int(np.prod(dims))
-    _, _, _, w = abi.lbfd_lattice_tables(lb.D3Q19)
+    _, w, _ = abi.lbfd_lattice_tables(lb.D3Q19)
     f0 = synth.random_populations(Q, N, rho, 0.3, seed=3)
     with lb.Simulation(lb.D3Q19, dims, 1.0, rho, 1, precision=precision, init=lb.INIT_NONE) as s:
         s.set_f(f0)
@@ -62,7 +62,7 @@ def test_equilibrium_statistics_hold(precision):
         m1 = s.mass()
         s.sample()
         ob = s.observables()
-        _, _, _, w = abi.lbfd_lattice_tables(lb.D3Q19)
+        _, w, _ = abi.lbfd_lattice_tables(lb.D3Q19)
     var = ob["sum_rho2"] / N - (ob["sum_rho"] / N) ** 2
     assert abs(var / rho - 1.0) < 0.03
     assert np.max(np.abs(ob["sum_f"] / N - w * rho)) < 2e-3 * rho
