@@ -222,18 +222,96 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_ensemble(args):
+    """Config 4: 4096 independent D2Q9 FP32 lattices (sides log-uniform in
+    [32, 512], rho_mean U[0.5, 200], tau U[0.6, 1.5], distinct seeds), one
+    launch per time step for all of them (graph-captured chunks), against the
+    plain way of running them: one launch per simulation per step."""
+    import torch
+
+    import paper_1606_07801_gb300 as lb
+    from paper_1606_07801_gb300 import synth
+
+    torch.cuda.set_device(0)
+    lb.load()
+    specs = synth.ensemble(args.members)
+    for k, sp in enumerate(specs):
+        sp["lattice_id"] = k
+        sp["init"] = lb.INIT_UNIFORM
+    stream = torch.cuda.Stream()
+    ens = lb.Ensemble(lb.D2Q9, specs, stream=stream)
+    n, sites, _, _ = ens.query()
+    vx = ens.tune(steps=3)
+    ens.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ens.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ens.close()
+    glups = sites * args.steps / (ms * 1e-3) / 1e9
+    # the same members run the plain way: one handle and one launch per simulation per step
+    sub = specs[: args.per_sim_members]
+    sims = [lb.Simulation(lb.D2Q9, sp["dims"], sp["tau"], sp["rho_mean"], sp["seed"], lattice_id=sp["lattice_id"],
+                          stream=stream) for sp in sub]
+    for s_ in sims:
+        s_.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.per_sim_steps):
+        for s_ in sims:
+            s_.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_ps = e0.elapsed_time(e1)
+    sub_sites = sum(int(np.prod(sp["dims"])) for sp in sub)
+    per_sim = sub_sites * args.per_sim_steps / (ms_ps * 1e-3) / 1e9
+    for s_ in sims:
+        s_.close()
+    peak, peak_kind = measured_peaks()
+    achieved = 72.0 * sites / (ms / args.steps * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ensemble of {n} D2Q9 FP32 lattices, sides log-uniform in [32, 512], rho_mean "
+                               f"U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian noise",
+                   "sites": sites, "items_per_thread_sites": vx, "graph_steps": 16,
+                   "l2": "inputs larger than L2: %.0f MB per population buffer" % (36.0 * sites / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "algorithmic_bytes_per_launch": 72 * sites, "kernel": "k_ens_step",
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "per_sim_baseline": {"value": per_sim, "unit": UNIT, "sims": len(sub), "steps": args.per_sim_steps,
+                             "how": "one lbfd handle and one k_step launch per simulation per step, same stream"},
+        "speedup_vs_per_sim": glups / per_sim,
+        "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40000)
     ap.add_argument("--warmup", type=int, default=200)
-    ap.add_argument("--workload", default="d2q9", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="d2q9", choices=sorted(WORKLOADS) + ["ensemble"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--members", type=int, default=4096)
+    ap.add_argument("--per-sim-members", type=int, default=256)
+    ap.add_argument("--per-sim-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload == "ensemble":
+        run_ensemble(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

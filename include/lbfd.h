@@ -224,15 +224,63 @@ int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t
 int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void *f_dev, int64_t n_sites, double *mass_dev,
                       void *stream);
 
+/* ---- batched ensembles ------------------------------------------------------
+ * Many independent lattices of one lattice type (each with its own size,
+ * tau, rho_mean, seed and Philox lattice id) advanced together: one launch
+ * per time step covers every member, and chunks of steps are captured into a
+ * CUDA graph and replayed.  Every member evolves exactly as the same lattice
+ * would under lbfd_create_ex with the same parameters (same arithmetic,
+ * same noise keys).  Members share one precision, noise mode and law. */
+typedef struct lbfd_member {
+    int64_t dims[3];    /* Lx, Ly, Lz; trailing dims of lower-D lattices must be 1 */
+    double tau;         /* > 1/2 */
+    double rho_mean;    /* >= 0 */
+    uint64_t seed;      /* Philox key */
+    uint32_t lattice_id; /* Philox counter word 1 */
+    int32_t init;       /* LBFD_INIT_UNIFORM / LBFD_INIT_SINE / LBFD_INIT_NONE */
+    double sine_amp;
+    int32_t sine_k[3];
+    int32_t reserved;
+} lbfd_member;
+
+typedef struct lbfd_ens *lbfd_ens_t;
+
+/* Creates an ensemble of n members on the current device (all populations in
+ * two device buffers allocated here).  stream: a cudaStream_t other than the
+ * legacy default stream (graphs are captured on it); NULL makes the ensemble
+ * create and own a non-blocking stream. */
+int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, int32_t noise_mode, int32_t noise_dist,
+                         const lbfd_member *members, int32_t n, void *stream);
+int lbfd_ensemble_destroy(lbfd_ens_t e);
+
+/* Advances every member by n steps (asynchronous).  Same step rule as
+ * lbfd_step; t is shared by the members. */
+int lbfd_ensemble_step(lbfd_ens_t e, int64_t n);
+int lbfd_ensemble_sync(lbfd_ens_t e);
+
+/* Times the candidate work decompositions (1 or 2 sites per item) over
+ * `steps` launches that write only the spare buffer, keeps the fastest and
+ * reports it.  The state and t are unchanged. */
+int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen);
+
+int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx);
+
+/* Per-member state in FP64, layout [i][site] (as lbfd_get_f / lbfd_set_f),
+ * and FP64 mass.  Synchronous. */
+int lbfd_ensemble_get_f(lbfd_ens_t e, int32_t member, double *f_host);
+int lbfd_ensemble_set_f(lbfd_ens_t e, int32_t member, const double *f_host);
+int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
+
 /* Message for the calling thread's last failure ("" if none). */
 const char *lbfd_last_error(void);
 
 /* Number of step-kernel launches the calling process has issued. */
 int64_t lbfd_kernel_launches(void);
 
-/* sizeof(lbfd_options) and sizeof(lbfd_obs) as compiled into the library,
- * for bindings that mirror the structs.  Either pointer may be NULL. */
-int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes);
+/* sizeof(lbfd_options), sizeof(lbfd_obs) and sizeof(lbfd_member) as compiled
+ * into the library, for bindings that mirror the structs.  Any pointer may be
+ * NULL. */
+int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes, int64_t *member_bytes);
 
 #ifdef __cplusplus
 }

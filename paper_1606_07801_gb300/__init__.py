@@ -19,7 +19,7 @@ from .lbfd import (D1Q3, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSU
                    Q_OF, UNIFORM, LbfdError, Options, load)
 from . import lbfd as abi
 
-__all__ = ["Simulation", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
+__all__ = ["Simulation", "Ensemble", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
            "F32_F16", "F32_BF16",
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
            "INIT_NONE", "Q_OF", "D_OF"]
@@ -132,3 +132,59 @@ class Simulation:
 
     def state_device(self):
         return abi.lbfd_state_device(self.h)
+
+
+class Ensemble:
+    """Many independent lattices of one type advanced together (one launch
+    per step for all members, graph-captured).  ``specs`` is a list of dicts
+    with dims, tau, rho_mean, seed and optionally lattice_id, init,
+    sine_amp, sine_k."""
+
+    def __init__(self, lattice: int, specs, *, precision: int = F32, noise_mode: int = NOISE_LOCAL,
+                 noise_dist: int = GAUSSIAN, stream=None):
+        self.lattice, self.specs = lattice, list(specs)
+        self.Q = Q_OF[lattice]
+        self._stream = stream
+        s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self.h = abi.lbfd_ensemble_create(lattice, precision, noise_mode, noise_dist, self.specs, s)
+
+    def sites(self, member: int) -> int:
+        return int(np.prod(self.specs[member]["dims"]))
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            h, self.h = self.h, None
+            abi.lbfd_ensemble_destroy(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1) -> None:
+        abi.lbfd_ensemble_step(self.h, n)
+
+    def sync(self) -> None:
+        abi.lbfd_ensemble_sync(self.h)
+
+    def tune(self, steps: int = 3) -> int:
+        return abi.lbfd_ensemble_tune(self.h, steps)
+
+    def query(self):
+        return abi.lbfd_ensemble_query(self.h)
+
+    def get_f(self, member: int) -> np.ndarray:
+        return abi.lbfd_ensemble_get_f(self.h, member, self.Q, self.sites(member))
+
+    def set_f(self, member: int, f) -> None:
+        abi.lbfd_ensemble_set_f(self.h, member, f)
+
+    def mass(self, member: int) -> float:
+        return abi.lbfd_ensemble_mass(self.h, member)

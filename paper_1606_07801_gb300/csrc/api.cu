@@ -252,14 +252,7 @@ int lbfd_step(lbfd_t h, int64_t n) {
   a.Ly = int32_t(o.dims[1]);
   a.Lz = int32_t(o.dims[2]);
   a.N = h->N;
-  a.omega = 1.0 - 1.0 / o.tau;
-  a.inv_tau = 1.0 / o.tau;
-  a.noise_var = (2.0 * o.tau - 1.0) / (o.tau * o.tau);
-  a.rho_eq = o.rho_mean;
-  a.omega_f = float(a.omega);
-  a.inv_tau_f = float(a.inv_tau);
-  a.noise_var_f = float(a.noise_var);
-  a.rho_eq_f = float(a.rho_eq);
+  fill_step_params(a, o.tau, o.rho_mean);
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
   for (int64_t k = 0; k < n; ++k) {
@@ -492,9 +485,10 @@ const char *lbfd_last_error(void) { return g_err.c_str(); }
 
 int64_t lbfd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
-int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes) {
+int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes, int64_t *member_bytes) {
   if (options_bytes) *options_bytes = int64_t(sizeof(lbfd_options));
   if (obs_bytes) *obs_bytes = int64_t(sizeof(lbfd_obs));
+  if (member_bytes) *member_bytes = int64_t(sizeof(lbfd_member));
   return LBFD_OK;
 }
 

@@ -28,6 +28,21 @@ struct StepArgs {
   PhiloxStep ph;       // Philox key and counter words of this step (seed, lattice id, t)
 };
 
+// Relaxation and noise parameters of a step from tau and rho_mean (FP64 and
+// their FP32 copies).  Every path that steps a lattice uses this one
+// function, so a lattice gets bit-identical parameters alone or in an
+// ensemble.
+__host__ __device__ inline void fill_step_params(StepArgs &a, double tau, double rho_mean) {
+  a.omega = 1.0 - 1.0 / tau;
+  a.inv_tau = 1.0 / tau;
+  a.noise_var = (2.0 * tau - 1.0) / (tau * tau);
+  a.rho_eq = rho_mean;
+  a.omega_f = static_cast<float>(a.omega);
+  a.inv_tau_f = static_cast<float>(a.inv_tau);
+  a.noise_var_f = static_cast<float>(a.noise_var);
+  a.rho_eq_f = static_cast<float>(a.rho_eq);
+}
+
 // Calls f(std::integral_constant<int, LAT>, Tag<S>) for a lattice id and a
 // storage id (0 FP32, 1 FP64, 2 FP16 deviations, 3 BF16 deviations).
 template <class F>
@@ -115,6 +130,22 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
 
 // Records msg as the calling thread's lbfd_last_error() and returns code.
 int set_last_error(int code, const std::string &msg);
+
+// Ensemble step launchers (one translation unit per lattice); vx is 1 or 2.
+struct EnsMember;
+struct EnsTile;
+cudaError_t launch_ens_step_d1q3(int precision, int vx, const void *src, void *dst, const EnsMember *members,
+                                 const EnsTile *tiles, int ntiles, const uint64_t *t_dev, int noise_mode, int noise_dist,
+                                 int grid, cudaStream_t stream);
+cudaError_t launch_ens_step_d2q9(int precision, int vx, const void *src, void *dst, const EnsMember *members,
+                                 const EnsTile *tiles, int ntiles, const uint64_t *t_dev, int noise_mode, int noise_dist,
+                                 int grid, cudaStream_t stream);
+cudaError_t launch_ens_step_d3q19(int precision, int vx, const void *src, void *dst, const EnsMember *members,
+                                  const EnsTile *tiles, int ntiles, const uint64_t *t_dev, int noise_mode,
+                                  int noise_dist, int grid, cudaStream_t stream);
+int ens_blocks_per_sm_d1q3(int precision, int vx, int noise_mode, int noise_dist);
+int ens_blocks_per_sm_d2q9(int precision, int vx, int noise_mode, int noise_dist);
+int ens_blocks_per_sm_d3q19(int precision, int vx, int noise_mode, int noise_dist);
 
 // Host copy of the moment matrix the kernels use, m[a*Q + i].
 int basis_table(int lattice, double *m);

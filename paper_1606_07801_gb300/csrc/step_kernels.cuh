@@ -70,15 +70,14 @@ __device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepAr
 
 // Scalar kernel: one site per thread, any lattice shape.  S is the storage
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
+// Update of site (x, y, z) of one lattice (any shape).  S is the storage
+// type (float, double, or a 16-bit deviation format with FP32 arithmetic).
 template <int LAT, typename S, int NOISE>
-__global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
+__device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a,
+                                                 int x, int y, int z) {
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   constexpr int Q = L::Q;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= a.Lx || y >= a.Ly) return;
   // periodic neighbours
   const int xm = (x == 0 ? a.Lx : x) - 1, xp = (x + 1 == a.Lx) ? 0 : x + 1;
   const int ym = (y == 0 ? a.Ly : y) - 1, yp = (y + 1 == a.Ly) ? 0 : y + 1;
@@ -104,6 +103,16 @@ __global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__re
   });
 }
 
+// Scalar kernel: one site per thread, any lattice shape.
+template <int LAT, typename S, int NOISE>
+__global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.Lx || y >= a.Ly) return;
+  step_scalar_body<LAT, S, NOISE>(src, dst, a, x, y, z);
+}
+
 // Vector kernel: VX consecutive sites of a row per thread (needs Lx % VX == 0).
 // Each population is one aligned VX-wide load at x0 (populations with
 // v_x = 0), plus, for v_x = +1 / -1, one scalar load of the column left of
@@ -126,17 +135,14 @@ constexpr int step_min_blocks() {
   return LAT == kD3Q19 ? 3 : 4;
 }
 
+// Update of sites (x0 .. x0 + VX - 1, y, z) of one lattice (Lx % VX == 0).
 template <int LAT, typename S, int VX, int NOISE>
-__global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
-    k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
+__device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a, int x0,
+                                              int y, int z) {
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   using P = Pack<S, VX>;
   constexpr int Q = L::Q;
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x0 >= a.Lx || y >= a.Ly) return;
   const int xl = (x0 == 0 ? a.Lx : x0) - 1;        // column left of the vector
   const int xr = (x0 + VX == a.Lx) ? 0 : x0 + VX;  // column right of the vector
   const int ym = (y == 0 ? a.Ly : y) - 1, yp = (y + 1 == a.Ly) ? 0 : y + 1;
@@ -180,6 +186,16 @@ __global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
     for (int k = 0; k < VX; ++k) pk.v[k] = Store<S>::put(f[k][i], wr);
     *reinterpret_cast<P *>(dst + static_cast<size_t>(i) * static_cast<size_t>(a.N) + row + x0) = pk;
   });
+}
+
+template <int LAT, typename S, int VX, int NOISE>
+__global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
+    k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
+  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x0 >= a.Lx || y >= a.Ly) return;
+  step_vec_body<LAT, S, VX, NOISE>(src, dst, a, x0, y, z);
 }
 
 inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block, int vx = 1) {

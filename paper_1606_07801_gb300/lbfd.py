@@ -50,6 +50,15 @@ class Obs(ctypes.Structure):
     ]
 
 
+class Member(ctypes.Structure):
+    """Mirror of ``lbfd_member``."""
+    _fields_ = [
+        ("dims", c_int64 * 3), ("tau", c_double), ("rho_mean", c_double), ("seed", c_uint64),
+        ("lattice_id", c_uint32), ("init", c_int32), ("sine_amp", c_double), ("sine_k", c_int32 * 3),
+        ("reserved", c_int32),
+    ]
+
+
 class LbfdError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where} failed with status {code}: {msg}")
@@ -83,9 +92,18 @@ SIGNATURES = {
                                   c_void_p]),
     "lbfd_box_muller_probe": (c_int32, [c_int32, c_void_p, c_int64, c_void_p]),
     "lbfd_mass_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p]),
+    "lbfd_ensemble_create": (c_int32, [P(c_void_p), c_int32, c_int32, c_int32, c_int32, P(Member), c_int32, c_void_p]),
+    "lbfd_ensemble_destroy": (c_int32, [c_void_p]),
+    "lbfd_ensemble_step": (c_int32, [c_void_p, c_int64]),
+    "lbfd_ensemble_sync": (c_int32, [c_void_p]),
+    "lbfd_ensemble_tune": (c_int32, [c_void_p, c_int32, P(c_int32)]),
+    "lbfd_ensemble_query": (c_int32, [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int32)]),
+    "lbfd_ensemble_get_f": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "lbfd_ensemble_set_f": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "lbfd_ensemble_mass": (c_int32, [c_void_p, c_int32, P(c_double)]),
     "lbfd_last_error": (ctypes.c_char_p, []),
     "lbfd_kernel_launches": (c_int64, []),
-    "lbfd_struct_sizes": (c_int32, [P(c_int64), P(c_int64)]),
+    "lbfd_struct_sizes": (c_int32, [P(c_int64), P(c_int64), P(c_int64)]),
 }
 
 _lib = None
@@ -280,11 +298,80 @@ def lbfd_mass_noalloc(lattice: int, precision: int, f_dev_ptr: int, n_sites: int
            "lbfd_mass_noalloc")
 
 
+def make_members(specs) -> ctypes.Array:
+    """specs: dicts with dims, tau, rho_mean, seed and optionally lattice_id,
+    init, sine_amp, sine_k."""
+    arr = (Member * len(specs))()
+    for k, sp in enumerate(specs):
+        d = [int(x) for x in sp["dims"]] + [1] * (3 - len(sp["dims"]))
+        m = arr[k]
+        for a in range(3):
+            m.dims[a] = d[a]
+        m.tau, m.rho_mean, m.seed = float(sp["tau"]), float(sp["rho_mean"]), int(sp["seed"])
+        m.lattice_id = int(sp.get("lattice_id", 0))
+        m.init = int(sp.get("init", INIT_UNIFORM))
+        m.sine_amp = float(sp.get("sine_amp", 0.0))
+        sk = list(sp.get("sine_k", (1, 0, 0))) + [0, 0, 0]
+        for a in range(3):
+            m.sine_k[a] = int(sk[a])
+    return arr
+
+
+def lbfd_ensemble_create(lattice: int, precision: int, noise_mode: int, noise_dist: int, specs, stream=None) -> int:
+    h = c_void_p()
+    arr = make_members(specs)
+    _check(load().lbfd_ensemble_create(ctypes.byref(h), lattice, precision, noise_mode, noise_dist, arr, len(specs),
+                                       stream), "lbfd_ensemble_create")
+    return h.value
+
+
+def lbfd_ensemble_destroy(e: int) -> None:
+    _check(load().lbfd_ensemble_destroy(e), "lbfd_ensemble_destroy")
+
+
+def lbfd_ensemble_step(e: int, n: int) -> None:
+    _check(load().lbfd_ensemble_step(e, n), "lbfd_ensemble_step")
+
+
+def lbfd_ensemble_sync(e: int) -> None:
+    _check(load().lbfd_ensemble_sync(e), "lbfd_ensemble_sync")
+
+
+def lbfd_ensemble_tune(e: int, steps: int = 3) -> int:
+    v = c_int32()
+    _check(load().lbfd_ensemble_tune(e, steps, ctypes.byref(v)), "lbfd_ensemble_tune")
+    return v.value
+
+
+def lbfd_ensemble_query(e: int):
+    n, sites, t, vx = c_int32(), c_int64(), c_int64(), c_int32()
+    _check(load().lbfd_ensemble_query(e, ctypes.byref(n), ctypes.byref(sites), ctypes.byref(t), ctypes.byref(vx)),
+           "lbfd_ensemble_query")
+    return n.value, sites.value, t.value, vx.value
+
+
+def lbfd_ensemble_get_f(e: int, member: int, Q: int, N: int) -> np.ndarray:
+    out = np.empty((Q, N), dtype=np.float64)
+    _check(load().lbfd_ensemble_get_f(e, member, _ptr(out)), "lbfd_ensemble_get_f")
+    return out
+
+
+def lbfd_ensemble_set_f(e: int, member: int, f: np.ndarray) -> None:
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(load().lbfd_ensemble_set_f(e, member, _ptr(f)), "lbfd_ensemble_set_f")
+
+
+def lbfd_ensemble_mass(e: int, member: int) -> float:
+    m = c_double()
+    _check(load().lbfd_ensemble_mass(e, member, ctypes.byref(m)), "lbfd_ensemble_mass")
+    return m.value
+
+
 def lbfd_kernel_launches() -> int:
     return int(load().lbfd_kernel_launches())
 
 
 def lbfd_struct_sizes():
-    a, b = c_int64(), c_int64()
-    _check(load().lbfd_struct_sizes(ctypes.byref(a), ctypes.byref(b)), "lbfd_struct_sizes")
-    return a.value, b.value
+    a, b, c = c_int64(), c_int64(), c_int64()
+    _check(load().lbfd_struct_sizes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "lbfd_struct_sizes")
+    return a.value, b.value, c.value

@@ -35,9 +35,19 @@ def test_every_declared_symbol_is_exported_and_bound():
 
 
 def test_struct_layouts_match_binding():
-    o, b = abi.lbfd_struct_sizes()
+    o, b, m = abi.lbfd_struct_sizes()
     assert o == ctypes.sizeof(abi.Options)
     assert b == ctypes.sizeof(abi.Obs)
+    assert m == ctypes.sizeof(abi.Member)
+
+
+def test_ensemble_rejects_bad_members_without_gpu():
+    lib = abi.load()
+    h = ctypes.c_void_p()
+    bad = abi.make_members([dict(dims=(8, 8), tau=0.4, rho_mean=1.0, seed=1)])
+    assert lib.lbfd_ensemble_create(ctypes.byref(h), lb.D2Q9, lb.F32, 0, 0, bad, 1, None) in (abi.EINVAL, abi.ECUDA)
+    assert lib.lbfd_ensemble_create(ctypes.byref(h), lb.D2Q9, 9, 0, 0, bad, 1, None) == abi.EINVAL
+    assert lib.lbfd_ensemble_create(ctypes.byref(h), lb.D2Q9, lb.F32, 0, 0, bad, 0, None) == abi.EINVAL
 
 
 def test_options_defaults():
