@@ -240,11 +240,12 @@ def run_ensemble(args):
         sp["init"] = lb.INIT_UNIFORM
     stream = torch.cuda.Stream()
     ens = lb.Ensemble(lb.D2Q9, specs, stream=stream)
-    n, sites, _, _ = ens.query()
-    vx = ens.tune(steps=3)
+    n, sites, _, _, _ = ens.query()
+    vx, passes = ens.tune(steps=3)
     ens.step(args.warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = lb.abi.lbfd_kernel_launches()
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -252,6 +253,7 @@ def run_ensemble(args):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    launches = lb.abi.lbfd_kernel_launches() - launches0
     ens.close()
     glups = sites * args.steps / (ms * 1e-3) / 1e9
     # the same members run the plain way: one handle and one launch per simulation per step
@@ -281,15 +283,15 @@ def run_ensemble(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"ensemble of {n} D2Q9 FP32 lattices, sides log-uniform in [32, 512], rho_mean "
                                f"U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian noise",
-                   "sites": sites, "items_per_thread_sites": vx, "graph_steps": 16,
+                   "sites": sites, "sites_per_item_max": vx, "tile_passes": passes, "graph_steps": 16,
                    "l2": "inputs larger than L2: %.0f MB per population buffer" % (36.0 * sites / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": 72 * sites, "kernel": "k_ens_step",
+                     "traffic": None, "algorithmic_bytes_per_launch": 72 * sites, "kernel": "k_batch_step",
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "per_sim_baseline": {"value": per_sim, "unit": UNIT, "sims": len(sub), "steps": args.per_sim_steps,
                              "how": "one lbfd handle and one k_step launch per simulation per step, same stream"},
         "speedup_vs_per_sim": glups / per_sim,
-        "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
+        "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 

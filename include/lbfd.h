@@ -230,7 +230,10 @@ int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void *f_dev, int
  * per time step covers every member, and chunks of steps are captured into a
  * CUDA graph and replayed.  Every member evolves exactly as the same lattice
  * would under lbfd_create_ex with the same parameters (same arithmetic,
- * same noise keys).  Members share one precision, noise mode and law. */
+ * same noise keys).  Members share one precision, noise mode and law.
+ * Work decomposition: a work item is 1 or 2 sites of a row (2 only where Lx
+ * is even), a tile is `passes` x 256 items of one member, and a persistent
+ * grid walks the tiles. */
 typedef struct lbfd_member {
     int64_t dims[3];    /* Lx, Ly, Lz; trailing dims of lower-D lattices must be 1 */
     double tau;         /* > 1/2 */
@@ -258,12 +261,15 @@ int lbfd_ensemble_destroy(lbfd_ens_t e);
 int lbfd_ensemble_step(lbfd_ens_t e, int64_t n);
 int lbfd_ensemble_sync(lbfd_ens_t e);
 
-/* Times the candidate work decompositions (1 or 2 sites per item) over
- * `steps` launches that write only the spare buffer, keeps the fastest and
- * reports it.  The state and t are unchanged. */
-int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen);
+/* Times the candidate work decompositions (at most 1 or 2 sites per item,
+ * times tiles of 1, 2, 4 or 8 passes) over `steps` launches each that write
+ * only the spare buffers, keeps the fastest and reports it (either output
+ * may be NULL).  The state and t are unchanged.  Synchronous. */
+int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen);
 
-int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx);
+/* Members, total sites, t and the current decomposition (any pointer may be NULL). */
+int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx,
+                        int32_t *passes);
 
 /* Per-member state in FP64, layout [i][site] (as lbfd_get_f / lbfd_set_f),
  * and FP64 mass.  Synchronous. */

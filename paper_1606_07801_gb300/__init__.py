@@ -174,7 +174,8 @@ class Ensemble:
     def sync(self) -> None:
         abi.lbfd_ensemble_sync(self.h)
 
-    def tune(self, steps: int = 3) -> int:
+    def tune(self, steps: int = 3):
+        """Picks the fastest work decomposition; returns (vx, passes)."""
         return abi.lbfd_ensemble_tune(self.h, steps)
 
     def query(self):

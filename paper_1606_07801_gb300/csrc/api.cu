@@ -56,6 +56,8 @@ int lattice_q(int lattice) { return lattice == LBFD_D1Q3 ? 3 : (lattice == LBFD_
 
 int lbfd::set_last_error(int code, const std::string &msg) { return fail(code, msg); }
 
+void lbfd::count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 struct lbfd_sim {
   lbfd_options opt{};
   int Q = 0, D = 0, elem = 0;

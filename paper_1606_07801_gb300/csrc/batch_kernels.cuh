@@ -1,0 +1,140 @@
+// Batched step: many independent lattices of one lattice type, each with its
+// own size, relaxation time, mean density, seed, Philox lattice id and step
+// counter, advanced by one launch per time step.  Used by the ensemble
+// (members that start together) and by the server (members admitted at
+// different times).
+//
+// Memory.  All members live in one device buffer `base`; member m keeps its
+// two population blocks at value offsets off[0] and off[1].  Its own step
+// counter is t = clock - t0, where clock counts the launches of the batch;
+// the stored state is in block t & 1 and the step writes block (t & 1) ^ 1.
+//
+// Work.  A launch walks a flat list of tiles with a persistent grid.  Member m
+// owns tiles [tile_start[m], tile_start[m + 1]); a tile is `passes` x 256
+// consecutive work items of one member, and an item is vx sites of a row
+// (vx = 2 for even Lx, else 1).  Per tile, warp 0 finds the member by a
+// 32-way search of tile_start and copies that member's step arguments into
+// shared memory; every item then runs the per-site code of the single-lattice
+// kernels, so a member evolves bit-identically to the same lattice stepped
+// alone.  The step arguments (relaxation constants and the Philox words of
+// the member's t) are written once per launch and member by k_batch_prep.
+#pragma once
+
+#include "step_kernels.cuh"
+
+namespace lbfd {
+
+constexpr int kBatchThreads = 256;
+
+// One member, as the host builds it (constant while the member is listed).
+struct BatchMember {
+  int32_t Lx, Ly, Lz, vx;  // vx: sites per work item, 1 or 2 (2 needs Lx even)
+  int64_t N;               // sites
+  int64_t off[2];          // first value of population block 0 / 1 in the batch buffer
+  int64_t tile0;           // first tile of the member in the launch's tile list
+  uint64_t t0;             // clock value at which the member's own step counter is 0
+  uint64_t seed;
+  uint32_t lattice_id, pad;
+  double tau, rho_mean;
+};
+
+// What one launch needs of one member (written by k_batch_prep).
+struct alignas(16) BatchStep {
+  StepArgs a;          // sizes, relaxation and noise constants, Philox words of this step
+  int64_t src, dst;    // value offsets of the blocks read and written
+  int64_t tile0;
+  int32_t items, cols; // work items and items per row
+  int32_t vx, pad[3];
+};
+static_assert(sizeof(BatchStep) % 16 == 0, "BatchStep is copied as int4 words");
+
+// Step arguments of every member for the clock value *clock_dev (or `clock`
+// when clock_dev is null).
+__global__ void k_batch_prep(const BatchMember *__restrict__ members, int n, const uint64_t *__restrict__ clock_dev,
+                             uint64_t clock, int noise_mode, int noise_dist, BatchStep *__restrict__ out);
+
+// Index m with tile_start[m] <= tile < tile_start[m + 1] (tile_start strictly
+// increasing, tile_start[0] = 0 <= tile), found by warp 0: each round tests
+// 32 evenly spaced splitters and keeps the segment of the last one passed.
+__device__ __forceinline__ int batch_find_member(const int64_t *__restrict__ tile_start, int n, int64_t tile) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, len = n;
+  while (len > 1) {
+    const int stride = (len + 31) >> 5;
+    const int idx = lo + lane * stride;
+    const bool pass = idx < lo + len && __ldg(tile_start + idx) <= tile;
+    const unsigned b = __ballot_sync(0xffffffffu, pass);
+    const int k = 31 - __clz(b);
+    const int nlo = lo + k * stride;
+    len = min(stride, lo + len - nlo);
+    lo = nlo;
+  }
+  return lo;
+}
+
+template <int LAT, typename S, int NOISE>
+__global__ void __launch_bounds__(kBatchThreads, step_min_blocks<LAT, S>())
+    k_batch_step(S *__restrict__ base, const BatchStep *__restrict__ steps, const int64_t *__restrict__ tile_start,
+                 int nmembers, int64_t ntiles, int passes) {
+  // two copies: the copy for tile k + 1 is written while no thread reads the
+  // copy of tile k - 1 any more (one barrier per tile)
+  __shared__ BatchStep sb[2];
+  int buf = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    if (threadIdx.x < 32) {
+      const int m = batch_find_member(tile_start, nmembers, tile);
+      const int4 *g = reinterpret_cast<const int4 *>(steps + m);
+      int4 *s = reinterpret_cast<int4 *>(&sb[buf]);
+      for (int k = threadIdx.x; k < int(sizeof(BatchStep) / 16); k += 32) s[k] = g[k];
+    }
+    __syncthreads();
+    const BatchStep &b = sb[buf];
+    const S *src = base + b.src;
+    S *dst = base + b.dst;
+    const int first = static_cast<int>(tile - b.tile0) * passes * kBatchThreads + threadIdx.x;
+    for (int p = 0; p < passes; ++p) {
+      const int item = first + p * kBatchThreads;
+      if (item < b.items) {
+        const int row = item / b.cols;
+        const int col = item - row * b.cols;
+        const int y = row % b.a.Ly, z = row / b.a.Ly;
+        if (b.vx == 2)
+          step_vec_body<LAT, S, 2, NOISE>(src, dst, b.a, col * 2, y, z);
+        else
+          step_scalar_body<LAT, S, NOISE>(src, dst, b.a, col, y, z);
+      }
+    }
+  }
+}
+
+template <int LAT, typename S>
+cudaError_t batch_step_t(void *base, const BatchStep *steps, const int64_t *tile_start, int nmembers, int64_t ntiles,
+                         int passes, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
+  S *b = static_cast<S *>(base);
+  if (noise_mode == kNoiseOff)
+    k_batch_step<LAT, S, kStepNoiseOff><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
+                                                                            passes);
+  else if (noise_dist == kGaussian)
+    k_batch_step<LAT, S, kStepNoiseGauss><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
+                                                                              passes);
+  else
+    k_batch_step<LAT, S, kStepNoiseFlat><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
+                                                                             passes);
+  return cudaGetLastError();
+}
+
+// Resident blocks per SM of the batch kernel (sizes the persistent grid).
+template <int LAT, typename S>
+int batch_blocks_per_sm(int noise_mode, int noise_dist) {
+  int nb = 0;
+  cudaError_t e;
+  if (noise_mode == kNoiseOff)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseOff>, kBatchThreads, 0);
+  else if (noise_dist == kGaussian)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseGauss>, kBatchThreads, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseFlat>, kBatchThreads, 0);
+  return e == cudaSuccess && nb > 0 ? nb : 1;
+}
+
+}  // namespace lbfd

@@ -131,21 +131,36 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
 // Records msg as the calling thread's lbfd_last_error() and returns code.
 int set_last_error(int code, const std::string &msg);
 
-// Ensemble step launchers (one translation unit per lattice); vx is 1 or 2.
-struct EnsMember;
-struct EnsTile;
-cudaError_t launch_ens_step_d1q3(int precision, int vx, const void *src, void *dst, const EnsMember *members,
-                                 const EnsTile *tiles, int ntiles, const uint64_t *t_dev, int noise_mode, int noise_dist,
-                                 int grid, cudaStream_t stream);
-cudaError_t launch_ens_step_d2q9(int precision, int vx, const void *src, void *dst, const EnsMember *members,
-                                 const EnsTile *tiles, int ntiles, const uint64_t *t_dev, int noise_mode, int noise_dist,
-                                 int grid, cudaStream_t stream);
-cudaError_t launch_ens_step_d3q19(int precision, int vx, const void *src, void *dst, const EnsMember *members,
-                                  const EnsTile *tiles, int ntiles, const uint64_t *t_dev, int noise_mode,
-                                  int noise_dist, int grid, cudaStream_t stream);
-int ens_blocks_per_sm_d1q3(int precision, int vx, int noise_mode, int noise_dist);
-int ens_blocks_per_sm_d2q9(int precision, int vx, int noise_mode, int noise_dist);
-int ens_blocks_per_sm_d3q19(int precision, int vx, int noise_mode, int noise_dist);
+// Batched step (batch_kernels.cuh): many lattices of one type per launch.
+struct BatchMember;
+struct BatchStep;
+cudaError_t launch_batch_step_d1q3(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
+                                   int nmembers, int64_t ntiles, int passes, int noise_mode, int noise_dist, int grid,
+                                   cudaStream_t stream);
+cudaError_t launch_batch_step_d2q9(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
+                                   int nmembers, int64_t ntiles, int passes, int noise_mode, int noise_dist, int grid,
+                                   cudaStream_t stream);
+cudaError_t launch_batch_step_d3q19(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
+                                    int nmembers, int64_t ntiles, int passes, int noise_mode, int noise_dist, int grid,
+                                    cudaStream_t stream);
+int batch_blocks_per_sm_d1q3(int precision, int noise_mode, int noise_dist);
+int batch_blocks_per_sm_d2q9(int precision, int noise_mode, int noise_dist);
+int batch_blocks_per_sm_d3q19(int precision, int noise_mode, int noise_dist);
+
+// batch.cu: lattice dispatch of the above, the per-launch argument kernel
+// and the tile assignment.
+cudaError_t launch_batch_step(int lattice, int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
+                              int nmembers, int64_t ntiles, int passes, int noise_mode, int noise_dist, int grid,
+                              cudaStream_t stream);
+int batch_blocks_per_sm(int lattice, int precision, int noise_mode, int noise_dist);
+// Step arguments of members[0..n) for the clock *clock_dev (clock when null).
+cudaError_t launch_batch_prep(const BatchMember *members, int n, const uint64_t *clock_dev, uint64_t clock,
+                              int noise_mode, int noise_dist, BatchStep *out, cudaStream_t stream);
+// clock += 1 on the device (between the launches of a captured graph).
+cudaError_t launch_clock_advance(uint64_t *clock_dev, cudaStream_t stream);
+
+// Records n launches of this library's kernels (lbfd_kernel_launches).
+void count_launches(int64_t n);
 
 // Host copy of the moment matrix the kernels use, m[a*Q + i].
 int basis_table(int lattice, double *m);

@@ -96,8 +96,8 @@ SIGNATURES = {
     "lbfd_ensemble_destroy": (c_int32, [c_void_p]),
     "lbfd_ensemble_step": (c_int32, [c_void_p, c_int64]),
     "lbfd_ensemble_sync": (c_int32, [c_void_p]),
-    "lbfd_ensemble_tune": (c_int32, [c_void_p, c_int32, P(c_int32)]),
-    "lbfd_ensemble_query": (c_int32, [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int32)]),
+    "lbfd_ensemble_tune": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32)]),
+    "lbfd_ensemble_query": (c_int32, [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int32), P(c_int32)]),
     "lbfd_ensemble_get_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_set_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_mass": (c_int32, [c_void_p, c_int32, P(c_double)]),
@@ -337,17 +337,18 @@ def lbfd_ensemble_sync(e: int) -> None:
     _check(load().lbfd_ensemble_sync(e), "lbfd_ensemble_sync")
 
 
-def lbfd_ensemble_tune(e: int, steps: int = 3) -> int:
-    v = c_int32()
-    _check(load().lbfd_ensemble_tune(e, steps, ctypes.byref(v)), "lbfd_ensemble_tune")
-    return v.value
+def lbfd_ensemble_tune(e: int, steps: int = 3):
+    """Returns the chosen (sites per item at most, tile passes)."""
+    v, p = c_int32(), c_int32()
+    _check(load().lbfd_ensemble_tune(e, steps, ctypes.byref(v), ctypes.byref(p)), "lbfd_ensemble_tune")
+    return v.value, p.value
 
 
 def lbfd_ensemble_query(e: int):
-    n, sites, t, vx = c_int32(), c_int64(), c_int64(), c_int32()
-    _check(load().lbfd_ensemble_query(e, ctypes.byref(n), ctypes.byref(sites), ctypes.byref(t), ctypes.byref(vx)),
-           "lbfd_ensemble_query")
-    return n.value, sites.value, t.value, vx.value
+    n, sites, t, vx, passes = c_int32(), c_int64(), c_int64(), c_int32(), c_int32()
+    _check(load().lbfd_ensemble_query(e, ctypes.byref(n), ctypes.byref(sites), ctypes.byref(t), ctypes.byref(vx),
+                                      ctypes.byref(passes)), "lbfd_ensemble_query")
+    return n.value, sites.value, t.value, vx.value, passes.value
 
 
 def lbfd_ensemble_get_f(e: int, member: int, Q: int, N: int) -> np.ndarray:
