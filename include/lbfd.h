@@ -277,6 +277,143 @@ int lbfd_ensemble_get_f(lbfd_ens_t e, int32_t member, double *f_host);
 int lbfd_ensemble_set_f(lbfd_ens_t e, int32_t member, const double *f_host);
 int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
 
+/* ---- serving: continuous batching of simulation requests ----------------
+ * A server keeps many simulations resident on one GPU and advances them
+ * together.  Requests (lattice, size, tau, rho_mean, seed, steps, initial
+ * state, result kind) queue on submission.  Between time steps the server
+ * admits queued requests, in arrival order with later ones allowed past an
+ * earlier one that does not fit, while a slot is free and their two
+ * population blocks fit in its device-memory budget (one arena allocated at
+ * creation; admission and retirement allocate nothing).  Every time step
+ * is one launch per lattice type covering all resident simulations of that
+ * type (the batched kernel of the ensemble), so requests that arrive while
+ * others run join the next step and their work overlaps on the device.  A
+ * simulation that has taken its steps is read back on a second stream while
+ * the others go on, and its memory returns to the arena once the copy is
+ * done.  Each simulation keeps its own step counter t (from 0) and its own
+ * Philox key and lattice id, so its result is bit-identical to the same
+ * lattice run alone by lbfd_create_ex / lbfd_step / lbfd_get_f_raw or
+ * lbfd_moments.  Members share one precision and noise mode and law.  A
+ * server is used by one host thread at a time. */
+#define LBFD_INIT_HOST 3    /* request only: f(x, 0) copied from in_host (storage format, [i][site]) */
+#define LBFD_RESULT_F 0     /* result: f(x, t = steps) in the storage format, Q*N values [i][site] */
+#define LBFD_RESULT_RHO 1   /* result: rho(x, t = steps) as N doubles */
+#define LBFD_RESULT_NONE 2  /* no result copy; completion only */
+
+#define LBFD_POLICY_FIFO 0      /* admit in arrival order (later requests may pass one that does not fit) */
+#define LBFD_POLICY_SHORTEST 1  /* admit the request with the fewest site updates (sites x steps) first */
+
+#define LBFD_REQ_UNKNOWN (-1)
+#define LBFD_REQ_QUEUED 0
+#define LBFD_REQ_RUNNING 1  /* resident, or its result is being copied */
+#define LBFD_REQ_DONE 2     /* result written to the host */
+
+typedef struct lbfd_server_options {
+    int32_t precision;      /* LBFD_F32 (default) / LBFD_F64 / LBFD_F32_F16 / LBFD_F32_BF16 */
+    int32_t noise_mode;     /* LBFD_NOISE_* */
+    int32_t noise_dist;     /* LBFD_GAUSSIAN / LBFD_UNIFORM */
+    int32_t device;         /* CUDA device ordinal; -1 = current */
+    int64_t hbm_budget;     /* bytes of the device arena for resident states (allocated at creation) */
+    int64_t max_active_sites; /* admit only while resident sites stay <= this (0 = no limit) */
+    int32_t max_active;     /* simulations resident at once (<= 65536) */
+    int32_t max_ahead;      /* time steps the host may queue ahead of the GPU (>= 1) */
+    int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
+    int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
+    int32_t reserved[8];
+} lbfd_server_options;
+
+typedef struct lbfd_request {
+    int32_t lattice;        /* LBFD_D1Q3 / LBFD_D2Q9 / LBFD_D3Q19 */
+    int32_t init;           /* LBFD_INIT_UNIFORM / LBFD_INIT_SINE / LBFD_INIT_HOST */
+    int64_t dims[3];        /* Lx, Ly, Lz; trailing dims of lower-D lattices must be 1 */
+    double tau;             /* > 1/2 */
+    double rho_mean;        /* >= 0 */
+    uint64_t seed;          /* Philox key */
+    uint32_t lattice_id;    /* Philox counter word 1 */
+    int32_t result;         /* LBFD_RESULT_* */
+    int64_t steps;          /* time steps to take, >= 0 */
+    double sine_amp;        /* LBFD_INIT_SINE */
+    int32_t sine_k[3];
+    int32_t reserved;
+    const void *in_host;    /* LBFD_INIT_HOST: Q*N values; read when the request is admitted */
+    void *out_host;         /* result buffer (caller-owned, written asynchronously; pinned memory
+                               lets the copy overlap the GPU work, pageable memory makes the
+                               host wait for it); NULL in lbfd_server_run_trace = its sink */
+} lbfd_request;
+
+typedef struct lbfd_server_stats {
+    int64_t submitted, queued, running, done;
+    int64_t clock;             /* time steps launched so far */
+    int64_t site_updates;      /* sum of sites x steps over finished requests */
+    int64_t resident_bytes, peak_resident_bytes; /* arena bytes held by admitted requests */
+    int64_t resident_sites, peak_resident_sites;
+    int32_t active, peak_active; /* resident simulations */
+    int64_t launches;          /* kernels launched by this server */
+} lbfd_server_stats;
+
+typedef struct lbfd_server *lbfd_server_t;
+
+/* Defaults: FP32, local Gaussian noise, current device, 1 GiB budget, no
+ * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO. */
+int lbfd_server_options_init(lbfd_server_options *opt);
+
+/* Creates a server: one device arena of hbm_budget bytes, two streams
+ * (compute and copy), and pinned staging for its tables.  LBFD_ENOMEM if
+ * the arena cannot be allocated. */
+int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt);
+
+/* Waits for all queued GPU work, then frees everything the server
+ * allocated.  Results already copied stay valid; unfinished requests are
+ * dropped.  NULL is accepted. */
+int lbfd_server_destroy(lbfd_server_t s);
+
+/* Queues a request and returns its id (0, 1, 2, ... in submission order).
+ * Touches no GPU state.  LBFD_EINVAL for a malformed request and for one
+ * that could never be admitted (its blocks exceed the whole budget or the
+ * site limit, or no result buffer is given for a result kind that needs
+ * one).  in_host and out_host must stay valid until the request is done. */
+int lbfd_server_submit(lbfd_server_t s, const lbfd_request *req, int64_t *id);
+
+/* Does up to max_steps rounds of: note finished copies, admit queued
+ * requests, launch one time step of every resident simulation.  Returns
+ * early when nothing is resident.  Blocks only while max_ahead steps are
+ * already queued on the GPU.  *unfinished (may be NULL) = requests not done. */
+int lbfd_server_pump(lbfd_server_t s, int32_t max_steps, int64_t *unfinished);
+
+/* Pumps until every submitted request is done. */
+int lbfd_server_drain(lbfd_server_t s);
+
+/* State of request id; latency_s (may be NULL) = seconds from submission
+ * (or trace arrival) until the host saw its result copy finish, once done. */
+int lbfd_server_poll(lbfd_server_t s, int64_t id, int32_t *state, double *latency_s);
+
+int lbfd_server_get_stats(lbfd_server_t s, lbfd_server_stats *st);
+
+/* The request loop for a fixed trace: submits reqs[k] when arrival_s[k]
+ * seconds (non-decreasing) have passed since the call began, pumps one
+ * step at a time, and returns when all are done.  Results of requests with
+ * out_host == NULL go to the caller's pinned buffer sink_host (sink_bytes),
+ * in a range reserved when the result is ready (while the sink is full, a
+ * finished simulation waits in device memory) and released when its copy is
+ * seen done (the contents are not kept).  latency_s[k] = completion - arrival;
+ * *makespan_s = last completion - call start.  Requests already submitted
+ * are served along with the trace. */
+int lbfd_server_run_trace(lbfd_server_t s, const lbfd_request *reqs, const double *arrival_s, int32_t n,
+                          void *sink_host, int64_t sink_bytes, double *latency_s, double *makespan_s);
+
+/* ---- host range allocator --------------------------------------------------
+ * The first-fit allocator the server carves its device arena and its host
+ * result staging with: ranges of [0, capacity), sizes rounded up to
+ * `align` (a power of two), freed neighbours coalesced.  Host only. */
+typedef struct lbfd_pool *lbfd_pool_t;
+int lbfd_pool_create(lbfd_pool_t *out, int64_t capacity, int64_t align);
+int lbfd_pool_destroy(lbfd_pool_t p);
+/* *offset of a free range of size bytes; LBFD_EBUSY (and *offset = -1) when none fits. */
+int lbfd_pool_alloc(lbfd_pool_t p, int64_t size, int64_t *offset);
+/* LBFD_EINVAL when no allocated range starts at offset. */
+int lbfd_pool_free(lbfd_pool_t p, int64_t offset);
+int lbfd_pool_stats(lbfd_pool_t p, int64_t *used, int64_t *largest_free, int32_t *free_ranges);
+
 /* Message for the calling thread's last failure ("" if none). */
 const char *lbfd_last_error(void);
 
@@ -287,6 +424,9 @@ int64_t lbfd_kernel_launches(void);
  * into the library, for bindings that mirror the structs.  Any pointer may be
  * NULL. */
 int lbfd_struct_sizes(int64_t *options_bytes, int64_t *obs_bytes, int64_t *member_bytes);
+
+/* sizeof(lbfd_server_options), sizeof(lbfd_request), sizeof(lbfd_server_stats). */
+int lbfd_server_struct_sizes(int64_t *options_bytes, int64_t *request_bytes, int64_t *stats_bytes);
 
 #ifdef __cplusplus
 }

@@ -14,15 +14,19 @@ import numpy as np
 
 from . import build as _build_mod
 from .lbfd import (D1Q3, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
-                   F64, GAUSSIAN,
-                   INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL, NOISE_LOCAL, NOISE_OFF, OK,
-                   Q_OF, UNIFORM, LbfdError, Options, load)
+                   F64, GAUSSIAN, INIT_HOST, INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL,
+                   NOISE_LOCAL, NOISE_OFF, OK, POLICY_FIFO, POLICY_SHORTEST, Q_OF, REQ_DONE, REQ_QUEUED, REQ_RUNNING,
+                   REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, LbfdError, Options, load)
 from . import lbfd as abi
 
-__all__ = ["Simulation", "Ensemble", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
+__all__ = ["Simulation", "Ensemble", "Server", "STORAGE_DTYPE", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
            "F32_F16", "F32_BF16",
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
-           "INIT_NONE", "Q_OF", "D_OF"]
+           "INIT_NONE", "INIT_HOST", "RESULT_F", "RESULT_RHO", "RESULT_NONE", "POLICY_FIFO", "POLICY_SHORTEST",
+           "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE", "REQ_UNKNOWN", "Q_OF", "D_OF"]
+
+# numpy type of one stored value per precision (bfloat16 as its raw 16 bits)
+STORAGE_DTYPE = {F32: np.float32, F64: np.float64, F32_F16: np.float16, F32_BF16: np.uint16}
 
 
 def build(force: bool = False) -> str:
@@ -189,3 +193,81 @@ class Ensemble:
 
     def mass(self, member: int) -> float:
         return abi.lbfd_ensemble_mass(self.h, member)
+
+
+class Server:
+    """Continuous-batching server of simulation requests on one GPU (see
+    ``lbfd_server_*`` in include/lbfd.h).  Results land in numpy arrays this
+    object allocates (or the caller passes) and keeps alive until read."""
+
+    def __init__(self, *, precision: int = F32, noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN,
+                 hbm_budget: int = 1 << 30, max_active: int = 1024, max_ahead: int = 4, passes: int = 1,
+                 policy: int = POLICY_FIFO, max_active_sites: int = 0, device: int = -1):
+        o = abi.lbfd_server_options_init()
+        o.precision, o.noise_mode, o.noise_dist, o.device = precision, noise_mode, noise_dist, device
+        o.hbm_budget, o.max_active, o.max_ahead, o.passes = int(hbm_budget), max_active, max_ahead, passes
+        o.policy, o.max_active_sites = policy, int(max_active_sites)
+        self.precision = precision
+        self._bufs = {}
+        self.h = abi.lbfd_server_create(o)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            h, self.h = self.h, None
+            abi.lbfd_server_destroy(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, lattice: int, dims, tau: float, rho_mean: float, seed: int, steps: int, *, lattice_id: int = 0,
+               init: int = INIT_UNIFORM, sine_amp: float = 0.0, sine_k=(1, 0, 0), f0=None,
+               result: int = RESULT_F, out=None) -> int:
+        """Queues a simulation; f0 (storage format, [Q, N]) is its initial f
+        when given.  Returns the request id."""
+        q, n = Q_OF[lattice], int(np.prod(dims))
+        keep = []
+        in_ptr = None
+        if f0 is not None:
+            f0 = np.ascontiguousarray(f0, dtype=STORAGE_DTYPE[self.precision])
+            assert f0.size == q * n
+            init, in_ptr = INIT_HOST, f0.ctypes.data
+            keep.append(f0)
+        if result != RESULT_NONE and out is None:
+            out = (np.empty((q, n), dtype=STORAGE_DTYPE[self.precision]) if result == RESULT_F
+                   else np.empty(n, dtype=np.float64))
+        out_ptr = None if out is None else out.ctypes.data
+        req = abi.make_request(lattice, dims, tau, rho_mean, seed, steps, lattice_id=lattice_id, init=init,
+                               sine_amp=sine_amp, sine_k=sine_k, result=result, in_host=in_ptr, out_host=out_ptr)
+        rid = abi.lbfd_server_submit(self.h, req)
+        self._bufs[rid] = (out, keep)
+        return rid
+
+    def pump(self, max_steps: int = 1) -> int:
+        return abi.lbfd_server_pump(self.h, max_steps)
+
+    def drain(self) -> None:
+        abi.lbfd_server_drain(self.h)
+
+    def poll(self, rid: int):
+        """(state, latency in seconds or -1)."""
+        return abi.lbfd_server_poll(self.h, rid)
+
+    def result(self, rid: int):
+        """The result array of a finished request (raw storage format for
+        RESULT_F, FP64 density for RESULT_RHO)."""
+        state, _ = self.poll(rid)
+        if state != REQ_DONE:
+            raise RuntimeError(f"request {rid} is not done (state {state})")
+        return self._bufs[rid][0]
+
+    def stats(self) -> dict:
+        return abi.lbfd_server_get_stats(self.h)

@@ -23,7 +23,10 @@ D1Q3, D2Q9, D3Q19 = 0, 1, 2
 F32, F64, F32_F16, F32_BF16 = 0, 1, 2, 3
 NOISE_LOCAL, NOISE_GLOBAL, NOISE_OFF = 0, 1, 2
 GAUSSIAN, UNIFORM = 0, 1
-INIT_UNIFORM, INIT_SINE, INIT_NONE = 0, 1, 2
+INIT_UNIFORM, INIT_SINE, INIT_NONE, INIT_HOST = 0, 1, 2, 3
+RESULT_F, RESULT_RHO, RESULT_NONE = 0, 1, 2
+POLICY_FIFO, POLICY_SHORTEST = 0, 1
+REQ_UNKNOWN, REQ_QUEUED, REQ_RUNNING, REQ_DONE = -1, 0, 1, 2
 MAX_Q, MAX_MODES = 19, 16
 
 Q_OF = {D1Q3: 3, D2Q9: 9, D3Q19: 19}
@@ -56,6 +59,35 @@ class Member(ctypes.Structure):
         ("dims", c_int64 * 3), ("tau", c_double), ("rho_mean", c_double), ("seed", c_uint64),
         ("lattice_id", c_uint32), ("init", c_int32), ("sine_amp", c_double), ("sine_k", c_int32 * 3),
         ("reserved", c_int32),
+    ]
+
+
+class ServerOptions(ctypes.Structure):
+    """Mirror of ``lbfd_server_options``."""
+    _fields_ = [
+        ("precision", c_int32), ("noise_mode", c_int32), ("noise_dist", c_int32), ("device", c_int32),
+        ("hbm_budget", c_int64), ("max_active_sites", c_int64), ("max_active", c_int32), ("max_ahead", c_int32),
+        ("passes", c_int32), ("policy", c_int32), ("reserved", c_int32 * 8),
+    ]
+
+
+class Request(ctypes.Structure):
+    """Mirror of ``lbfd_request``."""
+    _fields_ = [
+        ("lattice", c_int32), ("init", c_int32), ("dims", c_int64 * 3), ("tau", c_double), ("rho_mean", c_double),
+        ("seed", c_uint64), ("lattice_id", c_uint32), ("result", c_int32), ("steps", c_int64),
+        ("sine_amp", c_double), ("sine_k", c_int32 * 3), ("reserved", c_int32), ("in_host", c_void_p),
+        ("out_host", c_void_p),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    """Mirror of ``lbfd_server_stats``."""
+    _fields_ = [
+        ("submitted", c_int64), ("queued", c_int64), ("running", c_int64), ("done", c_int64), ("clock", c_int64),
+        ("site_updates", c_int64), ("resident_bytes", c_int64), ("peak_resident_bytes", c_int64),
+        ("resident_sites", c_int64), ("peak_resident_sites", c_int64), ("active", c_int32),
+        ("peak_active", c_int32), ("launches", c_int64),
     ]
 
 
@@ -101,6 +133,22 @@ SIGNATURES = {
     "lbfd_ensemble_get_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_set_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_mass": (c_int32, [c_void_p, c_int32, P(c_double)]),
+    "lbfd_server_options_init": (c_int32, [P(ServerOptions)]),
+    "lbfd_server_create": (c_int32, [P(c_void_p), P(ServerOptions)]),
+    "lbfd_server_destroy": (c_int32, [c_void_p]),
+    "lbfd_server_submit": (c_int32, [c_void_p, P(Request), P(c_int64)]),
+    "lbfd_server_pump": (c_int32, [c_void_p, c_int32, P(c_int64)]),
+    "lbfd_server_drain": (c_int32, [c_void_p]),
+    "lbfd_server_poll": (c_int32, [c_void_p, c_int64, P(c_int32), P(c_double)]),
+    "lbfd_server_get_stats": (c_int32, [c_void_p, P(ServerStats)]),
+    "lbfd_server_run_trace": (c_int32, [c_void_p, P(Request), c_void_p, c_int32, c_void_p, c_int64, c_void_p,
+                                        P(c_double)]),
+    "lbfd_server_struct_sizes": (c_int32, [P(c_int64), P(c_int64), P(c_int64)]),
+    "lbfd_pool_create": (c_int32, [P(c_void_p), c_int64, c_int64]),
+    "lbfd_pool_destroy": (c_int32, [c_void_p]),
+    "lbfd_pool_alloc": (c_int32, [c_void_p, c_int64, P(c_int64)]),
+    "lbfd_pool_free": (c_int32, [c_void_p, c_int64]),
+    "lbfd_pool_stats": (c_int32, [c_void_p, P(c_int64), P(c_int64), P(c_int32)]),
     "lbfd_last_error": (ctypes.c_char_p, []),
     "lbfd_kernel_launches": (c_int64, []),
     "lbfd_struct_sizes": (c_int32, [P(c_int64), P(c_int64), P(c_int64)]),
@@ -366,6 +414,120 @@ def lbfd_ensemble_mass(e: int, member: int) -> float:
     m = c_double()
     _check(load().lbfd_ensemble_mass(e, member, ctypes.byref(m)), "lbfd_ensemble_mass")
     return m.value
+
+
+# ---- serving -----------------------------------------------------------------
+
+def lbfd_server_options_init() -> ServerOptions:
+    o = ServerOptions()
+    _check(load().lbfd_server_options_init(ctypes.byref(o)), "lbfd_server_options_init")
+    return o
+
+
+def lbfd_server_create(opt: ServerOptions) -> int:
+    h = c_void_p()
+    _check(load().lbfd_server_create(ctypes.byref(h), ctypes.byref(opt)), "lbfd_server_create")
+    return h.value
+
+
+def lbfd_server_destroy(s: int) -> None:
+    _check(load().lbfd_server_destroy(s), "lbfd_server_destroy")
+
+
+def make_request(lattice: int, dims, tau: float, rho_mean: float, seed: int, steps: int, *, lattice_id: int = 0,
+                 init: int = INIT_UNIFORM, sine_amp: float = 0.0, sine_k=(1, 0, 0), result: int = RESULT_F,
+                 in_host: int | None = None, out_host: int | None = None) -> Request:
+    r = Request()
+    d = [int(x) for x in dims] + [1] * (3 - len(dims))
+    r.lattice, r.init, r.tau, r.rho_mean, r.seed = lattice, init, float(tau), float(rho_mean), int(seed)
+    for a in range(3):
+        r.dims[a] = d[a]
+    sk = list(sine_k) + [0, 0, 0]
+    for a in range(3):
+        r.sine_k[a] = int(sk[a])
+    r.lattice_id, r.result, r.steps, r.sine_amp = int(lattice_id), int(result), int(steps), float(sine_amp)
+    r.in_host, r.out_host = in_host, out_host
+    return r
+
+
+def lbfd_server_submit(s: int, req: Request) -> int:
+    i = c_int64()
+    _check(load().lbfd_server_submit(s, ctypes.byref(req), ctypes.byref(i)), "lbfd_server_submit")
+    return i.value
+
+
+def lbfd_server_pump(s: int, max_steps: int = 1) -> int:
+    left = c_int64()
+    _check(load().lbfd_server_pump(s, max_steps, ctypes.byref(left)), "lbfd_server_pump")
+    return left.value
+
+
+def lbfd_server_drain(s: int) -> None:
+    _check(load().lbfd_server_drain(s), "lbfd_server_drain")
+
+
+def lbfd_server_poll(s: int, rid: int):
+    st, lat = c_int32(), c_double()
+    _check(load().lbfd_server_poll(s, rid, ctypes.byref(st), ctypes.byref(lat)), "lbfd_server_poll")
+    return st.value, lat.value
+
+
+def lbfd_server_get_stats(s: int) -> dict:
+    st = ServerStats()
+    _check(load().lbfd_server_get_stats(s, ctypes.byref(st)), "lbfd_server_get_stats")
+    return {name: getattr(st, name) for name, _ in ServerStats._fields_}
+
+
+def lbfd_server_run_trace(s: int, reqs, arrival_s, sink_ptr: int | None, sink_bytes: int):
+    """Runs a fixed trace (see include/lbfd.h); returns (latencies [s], makespan [s])."""
+    n = len(reqs)
+    arr = (Request * n)(*reqs)
+    arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    lat = np.empty(n, dtype=np.float64)
+    mk = c_double()
+    _check(load().lbfd_server_run_trace(s, arr, _ptr(arrival), n, sink_ptr, int(sink_bytes), _ptr(lat),
+                                        ctypes.byref(mk)), "lbfd_server_run_trace")
+    return lat, mk.value
+
+
+def lbfd_server_struct_sizes():
+    a, b, c = c_int64(), c_int64(), c_int64()
+    _check(load().lbfd_server_struct_sizes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "lbfd_server_struct_sizes")
+    return a.value, b.value, c.value
+
+
+# ---- host range allocator ---------------------------------------------------------
+
+def lbfd_pool_create(capacity: int, align: int) -> int:
+    h = c_void_p()
+    _check(load().lbfd_pool_create(ctypes.byref(h), capacity, align), "lbfd_pool_create")
+    return h.value
+
+
+def lbfd_pool_destroy(p: int) -> None:
+    _check(load().lbfd_pool_destroy(p), "lbfd_pool_destroy")
+
+
+def lbfd_pool_alloc(p: int, size: int) -> int:
+    """Offset of a free range, or -1 when none fits."""
+    off = c_int64()
+    rc = load().lbfd_pool_alloc(p, size, ctypes.byref(off))
+    if rc == EBUSY:
+        return -1
+    _check(rc, "lbfd_pool_alloc")
+    return off.value
+
+
+def lbfd_pool_free(p: int, offset: int) -> None:
+    _check(load().lbfd_pool_free(p, offset), "lbfd_pool_free")
+
+
+def lbfd_pool_stats(p: int):
+    used, largest, nfree = c_int64(), c_int64(), c_int32()
+    _check(load().lbfd_pool_stats(p, ctypes.byref(used), ctypes.byref(largest), ctypes.byref(nfree)),
+           "lbfd_pool_stats")
+    return used.value, largest.value, nfree.value
 
 
 def lbfd_kernel_launches() -> int:

@@ -57,3 +57,39 @@ def ensemble(n: int, side_lo: int = 32, side_hi: int = 512, rho_lo: float = 0.5,
     seeds = (int(seed) * 1000003 + np.arange(n)).astype(np.uint64)
     return [dict(dims=(int(lx[i]), int(ly[i])), rho_mean=float(rho[i]), tau=float(tau[i]), seed=int(seeds[i]))
             for i in range(n)]
+
+
+def served_trace(n: int, rate: float = 500.0, seed: int = 777, d1_range=(256, 65536), d2_side=(32, 1024),
+                 d3_side=(32, 128), steps_range=(100, 10000), rho_lo: float = 0.5, rho_hi: float = 200.0,
+                 tau_lo: float = 0.6, tau_hi: float = 1.5):
+    """A stream of n simulation requests with Poisson arrivals at `rate` per
+    second.  The lattice type is uniform over D1Q3 / D2Q9 / D3Q19; D1Q3
+    lengths, D2Q9 square sides and D3Q19 cube sides are log-uniform in their
+    ranges (rounded), step counts log-uniform in steps_range, mean density
+    and tau uniform, seeds distinct.  Returns (arrival times [s], specs)."""
+    g = rng(seed)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, n))
+    arrivals -= arrivals[0]
+    kinds = g.integers(0, 3, n)
+    u = g.uniform(0.0, 1.0, n)
+    steps = np.rint(np.exp(g.uniform(math.log(steps_range[0]), math.log(steps_range[1]), n))).astype(np.int64)
+    rho = g.uniform(rho_lo, rho_hi, n)
+    tau = g.uniform(tau_lo, tau_hi, n)
+
+    def logu(lo, hi, x):
+        return int(round(math.exp(math.log(lo) + x * (math.log(hi) - math.log(lo)))))
+
+    specs = []
+    for i in range(n):
+        k = int(kinds[i])
+        if k == 0:
+            dims = (logu(*d1_range, u[i]),)
+        elif k == 1:
+            s = logu(*d2_side, u[i])
+            dims = (s, s)
+        else:
+            s = logu(*d3_side, u[i])
+            dims = (s, s, s)
+        specs.append(dict(lattice=k, dims=dims, steps=int(steps[i]), rho_mean=float(rho[i]), tau=float(tau[i]),
+                          seed=int(seed) * 1000003 + i, lattice_id=i))
+    return arrivals, specs
