@@ -222,11 +222,16 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+ENS_LATTICES = {"d1q3": (0, 1, (256, 65536)), "d2q9": (1, 2, (32, 512)), "d3q19": (2, 3, (32, 128))}
+
+
 def run_ensemble(args):
     """Config 4: 4096 independent D2Q9 FP32 lattices (sides log-uniform in
     [32, 512], rho_mean U[0.5, 200], tau U[0.6, 1.5], distinct seeds), one
     launch per time step for all of them (graph-captured chunks), against the
-    plain way of running them: one launch per simulation per step."""
+    plain way of running them: one launch per simulation per step.
+    --ens-lattice d3q19 / d1q3 runs the same kind of ensemble of the other
+    lattices (cube sides in [32, 128], lengths in [256, 65536])."""
     import torch
 
     import paper_1606_07801_gb300 as lb
@@ -234,14 +239,16 @@ def run_ensemble(args):
 
     torch.cuda.set_device(0)
     lb.load()
-    specs = synth.ensemble(args.members)
+    lat, ndim, (lo, hi) = ENS_LATTICES[args.ens_lattice]
+    Q = Q_OF[lat]
+    specs = synth.ensemble(args.members, side_lo=lo, side_hi=hi, ndim=ndim)
     for k, sp in enumerate(specs):
         sp["lattice_id"] = k
         sp["init"] = lb.INIT_UNIFORM
     stream = torch.cuda.Stream()
-    ens = lb.Ensemble(lb.D2Q9, specs, stream=stream)
-    n, sites, _, _, _ = ens.query()
-    vx, passes = ens.tune(steps=3)
+    ens = lb.Ensemble(lat, specs, stream=stream)
+    n, sites, _, _, _, _ = ens.query()
+    vx, passes, bps = ens.tune(steps=3)
     ens.step(args.warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -258,7 +265,7 @@ def run_ensemble(args):
     glups = sites * args.steps / (ms * 1e-3) / 1e9
     # the same members run the plain way: one handle and one launch per simulation per step
     sub = specs[: args.per_sim_members]
-    sims = [lb.Simulation(lb.D2Q9, sp["dims"], sp["tau"], sp["rho_mean"], sp["seed"], lattice_id=sp["lattice_id"],
+    sims = [lb.Simulation(lat, sp["dims"], sp["tau"], sp["rho_mean"], sp["seed"], lattice_id=sp["lattice_id"],
                           stream=stream) for sp in sub]
     for s_ in sims:
         s_.step(3)
@@ -276,17 +283,19 @@ def run_ensemble(args):
     for s_ in sims:
         s_.close()
     peak, peak_kind = measured_peaks()
-    achieved = 72.0 * sites / (ms / args.steps * 1e-3) / 1e9
+    achieved = 8.0 * Q * sites / (ms / args.steps * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"ensemble of {n} D2Q9 FP32 lattices, sides log-uniform in [32, 512], rho_mean "
-                               f"U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian noise",
-                   "sites": sites, "sites_per_item_max": vx, "tile_passes": passes, "graph_steps": 16,
-                   "l2": "inputs larger than L2: %.0f MB per population buffer" % (36.0 * sites / 1e6)},
+        "config": {"workload": f"ensemble of {n} {args.ens_lattice.upper()} FP32 lattices, sides log-uniform in "
+                               f"[{lo}, {hi}], rho_mean U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian "
+                               f"noise",
+                   "sites": sites, "sites_per_item_max": vx, "tile_passes": passes, "blocks_per_sm": bps,
+                   "graph_steps": 16,
+                   "l2": "inputs larger than L2: %.0f MB per population buffer" % (4.0 * Q * sites / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": 72 * sites, "kernel": "k_batch_step",
+                     "traffic": None, "algorithmic_bytes_per_launch": 8 * Q * sites, "kernel": "k_batch_step",
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "per_sim_baseline": {"value": per_sim, "unit": UNIT, "sims": len(sub), "steps": args.per_sim_steps,
                              "how": "one lbfd handle and one k_step launch per simulation per step, same stream"},
@@ -322,7 +331,7 @@ def run_served(args):
     sink = torch.empty(args.sink_mb << 20, dtype=torch.uint8).pin_memory()
     policy = lb.POLICY_SHORTEST if args.policy == "shortest" else lb.POLICY_FIFO
     srv = lb.Server(hbm_budget=int(args.budget_gb * (1 << 30)), max_active=4096, max_ahead=4, passes=args.passes,
-                    policy=policy, max_active_sites=args.max_active_sites)
+                    policy=policy, max_active_sites=args.max_active_sites, occupancy=args.occupancy)
     # warm-up: a short trace of small requests (module load, first launches)
     warm = [abi.make_request(k % 3, [(512,), (64, 64), (16, 16, 16)][k % 3], 1.0, 10.0, 99 + k, 20,
                              result=lb.RESULT_RHO) for k in range(max(3, args.warmup))]
@@ -336,28 +345,30 @@ def run_served(args):
     srv.close()
     glups = lups / makespan / 1e9
     p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
-    # the plain way on a prefix of the same stream: one request at a time
+    # the plain way on (a prefix of) the same stream: one request at a time
     nb = args.requests if args.plain_requests < 0 else min(args.requests, args.plain_requests)
-    stream = torch.cuda.Stream()
-    t_start = time.perf_counter()
-    plain_lat = []
-    for k in range(nb):
-        sp = specs[k]
-        wait = arrivals[k] - (time.perf_counter() - t_start)
-        if wait > 0:
-            time.sleep(wait)
-        with lb.Simulation(sp["lattice"], sp["dims"], sp["tau"], sp["rho_mean"], sp["seed"],
-                           lattice_id=sp["lattice_id"], stream=stream) as sim:
-            sim.step(sp["steps"])
-            sim.moments()
-        plain_lat.append(time.perf_counter() - t_start - arrivals[k])
-    plain_makespan = time.perf_counter() - t_start
-    plain_lups = int(np.sum(sites[:nb] * steps[:nb]))
-    plain = {"value": plain_lups / plain_makespan / 1e9, "unit": UNIT, "requests": nb,
-             "p50_latency_s": float(np.percentile(plain_lat, 50)), "p99_latency_s": float(np.percentile(plain_lat, 99)),
-             "makespan_s": plain_makespan,
-             "how": "the first requests of the same stream taken one at a time in arrival order: one lbfd handle "
-                    "per request, one k_step launch per time step, density read back"}
+    plain = None
+    if nb > 0:
+        stream = torch.cuda.Stream()
+        t_start = time.perf_counter()
+        plain_lat = []
+        for k in range(nb):
+            sp = specs[k]
+            wait = arrivals[k] - (time.perf_counter() - t_start)
+            if wait > 0:
+                time.sleep(wait)
+            with lb.Simulation(sp["lattice"], sp["dims"], sp["tau"], sp["rho_mean"], sp["seed"],
+                               lattice_id=sp["lattice_id"], stream=stream) as sim:
+                sim.step(sp["steps"])
+                sim.moments()
+            plain_lat.append(time.perf_counter() - t_start - arrivals[k])
+        plain_makespan = time.perf_counter() - t_start
+        plain_lups = int(np.sum(sites[:nb] * steps[:nb]))
+        plain = {"value": plain_lups / plain_makespan / 1e9, "unit": UNIT, "requests": nb,
+                 "p50_latency_s": float(np.percentile(plain_lat, 50)),
+                 "p99_latency_s": float(np.percentile(plain_lat, 99)), "makespan_s": plain_makespan,
+                 "how": "the same stream's requests taken one at a time in arrival order: one lbfd handle per "
+                        "request, one k_step launch per time step, density read back"}
     peak, peak_kind = measured_peaks()
     achieved = bytes_alg / makespan / 1e9
     line = {
@@ -368,7 +379,7 @@ def run_served(args):
                                "lattice uniform over D1Q3 (L log-uniform 256-65536) / D2Q9 (side log-uniform "
                                "32-1024) / D3Q19 (side log-uniform 32-128), steps log-uniform 100-10^4, tau "
                                "U[0.6, 1.5], rho_mean U[0.5, 200], FP32, local Gaussian noise, density result",
-                   "hbm_budget_gb": args.budget_gb, "policy": args.policy, "passes": args.passes,
+                   "hbm_budget_gb": args.budget_gb, "policy": args.policy, "passes": args.passes, "occupancy": args.occupancy,
                    "max_active_sites": args.max_active_sites, "site_updates": lups,
                    "step": "one bench step = one served request; value = total site updates / makespan"},
         "latency_s": {"p50": p50, "p99": p99, "mean": float(np.mean(lat)), "max": float(np.max(lat))},
@@ -396,6 +407,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=int, default=4096)
+    ap.add_argument("--ens-lattice", default="d2q9", choices=sorted(ENS_LATTICES))
     ap.add_argument("--per-sim-members", type=int, default=256)
     ap.add_argument("--per-sim-steps", type=int, default=20)
     ap.add_argument("--requests", type=int, default=1000)
@@ -403,6 +415,7 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--policy", default="fifo", choices=["fifo", "shortest"])
     ap.add_argument("--passes", type=int, default=4)
+    ap.add_argument("--occupancy", type=int, default=0)
     ap.add_argument("--max-active-sites", type=int, default=0)
     ap.add_argument("--sink-mb", type=int, default=2048)
     ap.add_argument("--plain-requests", type=int, default=-1)

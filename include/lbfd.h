@@ -262,14 +262,17 @@ int lbfd_ensemble_step(lbfd_ens_t e, int64_t n);
 int lbfd_ensemble_sync(lbfd_ens_t e);
 
 /* Times the candidate work decompositions (at most 1 or 2 sites per item,
- * times tiles of 1, 2, 4 or 8 passes) over `steps` launches each that write
- * only the spare buffers, keeps the fastest and reports it (either output
- * may be NULL).  The state and t are unchanged.  Synchronous. */
-int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen);
+ * times tiles of 1, 2, 4 or 8 passes, times two register/occupancy variants
+ * of the kernel) over `steps` launches each that write only the spare
+ * buffers, keeps the fastest and reports it: sites per item at most, passes,
+ * resident blocks per SM (any output may be NULL).  The state and t are
+ * unchanged.  Synchronous. */
+int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen,
+                       int32_t *blocks_per_sm);
 
 /* Members, total sites, t and the current decomposition (any pointer may be NULL). */
 int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx,
-                        int32_t *passes);
+                        int32_t *passes, int32_t *blocks_per_sm);
 
 /* Per-member state in FP64, layout [i][site] (as lbfd_get_f / lbfd_set_f),
  * and FP64 mass.  Synchronous. */
@@ -319,7 +322,8 @@ typedef struct lbfd_server_options {
     int32_t max_ahead;      /* time steps the host may queue ahead of the GPU (>= 1) */
     int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
     int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
-    int32_t reserved[8];
+    int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
+    int32_t reserved[7];
 } lbfd_server_options;
 
 typedef struct lbfd_request {

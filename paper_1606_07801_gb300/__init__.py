@@ -179,7 +179,7 @@ class Ensemble:
         abi.lbfd_ensemble_sync(self.h)
 
     def tune(self, steps: int = 3):
-        """Picks the fastest work decomposition; returns (vx, passes)."""
+        """Picks the fastest work decomposition; returns (vx, passes, blocks per SM)."""
         return abi.lbfd_ensemble_tune(self.h, steps)
 
     def query(self):
@@ -202,11 +202,11 @@ class Server:
 
     def __init__(self, *, precision: int = F32, noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN,
                  hbm_budget: int = 1 << 30, max_active: int = 1024, max_ahead: int = 4, passes: int = 1,
-                 policy: int = POLICY_FIFO, max_active_sites: int = 0, device: int = -1):
+                 policy: int = POLICY_FIFO, max_active_sites: int = 0, occupancy: int = 0, device: int = -1):
         o = abi.lbfd_server_options_init()
         o.precision, o.noise_mode, o.noise_dist, o.device = precision, noise_mode, noise_dist, device
         o.hbm_budget, o.max_active, o.max_ahead, o.passes = int(hbm_budget), max_active, max_ahead, passes
-        o.policy, o.max_active_sites = policy, int(max_active_sites)
+        o.policy, o.max_active_sites, o.occupancy = policy, int(max_active_sites), occupancy
         self.precision = precision
         self._bufs = {}
         self.h = abi.lbfd_server_create(o)

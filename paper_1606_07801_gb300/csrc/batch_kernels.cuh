@@ -20,6 +20,7 @@
 // the member's t) are written once per launch and member by k_batch_prep.
 #pragma once
 
+#include "fastdiv.cuh"
 #include "step_kernels.cuh"
 
 namespace lbfd {
@@ -44,7 +45,8 @@ struct alignas(16) BatchStep {
   int64_t src, dst;    // value offsets of the blocks read and written
   int64_t tile0;
   int32_t items, cols; // work items and items per row
-  int32_t vx, pad[3];
+  int32_t vx, pad;
+  FastDiv div_cols, div_Ly;  // division by cols and by Ly
 };
 static_assert(sizeof(BatchStep) % 16 == 0, "BatchStep is copied as int4 words");
 
@@ -72,8 +74,16 @@ __device__ __forceinline__ int batch_find_member(const int64_t *__restrict__ til
   return lo;
 }
 
-template <int LAT, typename S, int NOISE>
-__global__ void __launch_bounds__(kBatchThreads, step_min_blocks<LAT, S>())
+// Minimum resident blocks per SM asked of the register allocator: occupancy
+// variant 0 is the single-lattice kernel's choice, variant 1 one block fewer
+// (more registers per thread, no spills); the tuner picks between them.
+template <int LAT, typename S, int OCC>
+constexpr int batch_min_blocks() {
+  return OCC == 0 ? step_min_blocks<LAT, S>() : (step_min_blocks<LAT, S>() > 1 ? step_min_blocks<LAT, S>() - 1 : 1);
+}
+
+template <int LAT, typename S, int NOISE, int OCC>
+__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>())
     k_batch_step(S *__restrict__ base, const BatchStep *__restrict__ steps, const int64_t *__restrict__ tile_start,
                  int nmembers, int64_t ntiles, int passes) {
   // two copies: the copy for tile k + 1 is written while no thread reads the
@@ -95,9 +105,10 @@ __global__ void __launch_bounds__(kBatchThreads, step_min_blocks<LAT, S>())
     for (int p = 0; p < passes; ++p) {
       const int item = first + p * kBatchThreads;
       if (item < b.items) {
-        const int row = item / b.cols;
+        const int row = static_cast<int>(fastdiv(static_cast<uint32_t>(item), b.div_cols));
         const int col = item - row * b.cols;
-        const int y = row % b.a.Ly, z = row / b.a.Ly;
+        const int z = static_cast<int>(fastdiv(static_cast<uint32_t>(row), b.div_Ly));
+        const int y = row - z * b.a.Ly;
         if (b.vx == 2)
           step_vec_body<LAT, S, 2, NOISE>(src, dst, b.a, col * 2, y, z);
         else
@@ -107,34 +118,49 @@ __global__ void __launch_bounds__(kBatchThreads, step_min_blocks<LAT, S>())
   }
 }
 
+template <int LAT, typename S, int OCC>
+cudaError_t batch_step_occ(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int64_t ntiles,
+                           int passes, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
+  if (noise_mode == kNoiseOff)
+    k_batch_step<LAT, S, kStepNoiseOff, OCC><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
+                                                                                 passes);
+  else if (noise_dist == kGaussian)
+    k_batch_step<LAT, S, kStepNoiseGauss, OCC><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
+                                                                                   ntiles, passes);
+  else
+    k_batch_step<LAT, S, kStepNoiseFlat, OCC><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
+                                                                                  ntiles, passes);
+  return cudaGetLastError();
+}
+
 template <int LAT, typename S>
 cudaError_t batch_step_t(void *base, const BatchStep *steps, const int64_t *tile_start, int nmembers, int64_t ntiles,
-                         int passes, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
+                         int passes, int occ, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
   S *b = static_cast<S *>(base);
+  if (occ == 1)
+    return batch_step_occ<LAT, S, 1>(b, steps, tile_start, nmembers, ntiles, passes, noise_mode, noise_dist, grid,
+                                     stream);
+  return batch_step_occ<LAT, S, 0>(b, steps, tile_start, nmembers, ntiles, passes, noise_mode, noise_dist, grid,
+                                   stream);
+}
+
+template <int LAT, typename S, int OCC>
+int batch_blocks_occ(int noise_mode, int noise_dist) {
+  int nb = 0;
+  cudaError_t e;
   if (noise_mode == kNoiseOff)
-    k_batch_step<LAT, S, kStepNoiseOff><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
-                                                                            passes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseOff, OCC>, kBatchThreads, 0);
   else if (noise_dist == kGaussian)
-    k_batch_step<LAT, S, kStepNoiseGauss><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
-                                                                              passes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseGauss, OCC>, kBatchThreads, 0);
   else
-    k_batch_step<LAT, S, kStepNoiseFlat><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
-                                                                             passes);
-  return cudaGetLastError();
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseFlat, OCC>, kBatchThreads, 0);
+  return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 
 // Resident blocks per SM of the batch kernel (sizes the persistent grid).
 template <int LAT, typename S>
-int batch_blocks_per_sm(int noise_mode, int noise_dist) {
-  int nb = 0;
-  cudaError_t e;
-  if (noise_mode == kNoiseOff)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseOff>, kBatchThreads, 0);
-  else if (noise_dist == kGaussian)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseGauss>, kBatchThreads, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseFlat>, kBatchThreads, 0);
-  return e == cudaSuccess && nb > 0 ? nb : 1;
+int batch_blocks_per_sm(int occ, int noise_mode, int noise_dist) {
+  return occ == 1 ? batch_blocks_occ<LAT, S, 1>(noise_mode, noise_dist) : batch_blocks_occ<LAT, S, 0>(noise_mode, noise_dist);
 }
 
 }  // namespace lbfd

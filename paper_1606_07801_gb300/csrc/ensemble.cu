@@ -53,7 +53,7 @@ int d_of(int lattice) { return lattice == LBFD_D1Q3 ? 1 : (lattice == LBFD_D2Q9 
 
 struct lbfd_ens {
   int lattice = 0, precision = 0, noise_mode = 0, noise_dist = 0, elem = 4, Q = 0, device = 0, n = 0;
-  int vx_max = 2, passes = 1, grid = 1;
+  int vx_max = 2, passes = 1, occ = 0, grid = 1, bps = 1;
   int64_t ntiles = 0;
   std::vector<BatchMember> hmem;
   std::vector<int64_t> tile_start;
@@ -77,11 +77,12 @@ struct lbfd_ens {
 
 static cudaError_t ens_launch(lbfd_ens *e) {
   return launch_batch_step(e->lattice, e->precision, e->buf, e->dsteps, e->dtile_start, e->n, e->ntiles, e->passes,
-                           e->noise_mode, e->noise_dist, e->grid, e->stream);
+                           e->occ, e->noise_mode, e->noise_dist, e->grid, e->stream);
 }
 
-// Work decomposition (sites per item, tile passes) and persistent grid.
-static int ens_plan(lbfd_ens *e, int vx_max, int passes) {
+// Work decomposition (sites per item, tile passes, occupancy variant) and
+// persistent grid.
+static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ) {
   for (BatchMember &m : e->hmem) m.vx = (vx_max >= 2 && m.Lx % 2 == 0) ? 2 : 1;
   e->tile_start.assign(e->n, 0);
   e->ntiles = batch_assign_tiles(e->hmem.data(), e->n, passes, e->tile_start.data());
@@ -89,10 +90,11 @@ static int ens_plan(lbfd_ens *e, int vx_max, int passes) {
   ENS_CU(cudaMemcpy(e->dtile_start, e->tile_start.data(), sizeof(int64_t) * e->n, cudaMemcpyHostToDevice));
   e->vx_max = vx_max;
   e->passes = passes;
-  const int bps = batch_blocks_per_sm(e->lattice, e->precision, e->noise_mode, e->noise_dist);
+  e->occ = occ;
+  e->bps = batch_blocks_per_sm(e->lattice, e->precision, occ, e->noise_mode, e->noise_dist);
   int sms = 0;
   ENS_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
-  e->grid = int(std::max<int64_t>(1, std::min<int64_t>(e->ntiles, int64_t(sms) * bps)));
+  e->grid = int(std::max<int64_t>(1, std::min<int64_t>(e->ntiles, int64_t(sms) * e->bps)));
   if (e->graph) {
     cudaGraphExecDestroy(e->graph);
     e->graph = nullptr;
@@ -234,7 +236,7 @@ int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, in
     ens_free(e);
     return rc;
   }
-  int rc = ens_plan(e, 2, 1);
+  int rc = ens_plan(e, 2, 1, 0);
   if (rc) {
     ens_free(e);
     return rc;
@@ -283,59 +285,65 @@ int lbfd_ensemble_sync(lbfd_ens_t e) {
   return LBFD_OK;
 }
 
-int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen) {
+int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen,
+                       int32_t *blocks_per_sm) {
   if (!e || steps < 1) return ens_fail(LBFD_EINVAL, "lbfd_ensemble_tune: bad argument");
   DevGuard g(e->device);
   ENS_CU(ens_sync_t(e));
-  // candidates: sites per item (1, or 2 where Lx is even) x tile passes
+  // candidates: sites per item (1, or 2 where Lx is even) x tile passes x
+  // occupancy variant of the kernel
   const int vx_cand[2] = {1, 2};
   const int pass_cand[4] = {1, 2, 4, 8};
   float best_ms = -1.0f;
-  int best_vx = e->vx_max, best_passes = e->passes;
+  int best_vx = e->vx_max, best_passes = e->passes, best_occ = e->occ;
   cudaEvent_t a = nullptr, b = nullptr;
   ENS_CU(cudaEventCreate(&a));
   ENS_CU(cudaEventCreate(&b));
   // timing launches read the state and write the spare block only (t is not advanced)
-  ENS_CU(launch_batch_prep(e->dmem, e->n, e->t_dev, 0, e->noise_mode, e->noise_dist, e->dsteps, e->stream));
-  int64_t launched = 1;
-  for (int vx : vx_cand) {
-    for (int passes : pass_cand) {
-      int rc = ens_plan(e, vx, passes);
-      if (rc) return rc;
-      ENS_CU(launch_batch_prep(e->dmem, e->n, e->t_dev, 0, e->noise_mode, e->noise_dist, e->dsteps, e->stream));
-      ENS_CU(ens_launch(e));
-      ENS_CU(cudaEventRecord(a, e->stream));
-      for (int k = 0; k < steps; ++k) ENS_CU(ens_launch(e));
-      ENS_CU(cudaEventRecord(b, e->stream));
-      ENS_CU(cudaEventSynchronize(b));
-      launched += 2 + steps;
-      float ms = 0.0f;
-      ENS_CU(cudaEventElapsedTime(&ms, a, b));
-      if (best_ms < 0.0f || ms < best_ms) {
-        best_ms = ms;
-        best_vx = vx;
-        best_passes = passes;
+  int64_t launched = 0;
+  for (int occ = 0; occ < 2; ++occ) {
+    for (int vx : vx_cand) {
+      for (int passes : pass_cand) {
+        int rc = ens_plan(e, vx, passes, occ);
+        if (rc) return rc;
+        ENS_CU(launch_batch_prep(e->dmem, e->n, e->t_dev, 0, e->noise_mode, e->noise_dist, e->dsteps, e->stream));
+        ENS_CU(ens_launch(e));
+        ENS_CU(cudaEventRecord(a, e->stream));
+        for (int k = 0; k < steps; ++k) ENS_CU(ens_launch(e));
+        ENS_CU(cudaEventRecord(b, e->stream));
+        ENS_CU(cudaEventSynchronize(b));
+        launched += 2 + steps;
+        float ms = 0.0f;
+        ENS_CU(cudaEventElapsedTime(&ms, a, b));
+        if (best_ms < 0.0f || ms < best_ms) {
+          best_ms = ms;
+          best_vx = vx;
+          best_passes = passes;
+          best_occ = occ;
+        }
       }
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   count_launches(launched);
-  int rc = ens_plan(e, best_vx, best_passes);
+  int rc = ens_plan(e, best_vx, best_passes, best_occ);
   if (rc) return rc;
   if (vx_chosen) *vx_chosen = best_vx;
   if (passes_chosen) *passes_chosen = best_passes;
+  if (blocks_per_sm) *blocks_per_sm = e->bps;
   return LBFD_OK;
 }
 
 int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx,
-                        int32_t *passes) {
+                        int32_t *passes, int32_t *blocks_per_sm) {
   if (!e) return ens_fail(LBFD_EINVAL, "lbfd_ensemble_query: null handle");
   if (n_members) *n_members = e->n;
   if (total_sites) *total_sites = e->total_sites;
   if (t) *t = e->t;
   if (vx) *vx = e->vx_max;
   if (passes) *passes = e->passes;
+  if (blocks_per_sm) *blocks_per_sm = e->bps;
   return LBFD_OK;
 }
 

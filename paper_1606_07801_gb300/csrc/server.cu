@@ -14,6 +14,7 @@
 //   [table upload, when the resident set changed]  one copy from pinned staging
 //   k_batch_prep                                   step arguments of every member
 //   k_batch_step per lattice type                  one launch covers all members of that type
+//                                                  (forked onto one stream per type when several are resident)
 // then, for each member that has taken its steps, a result kernel (streaming
 // shift or density) into its spare block, and on the copy stream the
 // device-to-host copy of that result.  The host sees the copy's event
@@ -155,6 +156,8 @@ struct lbfd_server {
   int device = 0, elem = 4, sms = 1;
   int bps[3] = {1, 1, 1};
   cudaStream_t cs = nullptr, xs = nullptr;  // compute, copy
+  cudaStream_t ls[3] = {nullptr, nullptr, nullptr};  // per lattice type, so the launches of a tick overlap
+  cudaEvent_t prep_ev = nullptr, lat_ev[3] = {nullptr, nullptr, nullptr};
   char *arena = nullptr;
   RangePool *pool = nullptr;
   // result sink of run_trace (caller's pinned buffer)
@@ -209,6 +212,11 @@ void server_free(lbfd_server *s) {
     if (s->stage[k]) cudaFreeHost(s->stage[k]);
   }
   if (s->ready_ev) cudaEventDestroy(s->ready_ev);
+  if (s->prep_ev) cudaEventDestroy(s->prep_ev);
+  for (int L = 0; L < 3; ++L) {
+    if (s->lat_ev[L]) cudaEventDestroy(s->lat_ev[L]);
+    if (s->ls[L]) cudaStreamDestroy(s->ls[L]);
+  }
   cudaFree(s->d_members);
   cudaFree(s->d_tile_start);
   cudaFree(s->d_steps);
@@ -449,13 +457,24 @@ int tick(lbfd_server *s) {
   const int n = s->seg_off[2] + s->seg_n[2];
   SRV_CU(launch_batch_prep(s->d_members, n, nullptr, s->clock, s->opt.noise_mode, s->opt.noise_dist, s->d_steps, s->cs));
   s->launches += 1;
+  // one launch per lattice type; with more than one type they run on their
+  // own streams (forked after the prep kernel, joined before anything else)
+  int types = 0;
+  for (int L = 0; L < 3; ++L) types += s->seg_n[L] > 0;
+  if (types > 1) SRV_CU(cudaEventRecord(s->prep_ev, s->cs));
   for (int L = 0; L < 3; ++L) {
     if (s->seg_n[L] == 0) continue;
+    cudaStream_t st = types > 1 ? s->ls[L] : s->cs;
+    if (types > 1) SRV_CU(cudaStreamWaitEvent(st, s->prep_ev, 0));
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L])));
     SRV_CU(launch_batch_step(L, s->opt.precision, s->arena, s->d_steps + s->seg_off[L], s->d_tile_start + s->seg_off[L],
-                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.noise_mode, s->opt.noise_dist, grid,
-                             s->cs));
+                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.noise_mode,
+                             s->opt.noise_dist, grid, st));
     s->launches += 1;
+    if (types > 1) {
+      SRV_CU(cudaEventRecord(s->lat_ev[L], st));
+      SRV_CU(cudaStreamWaitEvent(s->cs, s->lat_ev[L], 0));
+    }
   }
   SRV_CU(cudaEventRecord(s->tick_ev[slot], s->cs));
   // members whose step counter reaches their step count after this step
@@ -536,6 +555,7 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   if (o.passes != 1 && o.passes != 2 && o.passes != 4 && o.passes != 8)
     return srv_fail(LBFD_EINVAL, "server: passes must be 1, 2, 4 or 8");
   if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST) return srv_fail(LBFD_EINVAL, "server: unknown policy");
+  if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.max_active_sites < 0) return srv_fail(LBFD_EINVAL, "server: max_active_sites must be >= 0");
   int dev = o.device;
   if (dev < 0) SRV_CU(cudaGetDevice(&dev));
@@ -560,6 +580,11 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
     if (err == cudaSuccess) err = cudaEventRecord(s->stage_ev[k], s->cs);
   }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->ready_ev, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->prep_ev, cudaEventDisableTiming);
+  for (int L = 0; L < 3 && err == cudaSuccess; ++L) {
+    err = cudaStreamCreateWithFlags(&s->ls[L], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->lat_ev[L], cudaEventDisableTiming);
+  }
   s->tick_ev.assign(size_t(o.max_ahead), nullptr);
   for (int k = 0; k < o.max_ahead && err == cudaSuccess; ++k)
     err = cudaEventCreateWithFlags(&s->tick_ev[k], cudaEventDisableTiming);
@@ -568,7 +593,7 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
     server_free(s);
     return rc;
   }
-  for (int L = 0; L < 3; ++L) s->bps[L] = batch_blocks_per_sm(L, o.precision, o.noise_mode, o.noise_dist);
+  for (int L = 0; L < 3; ++L) s->bps[L] = batch_blocks_per_sm(L, o.precision, o.occupancy, o.noise_mode, o.noise_dist);
   s->largest_free = s->pool->largest_free();
   *out = s;
   return LBFD_OK;
@@ -579,6 +604,8 @@ int lbfd_server_destroy(lbfd_server_t s) {
   DevScope scope(s->device);
   cudaError_t e1 = cudaStreamSynchronize(s->cs);
   cudaError_t e2 = cudaStreamSynchronize(s->xs);
+  for (int L = 0; L < 3; ++L)
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s->ls[L]);
   server_free(s);
   if (e1 != cudaSuccess) return srv_cuda("lbfd_server_destroy", e1);
   if (e2 != cudaSuccess) return srv_cuda("lbfd_server_destroy", e2);

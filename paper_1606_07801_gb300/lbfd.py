@@ -67,7 +67,7 @@ class ServerOptions(ctypes.Structure):
     _fields_ = [
         ("precision", c_int32), ("noise_mode", c_int32), ("noise_dist", c_int32), ("device", c_int32),
         ("hbm_budget", c_int64), ("max_active_sites", c_int64), ("max_active", c_int32), ("max_ahead", c_int32),
-        ("passes", c_int32), ("policy", c_int32), ("reserved", c_int32 * 8),
+        ("passes", c_int32), ("policy", c_int32), ("occupancy", c_int32), ("reserved", c_int32 * 7),
     ]
 
 
@@ -128,8 +128,9 @@ SIGNATURES = {
     "lbfd_ensemble_destroy": (c_int32, [c_void_p]),
     "lbfd_ensemble_step": (c_int32, [c_void_p, c_int64]),
     "lbfd_ensemble_sync": (c_int32, [c_void_p]),
-    "lbfd_ensemble_tune": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32)]),
-    "lbfd_ensemble_query": (c_int32, [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int32), P(c_int32)]),
+    "lbfd_ensemble_tune": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32), P(c_int32)]),
+    "lbfd_ensemble_query": (c_int32, [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int32), P(c_int32),
+                                       P(c_int32)]),
     "lbfd_ensemble_get_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_set_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_mass": (c_int32, [c_void_p, c_int32, P(c_double)]),
@@ -386,17 +387,18 @@ def lbfd_ensemble_sync(e: int) -> None:
 
 
 def lbfd_ensemble_tune(e: int, steps: int = 3):
-    """Returns the chosen (sites per item at most, tile passes)."""
-    v, p = c_int32(), c_int32()
-    _check(load().lbfd_ensemble_tune(e, steps, ctypes.byref(v), ctypes.byref(p)), "lbfd_ensemble_tune")
-    return v.value, p.value
+    """Returns the chosen (sites per item at most, tile passes, blocks per SM)."""
+    v, p, b = c_int32(), c_int32(), c_int32()
+    _check(load().lbfd_ensemble_tune(e, steps, ctypes.byref(v), ctypes.byref(p), ctypes.byref(b)),
+           "lbfd_ensemble_tune")
+    return v.value, p.value, b.value
 
 
 def lbfd_ensemble_query(e: int):
-    n, sites, t, vx, passes = c_int32(), c_int64(), c_int64(), c_int32(), c_int32()
+    n, sites, t, vx, passes, bps = c_int32(), c_int64(), c_int64(), c_int32(), c_int32(), c_int32()
     _check(load().lbfd_ensemble_query(e, ctypes.byref(n), ctypes.byref(sites), ctypes.byref(t), ctypes.byref(vx),
-                                      ctypes.byref(passes)), "lbfd_ensemble_query")
-    return n.value, sites.value, t.value, vx.value, passes.value
+                                      ctypes.byref(passes), ctypes.byref(bps)), "lbfd_ensemble_query")
+    return n.value, sites.value, t.value, vx.value, passes.value, bps.value
 
 
 def lbfd_ensemble_get_f(e: int, member: int, Q: int, N: int) -> np.ndarray:

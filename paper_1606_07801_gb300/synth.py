@@ -46,17 +46,18 @@ def density_noise(N: int, rho_mean: float, sd: float, seed: int) -> np.ndarray:
 
 
 def ensemble(n: int, side_lo: int = 32, side_hi: int = 512, rho_lo: float = 0.5, rho_hi: float = 200.0,
-             tau_lo: float = 0.6, tau_hi: float = 1.5, seed: int = 12345):
-    """n D2Q9 lattices: sides drawn independently log-uniform in [side_lo, side_hi]
-    (rounded), mean density and tau uniform in their ranges, distinct seeds."""
+             tau_lo: float = 0.6, tau_hi: float = 1.5, seed: int = 12345, ndim: int = 2):
+    """n lattices of ndim dimensions: sides drawn independently log-uniform in
+    [side_lo, side_hi] (rounded), mean density and tau uniform in their
+    ranges, distinct seeds."""
     g = rng(seed)
-    lx = np.rint(np.exp(g.uniform(math.log(side_lo), math.log(side_hi), n))).astype(np.int64)
-    ly = np.rint(np.exp(g.uniform(math.log(side_lo), math.log(side_hi), n))).astype(np.int64)
+    sides = [np.rint(np.exp(g.uniform(math.log(side_lo), math.log(side_hi), n))).astype(np.int64)
+             for _ in range(ndim)]
     rho = g.uniform(rho_lo, rho_hi, n)
     tau = g.uniform(tau_lo, tau_hi, n)
     seeds = (int(seed) * 1000003 + np.arange(n)).astype(np.uint64)
-    return [dict(dims=(int(lx[i]), int(ly[i])), rho_mean=float(rho[i]), tau=float(tau[i]), seed=int(seeds[i]))
-            for i in range(n)]
+    return [dict(dims=tuple(int(sd[i]) for sd in sides), rho_mean=float(rho[i]), tau=float(tau[i]),
+                 seed=int(seeds[i])) for i in range(n)]
 
 
 def served_trace(n: int, rate: float = 500.0, seed: int = 777, d1_range=(256, 65536), d2_side=(32, 1024),

@@ -59,3 +59,16 @@ int dhc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
   return 0;
 }
 }
+
+// Multiply-shift division of the batched kernel's index split, against the
+// hardware division: every (d, n) pair given; returns the number of mismatches.
+#include "fastdiv.cuh"
+
+extern "C" int64_t dhc_fastdiv_mismatches(const uint32_t *d, int64_t nd, const uint32_t *n, int64_t nn) {
+  int64_t bad = 0;
+  for (int64_t i = 0; i < nd; ++i) {
+    const FastDiv f = make_fastdiv(d[i]);
+    for (int64_t k = 0; k < nn; ++k) bad += fastdiv(n[k], f) != n[k] / d[i];
+  }
+  return bad;
+}

@@ -32,6 +32,8 @@ def dhc(tmp_path_factory):
     lib.dhc_philox.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.dhc_philox_site.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                     ctypes.c_void_p]
+    lib.dhc_fastdiv_mismatches.restype = ctypes.c_int64
+    lib.dhc_fastdiv_mismatches.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64]
     return lib
 
 
@@ -89,3 +91,30 @@ def test_variates_match_oracle(orc, dhc, nmom, dist):
         assert np.max(np.abs(z - zo)) < 1e-14
         dhc.dhc_variates(0, nmom, dist, 0xDEADBEEF12345, 9, site, t, z.ctypes.data)
         assert np.max(np.abs(z - zo)) < 5e-6 * max(1.0, np.max(np.abs(zo)))
+
+
+def test_multiply_shift_division_is_exact(dhc):
+    """The batched kernel splits work-item indices with multiply-shift
+    division; it must equal integer division for every divisor in
+    [1, 2^31) and numerator in [0, 2^31): all small divisors, powers of two
+    and their neighbours, random large ones, against edge and random
+    numerators."""
+    g = np.random.default_rng(3)
+    d = set(range(1, 4097))
+    for e in range(1, 31):
+        d |= {2**e - 1, 2**e, 2**e + 1}
+    d |= set(int(x) for x in g.integers(1, 2**31, 3000))
+    d.add(2**31 - 1)
+    d = np.array(sorted(d), dtype=np.uint32)
+    n = set(range(0, 70000))
+    for e in range(1, 32):
+        n |= {2**e - 1, 2**e, 2**e + 1}
+    n |= set(int(x) for x in g.integers(0, 2**31, 20000))
+    n = np.array(sorted(x for x in n if x < 2**31), dtype=np.uint32)
+    # multiples of each divisor and their neighbours, where rounding would show
+    for dv in d[::37]:
+        k = np.arange(1, 2**31 // int(dv), max(1, (2**31 // int(dv)) // 50), dtype=np.int64) * int(dv)
+        extra = np.concatenate([k - 1, k, k + 1])
+        extra = extra[(extra >= 0) & (extra < 2**31)].astype(np.uint32)
+        assert dhc.dhc_fastdiv_mismatches(np.array([dv]).ctypes.data, 1, extra.ctypes.data, extra.size) == 0
+    assert dhc.dhc_fastdiv_mismatches(d.ctypes.data, d.size, n.ctypes.data, n.size) == 0

@@ -44,7 +44,7 @@ def test_members_bit_identical_to_single_lattices(lat, precision):
         e.step(16)   # starts on the odd buffer: single steps, then a chunk
         e.step(1)
         got = [e.get_f(m) for m in range(len(specs))]
-        n, sites, t, vx, passes = e.query()
+        n, sites, t, vx, passes, bps = e.query()
     assert (n, t) == (len(specs), 38)
     assert sites == sum(int(np.prod(s["dims"])) for s in specs)
     for m, sp in enumerate(specs):
@@ -69,8 +69,8 @@ def test_tuner_keeps_state_and_results():
     with lb.Ensemble(lb.D2Q9, specs) as e:
         e.step(5)
         before = [e.get_f(m) for m in range(2)]
-        vx, passes = e.tune(steps=3)
-        assert vx in (1, 2) and passes in (1, 2, 4, 8)
+        vx, passes, bps = e.tune(steps=3)
+        assert vx in (1, 2) and passes in (1, 2, 4, 8) and bps >= 1
         assert all(np.array_equal(before[m], e.get_f(m)) for m in range(2))
         e.step(20)
         got = [e.get_f(m) for m in range(2)]
