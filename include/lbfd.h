@@ -51,6 +51,10 @@ extern "C" {
 #define LBFD_D3Q19 2 /* v = 0; (+-1,0,0),(0,+-1,0),(0,0,+-1) as +x,-x,+y,-y,+z,-z;
                         (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0); (1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1);
                         (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1);  w = 1/3, 1/18 x6, 1/36 x12 */
+#define LBFD_D2Q5 3  /* the paper's lattice (Sec. II): v = (0,0),(1,0),(-1,0),(0,1),(0,-1);
+                        w = 1 - 2 theta, theta/2 x4 with free theta in (0, 1/2); basis by
+                        Gram-Schmidt of 1, v_x, v_y, v_x^2 - v_y^2, v_x^2 + v_y^2.  FP32/FP64 only;
+                        not in ensembles or the server */
 
 /* ---- arithmetic and storage ------------------------------------------ */
 #define LBFD_F32 0      /* FP32 arithmetic and storage (default) */
@@ -94,6 +98,12 @@ typedef struct lbfd_options {
     int32_t n_modes;    /* structure-factor wave vectors sampled by lbfd_sample */
     int32_t modes[LBFD_MAX_MODES][3];
     int32_t reserved[8];
+    double theta;       /* D2Q5: sum_i w_i v_ix^2, in (0, 1/2); 0 = 1/3.  Other lattices: 0 or 1/3 */
+    double tau_moments[LBFD_MAX_Q]; /* multiple relaxation times (Sec. III): tau^a of moment a of
+                           the basis, a = 1..Q-1 (entry 0, the conserved density, is ignored);
+                           0 = tau.  Each moment's noise variance is rho (2 tau^a - 1)/(tau^a)^2.
+                           Any entry other than 0 or tau selects the moment-space kernel
+                           (FP32/FP64 storage only). */
 } lbfd_options;
 
 /* Observables accumulated by lbfd_sample (FP64, deterministic reductions). */
@@ -183,6 +193,10 @@ int lbfd_state_device(lbfd_t h, void **f_dev, void **stream);
  * the moment matrix m[a][i] (Gram-Schmidt basis of Sec. II, n_i^a = m_i^a w_i).
  * Any output pointer may be NULL.  No device work. */
 int lbfd_lattice_tables(int32_t lattice, int32_t *Q, int32_t *v, double *w, double *m);
+
+/* Same for a given theta (D2Q5: weights and basis of that theta; the other
+ * lattices accept only theta = 1/3 or 0). */
+int lbfd_lattice_tables_ex(int32_t lattice, double theta, int32_t *Q, int32_t *v, double *w, double *m);
 
 /* Noise variates the step kernel draws: z^1..z^nmom (unit variance) of sites
  * site0 .. site0+nsites-1 at step t, computed on the current device in the

@@ -13,13 +13,13 @@ import ctypes
 import numpy as np
 
 from . import build as _build_mod
-from .lbfd import (D1Q3, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
+from .lbfd import (D1Q3, D2Q5, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
                    F64, GAUSSIAN, INIT_HOST, INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL,
                    NOISE_LOCAL, NOISE_OFF, OK, POLICY_FIFO, POLICY_SHORTEST, Q_OF, REQ_DONE, REQ_QUEUED, REQ_RUNNING,
                    REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, LbfdError, Options, load)
 from . import lbfd as abi
 
-__all__ = ["Simulation", "Ensemble", "Server", "STORAGE_DTYPE", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "F32", "F64",
+__all__ = ["Simulation", "Ensemble", "Server", "STORAGE_DTYPE", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "D2Q5", "F32", "F64",
            "F32_F16", "F32_BF16",
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
            "INIT_NONE", "INIT_HOST", "RESULT_F", "RESULT_RHO", "RESULT_NONE", "POLICY_FIFO", "POLICY_SHORTEST",
@@ -45,7 +45,7 @@ class Simulation:
     def __init__(self, lattice: int, dims, tau: float, rho_mean: float, seed: int = 1, *, precision: int = F32,
                  noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN, init: int = INIT_UNIFORM,
                  sine_amp: float = 0.0, sine_k=(1, 0, 0), lattice_id: int = 0, modes=(), stream=None,
-                 torch_buffers: bool = False, device: int = -1):
+                 torch_buffers: bool = False, device: int = -1, theta: float = 0.0, tau_moments=None):
         o = abi.lbfd_options_init()
         o.lattice, o.precision, o.noise_mode, o.noise_dist, o.init = lattice, precision, noise_mode, noise_dist, init
         d = [int(x) for x in dims] + [1] * (3 - len(dims))
@@ -53,6 +53,13 @@ class Simulation:
             o.dims[a] = d[a]
         o.tau, o.rho_mean, o.seed, o.lattice_id, o.device = float(tau), float(rho_mean), int(seed), int(lattice_id), device
         o.sine_amp = float(sine_amp)
+        o.theta = float(theta)
+        if tau_moments is not None:
+            tm = [float(x) for x in tau_moments]
+            if len(tm) > MAX_Q:
+                raise ValueError(f"at most {MAX_Q} relaxation times")
+            for a, x in enumerate(tm):
+                o.tau_moments[a] = x
         for a in range(3):
             o.sine_k[a] = int(sine_k[a]) if a < len(sine_k) else 0
         modes = list(modes)

@@ -49,8 +49,10 @@ struct DeviceGuard {
   }
 };
 
-int lattice_dims(int lattice) { return lattice == LBFD_D1Q3 ? 1 : (lattice == LBFD_D2Q9 ? 2 : 3); }
-int lattice_q(int lattice) { return lattice == LBFD_D1Q3 ? 3 : (lattice == LBFD_D2Q9 ? 9 : 19); }
+int lattice_dims(int lattice) { return lattice == LBFD_D1Q3 ? 1 : (lattice == LBFD_D3Q19 ? 3 : 2); }
+int lattice_q(int lattice) {
+  return lattice == LBFD_D1Q3 ? 3 : (lattice == LBFD_D2Q9 ? 9 : (lattice == LBFD_D2Q5 ? 5 : 19));
+}
 
 }  // namespace
 
@@ -75,6 +77,10 @@ struct lbfd_sim {
   double *mom = nullptr;  // rho and j for lbfd_moments, allocated on first use
   int64_t n_samples = 0;
   int32_t modes_host[LBFD_MAX_MODES][3] = {};
+  // moment-space (multiple-relaxation-time) kernel: taken for D2Q5 and when
+  // any tau^a differs from tau; tables of the lattice at its theta
+  bool mrt = false;
+  double w[LBFD_MAX_Q] = {}, m[LBFD_MAX_Q * LBFD_MAX_Q] = {}, tau_m[LBFD_MAX_Q] = {};
 };
 
 // The handle stores the post-collision populations g of the last step (the
@@ -131,7 +137,7 @@ int lbfd_options_init(lbfd_options *o) {
 }
 
 static int validate(const lbfd_options *o) {
-  if (o->lattice < LBFD_D1Q3 || o->lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
+  if (o->lattice < LBFD_D1Q3 || o->lattice > LBFD_D2Q5) return fail(LBFD_EINVAL, "unknown lattice");
   if (o->precision < LBFD_F32 || o->precision > LBFD_F32_BF16) return fail(LBFD_EINVAL, "unknown precision");
   if (o->noise_mode < LBFD_NOISE_LOCAL || o->noise_mode > LBFD_NOISE_OFF) return fail(LBFD_EINVAL, "unknown noise mode");
   if (o->noise_dist != LBFD_GAUSSIAN && o->noise_dist != LBFD_UNIFORM) return fail(LBFD_EINVAL, "unknown noise distribution");
@@ -150,6 +156,21 @@ static int validate(const lbfd_options *o) {
   if (!std::isfinite(o->sine_amp)) return fail(LBFD_EINVAL, "sine_amp must be finite");
   if (o->n_modes < 0 || o->n_modes > LBFD_MAX_MODES) return fail(LBFD_EINVAL, "n_modes out of range");
   if ((o->f_dev[0] == nullptr) != (o->f_dev[1] == nullptr)) return fail(LBFD_EINVAL, "give both f_dev buffers or neither");
+  if (o->lattice == LBFD_D2Q5) {
+    if (!(o->theta == 0.0 || (o->theta > 0.0 && o->theta < 0.5)))
+      return fail(LBFD_EINVAL, "theta of D2Q5 must be in (0, 1/2) (or 0 for 1/3)");
+  } else if (!(o->theta == 0.0 || std::fabs(o->theta - 1.0 / 3.0) < 1e-15)) {
+    return fail(LBFD_EINVAL, "theta is 1/3 for D1Q3, D2Q9 and D3Q19");
+  }
+  bool mrt = o->lattice == LBFD_D2Q5;
+  for (int a = 1; a < lattice_q(o->lattice); ++a) {
+    const double ta = o->tau_moments[a];
+    if (ta == 0.0 || ta == o->tau) continue;
+    if (!(ta > 0.5) || !std::isfinite(ta)) return fail(LBFD_EINVAL, "tau_moments entries must be 0 or finite > 1/2");
+    mrt = true;
+  }
+  if (mrt && o->precision != LBFD_F32 && o->precision != LBFD_F64)
+    return fail(LBFD_ENOTSUP, "D2Q5 and multiple relaxation times need FP32 or FP64 storage");
   if (o->f_dev[0] && o->f_dev[0] == o->f_dev[1]) return fail(LBFD_EINVAL, "the two f_dev buffers must differ");
   return LBFD_OK;
 }
@@ -187,6 +208,20 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   h->stream = static_cast<cudaStream_t>(opt->stream);
   for (int m = 0; m < opt->n_modes; ++m)
     for (int k = 0; k < 3; ++k) h->modes_host[m][k] = opt->modes[m][k];
+  // tables of the lattice at its theta, and the relaxation time of each moment
+  if (opt->lattice == LBFD_D2Q5) {
+    d2q5_tables(opt->theta == 0.0 ? 1.0 / 3.0 : opt->theta, h->w, h->m);
+  } else {
+    int q = 0, d = 0, v[LBFD_MAX_Q * 3];
+    lattice_table(opt->lattice, &q, &d, v, h->w);
+    basis_table(opt->lattice, h->m);
+  }
+  h->mrt = opt->lattice == LBFD_D2Q5;
+  for (int a = 0; a < h->Q; ++a) {
+    const double ta = opt->tau_moments[a];
+    h->tau_m[a] = (a == 0 || ta == 0.0) ? opt->tau : ta;
+    if (a > 0 && h->tau_m[a] != opt->tau) h->mrt = true;
+  }
   const size_t fbytes = size_t(h->Q) * size_t(h->N) * size_t(h->elem);
   cudaError_t e = cudaSuccess;
   if (opt->f_dev[0]) {
@@ -208,7 +243,7 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
     // f(x, 0) into the spare buffer, then stored as g = f shifted back
     const double amp = opt->init == LBFD_INIT_SINE ? opt->sine_amp : 0.0;
     e = launch_init(opt->lattice, opt->precision, h->f[1], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
-                    int32_t(opt->dims[2]), opt->rho_mean, amp, opt->sine_k, h->stream);
+                    int32_t(opt->dims[2]), opt->rho_mean, amp, opt->sine_k, h->stream, h->w);
     if (e == cudaSuccess) e = store_f_from_spare(h);
   }
   if (e != cudaSuccess) {
@@ -222,7 +257,7 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
 
 int lbfd_create(lbfd_t *out, int32_t lattice, const int64_t *dims, double tau, double rho_mean, uint64_t seed) {
   if (!out || !dims) return fail(LBFD_EINVAL, "lbfd_create: null argument");
-  if (lattice < LBFD_D1Q3 || lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
+  if (lattice < LBFD_D1Q3 || lattice > LBFD_D2Q5) return fail(LBFD_EINVAL, "unknown lattice");
   lbfd_options o;
   lbfd_options_init(&o);
   o.lattice = lattice;
@@ -259,7 +294,9 @@ int lbfd_step(lbfd_t h, int64_t n) {
   a.noise_dist = o.noise_dist;
   for (int64_t k = 0; k < n; ++k) {
     a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
-    cudaError_t e = launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream);
+    cudaError_t e = h->mrt ? launch_step_mrt(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->m, h->w,
+                                             h->tau_m, h->stream)
+                           : launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream);
     if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
     h->cur ^= 1;
     h->t += 1;
@@ -432,19 +469,31 @@ int lbfd_state_device(lbfd_t h, void **f_dev, void **stream) {
   return LBFD_OK;
 }
 
-int lbfd_lattice_tables(int32_t lattice, int32_t *Q, int32_t *v, double *w, double *m) {
-  if (lattice < LBFD_D1Q3 || lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "unknown lattice");
+int lbfd_lattice_tables_ex(int32_t lattice, double theta, int32_t *Q, int32_t *v, double *w, double *m) {
+  if (lattice < LBFD_D1Q3 || lattice > LBFD_D2Q5) return fail(LBFD_EINVAL, "unknown lattice");
+  if (theta == 0.0) theta = 1.0 / 3.0;
+  if (lattice == LBFD_D2Q5 ? !(theta > 0.0 && theta < 0.5) : std::fabs(theta - 1.0 / 3.0) > 1e-15)
+    return fail(LBFD_EINVAL, "theta out of range for the lattice");
   int q = 0, d = 0;
   int vv[LBFD_MAX_Q * 3];
-  double ww[LBFD_MAX_Q];
+  double ww[LBFD_MAX_Q], mm[LBFD_MAX_Q * LBFD_MAX_Q];
   lattice_table(lattice, &q, &d, vv, ww);
+  if (lattice == LBFD_D2Q5)
+    d2q5_tables(theta, ww, mm);
+  else
+    basis_table(lattice, mm);
   if (Q) *Q = q;
   if (v)
     for (int k = 0; k < 3 * q; ++k) v[k] = vv[k];
   if (w)
     for (int k = 0; k < q; ++k) w[k] = ww[k];
-  if (m) basis_table(lattice, m);
+  if (m)
+    for (int k = 0; k < q * q; ++k) m[k] = mm[k];
   return LBFD_OK;
+}
+
+int lbfd_lattice_tables(int32_t lattice, int32_t *Q, int32_t *v, double *w, double *m) {
+  return lbfd_lattice_tables_ex(lattice, 1.0 / 3.0, Q, v, w, m);
 }
 
 int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lattice_id, uint64_t t, int64_t site0,

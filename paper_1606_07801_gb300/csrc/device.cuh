@@ -18,7 +18,7 @@
 
 namespace lbfd {
 
-enum LatticeId : int { kD1Q3 = 0, kD2Q9 = 1, kD3Q19 = 2 };
+enum LatticeId : int { kD1Q3 = 0, kD2Q9 = 1, kD3Q19 = 2, kD2Q5 = 3 };
 enum NoiseMode : int { kNoiseLocal = 0, kNoiseGlobal = 1, kNoiseOff = 2 };
 enum NoiseDist : int { kGaussian = 0, kUniform = 1 };
 
@@ -144,6 +144,21 @@ struct Lattice<kD3Q19> {
                               {0, 2, 1}, {0, 1, 2}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}};
     return t[a][k];
   }
+};
+
+// The paper's own lattice (Sec. II), in its velocity order.  Its weights
+// w_0 = 1 - 2 theta, w_1..4 = theta / 2 depend on theta, a parameter of the
+// simulation, so its step and init kernels take the weights and the moment
+// basis at run time.  w() below is the theta = 1/3 case; it only offsets the
+// 16-bit storage formats, which D2Q5 does not offer.
+template <>
+struct Lattice<kD2Q5> {
+  static constexpr int D = 2, Q = 5;
+  __host__ __device__ static constexpr int v(int i, int a) {
+    constexpr int t[5][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+    return a < 2 ? t[i][a] : 0;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
 };
 
 // ---------------------------------------------------------------------------

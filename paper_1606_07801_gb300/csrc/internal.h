@@ -9,6 +9,7 @@
 #include "device.cuh"
 
 #define LBFD_MAX_MODES_DEV 16
+#define LBFD_MAX_Q_DEV 19
 
 namespace lbfd {
 
@@ -61,6 +62,7 @@ inline cudaError_t dispatch_lattice(int lattice, F &&f) {
     case kD1Q3: return f(std::integral_constant<int, kD1Q3>{});
     case kD2Q9: return f(std::integral_constant<int, kD2Q9>{});
     case kD3Q19: return f(std::integral_constant<int, kD3Q19>{});
+    case kD2Q5: return f(std::integral_constant<int, kD2Q5>{});
   }
   return cudaErrorInvalidValue;
 }
@@ -94,9 +96,19 @@ cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, 
 cudaError_t launch_shift(int lattice, int value_bytes, const void *src, void *dst, int32_t Lx, int32_t Ly, int32_t Lz,
                          int dir, cudaStream_t stream);
 
-// f_i = w_i rho(x), rho = rho_mean (+ amp sin(2 pi k.x / L)).
+// f_i = w_i rho(x), rho = rho_mean (+ amp sin(2 pi k.x / L)); w (Q values)
+// overrides the lattice's compiled weights (D2Q5 with theta != 1/3).
 cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
-                        double amp, const int32_t *k, cudaStream_t stream);
+                        double amp, const int32_t *k, cudaStream_t stream, const double *w = nullptr);
+
+// Multiple-relaxation-time step (mrt_kernels.cuh), FP32 or FP64 storage:
+// m (Q*Q, [a][i]) and w (Q) the basis and weights (run-time for D2Q5), tau
+// the relaxation time of each moment (entry 0 unused).
+cudaError_t launch_step_mrt(int lattice, int precision, const void *src, void *dst, const StepArgs &a, const double *m,
+                            const double *w, const double *tau, cudaStream_t stream);
+
+// D2Q5 weights and moment basis (m[a*5 + i]) for second moment theta.
+void d2q5_tables(double theta, double *w, double *m);
 
 // rho(x) = sum_i f_i, j_a(x) = sum_i f_i v_ia (FP64 outputs; j may be null).
 // rho_mean decodes the 16-bit deviation formats.

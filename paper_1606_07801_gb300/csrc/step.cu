@@ -87,9 +87,14 @@ cudaError_t launch_shift(int lattice, int value_bytes, const void *src, void *ds
 // ---------------------------------------------------------------------------
 // Initial state f_i = w_i rho(x) (local equilibrium, eq. f0def)
 // ---------------------------------------------------------------------------
+// Weights passed by value (run-time for D2Q5, whose weights depend on theta).
+struct WeightArg {
+  double w[LBFD_MAX_Q_DEV];
+};
+
 template <int LAT, typename S>
 __global__ void k_init(S *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, int32_t kx,
-                       int32_t ky, int32_t kz) {
+                       int32_t ky, int32_t kz, const WeightArg wt) {
   using L = Lattice<LAT>;
   const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
   for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < N;
@@ -106,20 +111,22 @@ __global__ void k_init(S *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, do
     }
     static_for<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      f[i * N + s] = Store<S>::putd(L::w(i) * rho, L::w(i) * rho_mean);
+      f[i * N + s] = Store<S>::putd(wt.w[i] * rho, wt.w[i] * rho_mean);
     });
   }
 }
 
 cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
-                        double amp, const int32_t *k, cudaStream_t stream) {
+                        double amp, const int32_t *k, cudaStream_t stream, const double *w) {
   return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
     constexpr int LAT = decltype(lat)::value;
     using S = typename decltype(tag)::type;
+    WeightArg wt{};
+    for (int i = 0; i < Lattice<LAT>::Q; ++i) wt.w[i] = w ? w[i] : Lattice<LAT>::w(i);
     const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
     const int64_t blocks = (N + 255) / 256;
     const int grid = static_cast<int>(blocks < 152 * 64 ? blocks : 152 * 64);
-    k_init<LAT, S><<<grid, 256, 0, stream>>>(static_cast<S *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2]);
+    k_init<LAT, S><<<grid, 256, 0, stream>>>(static_cast<S *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2], wt);
     return cudaGetLastError();
   });
 }
@@ -253,6 +260,18 @@ int lattice_table(int lattice, int *Q, int *D, int *v, double *w) {
     case kD1Q3: tables_t<kD1Q3>(Q, D, v, w, nullptr); return 0;
     case kD2Q9: tables_t<kD2Q9>(Q, D, v, w, nullptr); return 0;
     case kD3Q19: tables_t<kD3Q19>(Q, D, v, w, nullptr); return 0;
+    case kD2Q5: {
+      // theta = 1/3; lattice_table_theta gives other theta
+      using L = Lattice<kD2Q5>;
+      if (Q) *Q = 5;
+      if (D) *D = 2;
+      for (int i = 0; i < 5; ++i) {
+        if (v)
+          for (int a = 0; a < 3; ++a) v[3 * i + a] = L::v(i, a);
+        if (w) w[i] = L::w(i);
+      }
+      return 0;
+    }
   }
   return -1;
 }
@@ -274,6 +293,11 @@ int basis_table(int lattice, double *m) {
       return 0;
     }
     case kD3Q19: tables_t<kD3Q19>(nullptr, nullptr, nullptr, nullptr, m); return 0;
+    case kD2Q5: {
+      double w[5];
+      d2q5_tables(1.0 / 3.0, w, m);
+      return 0;
+    }
   }
   return -1;
 }

@@ -57,6 +57,15 @@ __device__ __forceinline__ void collide_site(R (&f)[Lattice<LAT>::Q], uint32_t s
   f[0] = rho - moved;
 }
 
+// The single-relaxation-time collision as a function object, the default
+// collision of the site-update bodies below.
+template <int LAT, typename R, int NOISE>
+struct SrtCollide {
+  __device__ __forceinline__ void operator()(R (&f)[Lattice<LAT>::Q], uint32_t s, const StepArgs &a) const {
+    collide_site<LAT, R, NOISE>(f, s, a);
+  }
+};
+
 // w_i rho_mean in the compute type: the offset that the 16-bit formats store
 // the deviation from (zero for FP32/FP64 storage).
 template <int LAT, typename S>
@@ -72,9 +81,9 @@ __device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepAr
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
 // Update of site (x, y, z) of one lattice (any shape).  S is the storage
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
-template <int LAT, typename S, int NOISE>
+template <int LAT, typename S, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>>
 __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a,
-                                                 int x, int y, int z) {
+                                                 int x, int y, int z, const C &collide = C()) {
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   constexpr int Q = L::Q;
@@ -96,7 +105,7 @@ __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *_
     const uint32_t so = static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
     f[i] = Store<S>::get(src[static_cast<size_t>(i) * static_cast<size_t>(a.N) + so], store_offset<LAT, S>(i, a));
   });
-  collide_site<LAT, R, NOISE>(f, s, a);
+  collide(f, s, a);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = Store<S>::put(f[i], store_offset<LAT, S>(i, a));
@@ -136,9 +145,9 @@ constexpr int step_min_blocks() {
 }
 
 // Update of sites (x0 .. x0 + VX - 1, y, z) of one lattice (Lx % VX == 0).
-template <int LAT, typename S, int VX, int NOISE>
+template <int LAT, typename S, int VX, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>>
 __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a, int x0,
-                                              int y, int z) {
+                                              int y, int z, const C &collide = C()) {
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   using P = Pack<S, VX>;
@@ -177,7 +186,7 @@ __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__re
     }
   });
 #pragma unroll
-  for (int k = 0; k < VX; ++k) collide_site<LAT, R, NOISE>(f[k], row + static_cast<uint32_t>(x0 + k), a);
+  for (int k = 0; k < VX; ++k) collide(f[k], row + static_cast<uint32_t>(x0 + k), a);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const R wr = store_offset<LAT, S>(i, a);

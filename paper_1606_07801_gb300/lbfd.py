@@ -19,7 +19,7 @@ c_int32, c_int64, c_uint32, c_uint64, c_double, c_void_p = (ctypes.c_int32, ctyp
 P = ctypes.POINTER
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-D1Q3, D2Q9, D3Q19 = 0, 1, 2
+D1Q3, D2Q9, D3Q19, D2Q5 = 0, 1, 2, 3
 F32, F64, F32_F16, F32_BF16 = 0, 1, 2, 3
 NOISE_LOCAL, NOISE_GLOBAL, NOISE_OFF = 0, 1, 2
 GAUSSIAN, UNIFORM = 0, 1
@@ -29,8 +29,8 @@ POLICY_FIFO, POLICY_SHORTEST = 0, 1
 REQ_UNKNOWN, REQ_QUEUED, REQ_RUNNING, REQ_DONE = -1, 0, 1, 2
 MAX_Q, MAX_MODES = 19, 16
 
-Q_OF = {D1Q3: 3, D2Q9: 9, D3Q19: 19}
-D_OF = {D1Q3: 1, D2Q9: 2, D3Q19: 3}
+Q_OF = {D1Q3: 3, D2Q9: 9, D3Q19: 19, D2Q5: 5}
+D_OF = {D1Q3: 1, D2Q9: 2, D3Q19: 3, D2Q5: 2}
 
 
 class Options(ctypes.Structure):
@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
         ("init", c_int32), ("device", c_int32), ("dims", c_int64 * 3), ("tau", c_double),
         ("rho_mean", c_double), ("sine_amp", c_double), ("sine_k", c_int32 * 3), ("lattice_id", c_uint32),
         ("seed", c_uint64), ("stream", c_void_p), ("f_dev", c_void_p * 2), ("n_modes", c_int32),
-        ("modes", (c_int32 * 3) * MAX_MODES), ("reserved", c_int32 * 8),
+        ("modes", (c_int32 * 3) * MAX_MODES), ("reserved", c_int32 * 8), ("theta", c_double),
+        ("tau_moments", c_double * MAX_Q),
     ]
 
 
@@ -120,6 +121,7 @@ SIGNATURES = {
     "lbfd_query": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int64), P(c_int32)]),
     "lbfd_state_device": (c_int32, [c_void_p, P(c_void_p), P(c_void_p)]),
     "lbfd_lattice_tables": (c_int32, [c_int32, P(c_int32), c_void_p, c_void_p, c_void_p]),
+    "lbfd_lattice_tables_ex": (c_int32, [c_int32, c_double, P(c_int32), c_void_p, c_void_p, c_void_p]),
     "lbfd_noise_draw": (c_int32, [c_int32, c_int32, c_uint64, c_uint32, c_uint64, c_int64, c_int64, c_int32,
                                   c_void_p]),
     "lbfd_box_muller_probe": (c_int32, [c_int32, c_void_p, c_int64, c_void_p]),
@@ -311,13 +313,14 @@ def lbfd_state_device(h: int):
     return f.value, s.value
 
 
-def lbfd_lattice_tables(lattice: int):
-    """(v[Q,3], w[Q], m[Q,Q]) as compiled into the kernels."""
+def lbfd_lattice_tables(lattice: int, theta: float = 0.0):
+    """(v[Q,3], w[Q], m[Q,Q]) the kernels use (theta: D2Q5's second moment, 0 = 1/3)."""
     Q = c_int32()
     v = np.zeros(3 * MAX_Q, dtype=np.int32)
     w = np.zeros(MAX_Q)
     m = np.zeros(MAX_Q * MAX_Q)
-    _check(load().lbfd_lattice_tables(lattice, ctypes.byref(Q), _ptr(v), _ptr(w), _ptr(m)), "lbfd_lattice_tables")
+    _check(load().lbfd_lattice_tables_ex(lattice, theta, ctypes.byref(Q), _ptr(v), _ptr(w), _ptr(m)),
+           "lbfd_lattice_tables_ex")
     q = Q.value
     return v[:3 * q].reshape(q, 3).astype(np.int64), w[:q].copy(), m[:q * q].reshape(q, q).copy()
 

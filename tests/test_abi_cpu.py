@@ -108,3 +108,36 @@ def test_kernel_tables_match_oracle(orc, lat):
 def test_step_rejects_negative_n_without_gpu():
     lib = abi.load()
     assert lib.lbfd_step(ctypes.c_void_p(1), -1) == abi.EINVAL
+
+
+@pytest.mark.parametrize("theta", [0.1, 0.2, 1.0 / 3.0, 0.45])
+def test_d2q5_tables_match_oracle(orc, theta):
+    """D2Q5 at free theta: the run-time weights and Gram-Schmidt basis the
+    moment-space kernel receives equal the oracle's."""
+    v, w, m = abi.lbfd_lattice_tables(lb.D2Q5, theta)
+    D, Q, ov, ow = orc.lattice(orc.D2Q5, theta)
+    assert np.array_equal(v, ov)
+    assert np.max(np.abs(w - ow)) < 1e-16
+    assert np.max(np.abs(m - orc.basis(orc.D2Q5, theta))) < 1e-14
+
+
+@pytest.mark.parametrize("kw,code,msg", [
+    (dict(lattice=3, theta=0.5), abi.EINVAL, "theta"),
+    (dict(lattice=3, theta=-0.1), abi.EINVAL, "theta"),
+    (dict(lattice=1, theta=0.25), abi.EINVAL, "theta"),
+    (dict(lattice=3, precision=2), abi.ENOTSUP, "FP32 or FP64"),
+    (dict(lattice=1, precision=3, tau_moments=[0, 0.9]), abi.ENOTSUP, "FP32 or FP64"),
+    (dict(lattice=1, tau_moments=[0, 0.4]), abi.EINVAL, "tau_moments"),
+])
+def test_create_rejects_bad_paper_variants(kw, code, msg):
+    o = abi.lbfd_options_init()
+    o.dims[0], o.dims[1] = 8, 8
+    for k, v in kw.items():
+        if k == "tau_moments":
+            for a, x in enumerate(v):
+                o.tau_moments[a] = x
+        else:
+            setattr(o, k, v)
+    with pytest.raises(abi.LbfdError) as e:
+        abi.lbfd_create_ex(o)
+    assert e.value.code == code and msg in str(e.value)
