@@ -85,6 +85,30 @@ def profiled(workload: str, key: str):
 ISSUE_PEAK = 152 * 4 * 32 * 2.070e9
 
 
+def replica(rank: int) -> dict:
+    """Each rank runs its own lattice: seed 1 + rank and Philox lattice id
+    rank, so the replicas draw independent noise (no data-path collective)."""
+    return {"seed": 1 + rank, "lattice_id": rank}
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The slowest rank's figure (the timed region ends when every rank has
+    finished)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_glups(world: int, sites: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: the site updates of all ranks over the slowest
+    rank's time (weak scaling: every rank has the same lattice)."""
+    return world * sites * steps / seconds / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -453,7 +477,8 @@ def main():
     elem = ELEM_BYTES[prec]
     stream = torch.cuda.Stream()
     init = lb.INIT_SINE if args.workload == "d1q3" else lb.INIT_UNIFORM
-    sim = lb.Simulation(lat, dims, tau, rho, 1 + rank, precision=prec, lattice_id=rank, stream=stream,
+    rep = replica(rank)
+    sim = lb.Simulation(lat, dims, tau, rho, rep["seed"], precision=prec, lattice_id=rep["lattice_id"], stream=stream,
                         torch_buffers=True, device=local, init=init, sine_amp=1.0, sine_k=(1, 0, 0))
 
     def barrier():
@@ -473,14 +498,10 @@ def main():
         ev1.record(stream)
         barrier()
     launches = lb.abi.lbfd_kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     clocks = clk.summary()
     ms_per_step = ms / args.steps
-    value = world * N * args.steps / (ms * 1e-3) / 1e9
+    value = job_glups(world, N, args.steps, ms * 1e-3)
 
     # roofline of the dominant kernel (k_step is the only kernel in the timed region)
     bytes_per_launch = 2 * Q * elem * N
@@ -508,12 +529,8 @@ def main():
         sim.step(1)
         lb.abi.load().lbfd_moments(sim.h, h_rho.data_ptr(), None)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * N * e_steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": Q * N * elem,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": job_glups(world, N, e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": Q * N * elem,
            "d2h_bytes_per_step": N * 8}
     sim.close()
 

@@ -339,14 +339,21 @@ template <>
 struct BoxMuller<float> {
   __host__ __device__ static __forceinline__ void pair(uint32_t r0, uint32_t r1, float &z0, float &z1) {
 #ifdef __CUDA_ARCH__
-    const float v = unit24<float>(~r0);
-    const float series = 2.0f * v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 0.33333334f), 0.5f), 1.0f);
-    const float x = v < 0.015625f ? series : -2.0f * __logf(unit24<float>(r0));  // x >= 2^-24 > 0
+    // each uniform ((r >> 8) + 1/2) 2^-24 is one rounding of k 2^-24 + 2^-25
+    // (exact for v < 1/2)
+    const float v = fmaf(static_cast<float>(~r0 >> 8), 5.9604644775390625e-08f, 2.98023223876953125e-08f);
+    const float u0 = fmaf(static_cast<float>(r0 >> 8), 5.9604644775390625e-08f, 2.98023223876953125e-08f);
+    // -2 ln(1 - v) = v (2 + v (1 + v (2/3 + v/2))) + O(v^5), used below 1/64;
+    // above, -2 ln u0 = -2 ln(2) log2(u0)
+    const float series = v * fmaf(v, fmaf(v, fmaf(v, 0.5f, 0.6666667f), 1.0f), 2.0f);
+    const float x = v < 0.015625f ? series : -1.38629436111989061f * __log2f(u0);  // x >= 2^-24 > 0
     const float rad = x * rsqrtf(x);
-    const float half_turns = (static_cast<float>(static_cast<int32_t>(r1 >> 8) - 8388608) + 0.5f) *
-                             5.9604644775390625e-08f;  // u1 - 1/2, exact
+    // angle 2 pi u1 - pi in [-pi, pi) from the exact u1 - 1/2 = (k - 2^23 + 1/2) 2^-24
+    const float angle = fmaf(static_cast<float>(static_cast<int32_t>(r1 >> 8) - 8388608),
+                             3.7450703871400037e-07f /* 2 pi 2^-24 */,
+                             1.8725351935700019e-07f /* pi 2^-24 */);
     float s, c;
-    __sincosf(6.28318530717958648f * half_turns, &s, &c);
+    __sincosf(angle, &s, &c);
     z0 = -rad * c;
     z1 = -rad * s;
 #else
