@@ -103,7 +103,7 @@ typedef struct lbfd_options {
                            the basis, a = 1..Q-1 (entry 0, the conserved density, is ignored);
                            0 = tau.  Each moment's noise variance is rho (2 tau^a - 1)/(tau^a)^2.
                            Any entry other than 0 or tau selects the moment-space kernel
-                           (FP32/FP64 storage only). */
+                           (FP32/FP64 storage, Q * sites < 2^32). */
 } lbfd_options;
 
 /* Observables accumulated by lbfd_sample (FP64, deterministic reductions). */
@@ -244,10 +244,10 @@ int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void *f_dev, int
  * per time step covers every member, and chunks of steps are captured into a
  * CUDA graph and replayed.  Every member evolves exactly as the same lattice
  * would under lbfd_create_ex with the same parameters (same arithmetic,
- * same noise keys).  Members share one precision, noise mode and law.
- * Work decomposition: a work item is 1 or 2 sites of a row (2 only where Lx
- * is even), a tile is `passes` x 256 items of one member, and a persistent
- * grid walks the tiles. */
+ * same noise keys).  Members share one precision, noise mode and law, and
+ * each member has Q * sites < 2^32.  Work decomposition: a work item is 1
+ * or 2 sites of a row (2 only where Lx is even), a tile is `passes` x 256
+ * items of one member, and a persistent grid walks the tiles. */
 typedef struct lbfd_member {
     int64_t dims[3];    /* Lx, Ly, Lz; trailing dims of lower-D lattices must be 1 */
     double tau;         /* > 1/2 */
@@ -303,8 +303,10 @@ int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
  * population blocks fit in its device-memory budget (one arena allocated at
  * creation; admission and retirement allocate nothing).  Every time step
  * is one launch per lattice type covering all resident simulations of that
- * type (the batched kernel of the ensemble), so requests that arrive while
- * others run join the next step and their work overlaps on the device.  A
+ * type (the batched kernel of the ensemble), plus one single-lattice launch
+ * for each simulation of at least solo_sites sites, all on side streams, so
+ * requests that arrive while others run join the next step and their work
+ * overlaps on the device.  A
  * simulation that has taken its steps is read back on a second stream while
  * the others go on, and its memory returns to the arena once the copy is
  * done.  Each simulation keeps its own step counter t (from 0) and its own
@@ -338,6 +340,9 @@ typedef struct lbfd_server_options {
     int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
     int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
     int32_t reserved[7];
+    int64_t solo_sites;     /* simulations of at least this many sites are stepped by their own
+                               single-lattice launch (parameters as kernel arguments) instead of the
+                               batched launch; 0 = all batched.  Results are the same either way. */
 } lbfd_server_options;
 
 typedef struct lbfd_request {
@@ -372,7 +377,7 @@ typedef struct lbfd_server_stats {
 typedef struct lbfd_server *lbfd_server_t;
 
 /* Defaults: FP32, local Gaussian noise, current device, 1 GiB budget, no
- * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO. */
+ * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO, solo_sites 2^17. */
 int lbfd_server_options_init(lbfd_server_options *opt);
 
 /* Creates a server: one device arena of hbm_budget bytes, two streams
@@ -386,7 +391,8 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt);
 int lbfd_server_destroy(lbfd_server_t s);
 
 /* Queues a request and returns its id (0, 1, 2, ... in submission order).
- * Touches no GPU state.  LBFD_EINVAL for a malformed request and for one
+ * Touches no GPU state.  LBFD_EINVAL for a malformed request (including
+ * Q * sites >= 2^32) and for one
  * that could never be admitted (its blocks exceed the whole budget or the
  * site limit, or no result buffer is given for a result kind that needs
  * one).  in_host and out_host must stay valid until the request is done. */

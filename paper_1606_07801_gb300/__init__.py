@@ -209,11 +209,13 @@ class Server:
 
     def __init__(self, *, precision: int = F32, noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN,
                  hbm_budget: int = 1 << 30, max_active: int = 1024, max_ahead: int = 4, passes: int = 1,
-                 policy: int = POLICY_FIFO, max_active_sites: int = 0, occupancy: int = 0, device: int = -1):
+                 policy: int = POLICY_FIFO, max_active_sites: int = 0, occupancy: int = 0,
+                 solo_sites: int = 1 << 17, device: int = -1):
         o = abi.lbfd_server_options_init()
         o.precision, o.noise_mode, o.noise_dist, o.device = precision, noise_mode, noise_dist, device
         o.hbm_budget, o.max_active, o.max_ahead, o.passes = int(hbm_budget), max_active, max_ahead, passes
         o.policy, o.max_active_sites, o.occupancy = policy, int(max_active_sites), occupancy
+        o.solo_sites = int(solo_sites)
         self.precision = precision
         self._bufs = {}
         self.h = abi.lbfd_server_create(o)

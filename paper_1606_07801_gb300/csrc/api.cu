@@ -171,6 +171,8 @@ static int validate(const lbfd_options *o) {
   }
   if (mrt && o->precision != LBFD_F32 && o->precision != LBFD_F64)
     return fail(LBFD_ENOTSUP, "D2Q5 and multiple relaxation times need FP32 or FP64 storage");
+  if (mrt && double(lattice_q(o->lattice)) * n > 4294967295.0)
+    return fail(LBFD_ENOTSUP, "D2Q5 and multiple relaxation times need Q * sites < 2^32");
   if (o->f_dev[0] && o->f_dev[0] == o->f_dev[1]) return fail(LBFD_EINVAL, "the two f_dev buffers must differ");
   return LBFD_OK;
 }

@@ -109,10 +109,12 @@ __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>()
         const int col = item - row * b.cols;
         const int z = static_cast<int>(fastdiv(static_cast<uint32_t>(row), b.div_Ly));
         const int y = row - z * b.a.Ly;
+        // a member's value offsets fit 32 bits (checked when it is listed)
+        using C = SrtCollide<LAT, typename Store<S>::R, NOISE>;
         if (b.vx == 2)
-          step_vec_body<LAT, S, 2, NOISE>(src, dst, b.a, col * 2, y, z);
+          step_vec_body<LAT, S, 2, NOISE, C, uint32_t>(src, dst, b.a, col * 2, y, z);
         else
-          step_scalar_body<LAT, S, NOISE>(src, dst, b.a, col, y, z);
+          step_scalar_body<LAT, S, NOISE, C, uint32_t>(src, dst, b.a, col, y, z);
       }
     }
   }

@@ -295,8 +295,17 @@ struct Math<float> {
   }
 };
 
+// Square root on the special-function unit: the PTX instruction
+// sqrt.approx.ftz.f32 (relative error about 2^-23; subnormal inputs count
+// as 0).  Used where the argument is a noise variance or -2 ln u >= 2^-24.
+__device__ __forceinline__ float sqrt_sfu(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Noise amplitude sqrt(x), x = rho_n (2 tau - 1)/tau^2 >= 0.  FP32 on the
-// device: x * rsqrt(x) on the special-function unit (about 2 ulp).
+// device: sqrt_sfu.
 template <typename R>
 __host__ __device__ __forceinline__ R noise_amplitude(R x) {
   return Math<R>::sqrt(x);
@@ -304,7 +313,7 @@ __host__ __device__ __forceinline__ R noise_amplitude(R x) {
 template <>
 __host__ __device__ __forceinline__ float noise_amplitude<float>(float x) {
 #ifdef __CUDA_ARCH__
-  return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+  return sqrt_sfu(x);
 #else
   return sqrtf(x);
 #endif
@@ -347,7 +356,7 @@ struct BoxMuller<float> {
     // above, -2 ln u0 = -2 ln(2) log2(u0)
     const float series = v * fmaf(v, fmaf(v, fmaf(v, 0.5f, 0.6666667f), 1.0f), 2.0f);
     const float x = v < 0.015625f ? series : -1.38629436111989061f * __log2f(u0);  // x >= 2^-24 > 0
-    const float rad = x * rsqrtf(x);
+    const float rad = sqrt_sfu(x);
     // angle 2 pi u1 - pi in [-pi, pi) from the exact u1 - 1/2 = (k - 2^23 + 1/2) 2^-24
     const float angle = fmaf(static_cast<float>(static_cast<int32_t>(r1 >> 8) - 8388608),
                              3.7450703871400037e-07f /* 2 pi 2^-24 */,

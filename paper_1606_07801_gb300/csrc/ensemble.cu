@@ -187,6 +187,10 @@ int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, in
       delete e;
       return ens_fail(LBFD_EINVAL, "member " + std::to_string(m) + ": 2^31 sites or more");
     }
+    if (double(e->Q) * sites > 4294967295.0) {
+      delete e;
+      return ens_fail(LBFD_EINVAL, "member " + std::to_string(m) + ": Q * sites must be < 2^32");
+    }
     if (mb.dims[1] > 65535 || mb.dims[2] > 65535) {
       delete e;
       return ens_fail(LBFD_EINVAL, "member " + std::to_string(m) + ": Ly and Lz must be <= 65535");

@@ -110,11 +110,12 @@ __global__ void __launch_bounds__(256)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x0 >= a.Lx || y >= a.Ly) return;
+  // value offsets fit 32 bits (checked by the API)
   const MrtCollide<LAT, R, NOISE, CT> c{p};
   if constexpr (VX == 1)
-    step_scalar_body<LAT, S, NOISE>(src, dst, a, x0, y, z, c);
+    step_scalar_body<LAT, S, NOISE, MrtCollide<LAT, R, NOISE, CT>, uint32_t>(src, dst, a, x0, y, z, c);
   else
-    step_vec_body<LAT, S, VX, NOISE>(src, dst, a, x0, y, z, c);
+    step_vec_body<LAT, S, VX, NOISE, MrtCollide<LAT, R, NOISE, CT>, uint32_t>(src, dst, a, x0, y, z, c);
 }
 
 // Launch for one lattice and storage type (FP32 or FP64).  m (Q*Q, [a][i])

@@ -14,7 +14,9 @@
 //   [table upload, when the resident set changed]  one copy from pinned staging
 //   k_batch_prep                                   step arguments of every member
 //   k_batch_step per lattice type                  one launch covers all members of that type
-//                                                  (forked onto one stream per type when several are resident)
+//   k_step per simulation of >= solo_sites sites   the single-lattice kernel, parameters as
+//                                                  kernel arguments
+// (forked onto side streams when there is more than one launch, joined after)
 // then, for each member that has taken its steps, a result kernel (streaming
 // shift or density) into its spare block, and on the copy stream the
 // device-to-host copy of that result.  The host sees the copy's event
@@ -158,6 +160,13 @@ struct lbfd_server {
   cudaStream_t cs = nullptr, xs = nullptr;  // compute, copy
   cudaStream_t ls[3] = {nullptr, nullptr, nullptr};  // per lattice type, so the launches of a tick overlap
   cudaEvent_t prep_ev = nullptr, lat_ev[3] = {nullptr, nullptr, nullptr};
+  // simulations of at least solo_sites sites take the single-lattice kernel,
+  // one launch each per step, spread over these streams
+  static constexpr int kSoloStreams = 4;
+  cudaStream_t ss[kSoloStreams] = {};
+  cudaEvent_t solo_ev[kSoloStreams] = {};
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<int64_t> solo;
   char *arena = nullptr;
   RangePool *pool = nullptr;
   // result sink of run_trace (caller's pinned buffer)
@@ -213,6 +222,11 @@ void server_free(lbfd_server *s) {
   }
   if (s->ready_ev) cudaEventDestroy(s->ready_ev);
   if (s->prep_ev) cudaEventDestroy(s->prep_ev);
+  if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+  for (int k = 0; k < lbfd_server::kSoloStreams; ++k) {
+    if (s->solo_ev[k]) cudaEventDestroy(s->solo_ev[k]);
+    if (s->ss[k]) cudaStreamDestroy(s->ss[k]);
+  }
   for (int L = 0; L < 3; ++L) {
     if (s->lat_ev[L]) cudaEventDestroy(s->lat_ev[L]);
     if (s->ls[L]) cudaStreamDestroy(s->ls[L]);
@@ -242,6 +256,7 @@ int prepare_request(lbfd_server *s, const lbfd_request &r, SrvRequest &q, bool i
   if (r.dims[1] > 65535 || r.dims[2] > 65535) return srv_fail(LBFD_EINVAL, "request: Ly and Lz must be <= 65535");
   const double sites = double(r.dims[0]) * double(r.dims[1]) * double(r.dims[2]);
   if (sites >= 2147483648.0) return srv_fail(LBFD_EINVAL, "request: 2^31 sites or more");
+  if (double(q_of(r.lattice)) * sites > 4294967295.0) return srv_fail(LBFD_EINVAL, "request: Q * sites must be < 2^32");
   if (!(r.tau > 0.5) || !std::isfinite(r.tau)) return srv_fail(LBFD_EINVAL, "request: tau must be > 1/2");
   if (!(r.rho_mean >= 0.0) || !std::isfinite(r.rho_mean)) return srv_fail(LBFD_EINVAL, "request: rho_mean must be >= 0");
   if (r.steps < 0) return srv_fail(LBFD_EINVAL, "request: steps must be >= 0");
@@ -428,10 +443,15 @@ int upload_tables(lbfd_server *s) {
   BatchMember *hm = reinterpret_cast<BatchMember *>(s->stage[slot]);
   int64_t *hts = reinterpret_cast<int64_t *>(s->stage[slot] + sizeof(BatchMember) * size_t(s->opt.max_active));
   int n = 0;
+  s->solo.clear();
   for (int L = 0; L < 3; ++L) {
     s->seg_off[L] = n;
     for (int64_t id : s->active[L]) {
       const SrvRequest &q = s->reqs[id];
+      if (s->opt.solo_sites > 0 && q.N >= s->opt.solo_sites) {
+        s->solo.push_back(id);
+        continue;
+      }
       hm[n++] = make_batch_member(q.r.dims, q.r.tau, q.r.rho_mean, q.r.seed, q.r.lattice_id, q.region / s->elem,
                                   (q.region + q.block) / s->elem, q.t0, 2);
     }
@@ -455,25 +475,57 @@ int tick(lbfd_server *s) {
   if (s->clock >= uint64_t(ring)) SRV_CU(cudaEventSynchronize(s->tick_ev[slot]));
   if (s->dirty) SRV_RC(upload_tables(s));
   const int n = s->seg_off[2] + s->seg_n[2];
-  SRV_CU(launch_batch_prep(s->d_members, n, nullptr, s->clock, s->opt.noise_mode, s->opt.noise_dist, s->d_steps, s->cs));
-  s->launches += 1;
-  // one launch per lattice type; with more than one type they run on their
-  // own streams (forked after the prep kernel, joined before anything else)
   int types = 0;
   for (int L = 0; L < 3; ++L) types += s->seg_n[L] > 0;
-  if (types > 1) SRV_CU(cudaEventRecord(s->prep_ev, s->cs));
+  const bool fork = types + int64_t(s->solo.size()) > 1;
+  if (n > 0) {
+    SRV_CU(launch_batch_prep(s->d_members, n, nullptr, s->clock, s->opt.noise_mode, s->opt.noise_dist, s->d_steps,
+                             s->cs));
+    s->launches += 1;
+  }
+  // one batched launch per lattice type, and one single-lattice launch per
+  // large simulation; with more than one launch they run on their own
+  // streams, forked here and joined before anything else uses the state
+  if (fork) SRV_CU(cudaEventRecord(s->fork_ev, s->cs));
   for (int L = 0; L < 3; ++L) {
     if (s->seg_n[L] == 0) continue;
-    cudaStream_t st = types > 1 ? s->ls[L] : s->cs;
-    if (types > 1) SRV_CU(cudaStreamWaitEvent(st, s->prep_ev, 0));
+    cudaStream_t st = fork ? s->ls[L] : s->cs;
+    if (fork) SRV_CU(cudaStreamWaitEvent(st, s->fork_ev, 0));
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L])));
     SRV_CU(launch_batch_step(L, s->opt.precision, s->arena, s->d_steps + s->seg_off[L], s->d_tile_start + s->seg_off[L],
                              s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.noise_mode,
                              s->opt.noise_dist, grid, st));
     s->launches += 1;
-    if (types > 1) {
+    if (fork) {
       SRV_CU(cudaEventRecord(s->lat_ev[L], st));
       SRV_CU(cudaStreamWaitEvent(s->cs, s->lat_ev[L], 0));
+    }
+  }
+  if (!s->solo.empty()) {
+    const int nst = std::min<int>(lbfd_server::kSoloStreams, int(s->solo.size()));
+    for (int k = 0; k < nst; ++k)
+      if (fork) SRV_CU(cudaStreamWaitEvent(s->ss[k], s->fork_ev, 0));
+    for (size_t k = 0; k < s->solo.size(); ++k) {
+      const SrvRequest &q = s->reqs[s->solo[k]];
+      const uint64_t t = s->clock - q.t0;  // the simulation's own step counter
+      StepArgs a{};
+      a.Lx = int32_t(q.r.dims[0]);
+      a.Ly = int32_t(q.r.dims[1]);
+      a.Lz = int32_t(q.r.dims[2]);
+      a.N = q.N;
+      fill_step_params(a, q.r.tau, q.r.rho_mean);
+      a.noise_mode = s->opt.noise_mode;
+      a.noise_dist = s->opt.noise_dist;
+      a.ph = make_philox_step(q.r.seed, q.r.lattice_id, t);
+      char *A = s->arena + q.region;
+      char *src = (t & 1) ? A + q.block : A;
+      char *dst = (t & 1) ? A : A + q.block;
+      SRV_CU(launch_step(q.r.lattice, s->opt.precision, src, dst, a, fork ? s->ss[k % nst] : s->cs));
+      s->launches += 1;
+    }
+    for (int k = 0; k < nst && fork; ++k) {
+      SRV_CU(cudaEventRecord(s->solo_ev[k], s->ss[k]));
+      SRV_CU(cudaStreamWaitEvent(s->cs, s->solo_ev[k], 0));
     }
   }
   SRV_CU(cudaEventRecord(s->tick_ev[slot], s->cs));
@@ -537,6 +589,7 @@ int lbfd_server_options_init(lbfd_server_options *opt) {
   opt->max_ahead = 4;
   opt->passes = 1;
   opt->policy = LBFD_POLICY_FIFO;
+  opt->solo_sites = int64_t(1) << 17;
   return LBFD_OK;
 }
 
@@ -557,6 +610,7 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST) return srv_fail(LBFD_EINVAL, "server: unknown policy");
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.max_active_sites < 0) return srv_fail(LBFD_EINVAL, "server: max_active_sites must be >= 0");
+  if (o.solo_sites < 0) return srv_fail(LBFD_EINVAL, "server: solo_sites must be >= 0");
   int dev = o.device;
   if (dev < 0) SRV_CU(cudaGetDevice(&dev));
   DevScope scope(dev);
@@ -581,6 +635,11 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->ready_ev, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->prep_ev, cudaEventDisableTiming);
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming);
+  for (int k = 0; k < lbfd_server::kSoloStreams && err == cudaSuccess; ++k) {
+    err = cudaStreamCreateWithFlags(&s->ss[k], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->solo_ev[k], cudaEventDisableTiming);
+  }
   for (int L = 0; L < 3 && err == cudaSuccess; ++L) {
     err = cudaStreamCreateWithFlags(&s->ls[L], cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&s->lat_ev[L], cudaEventDisableTiming);
@@ -606,6 +665,8 @@ int lbfd_server_destroy(lbfd_server_t s) {
   cudaError_t e2 = cudaStreamSynchronize(s->xs);
   for (int L = 0; L < 3; ++L)
     if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s->ls[L]);
+  for (int k = 0; k < lbfd_server::kSoloStreams; ++k)
+    if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(s->ss[k]);
   server_free(s);
   if (e1 != cudaSuccess) return srv_cuda("lbfd_server_destroy", e1);
   if (e2 != cudaSuccess) return srv_cuda("lbfd_server_destroy", e2);

@@ -81,7 +81,9 @@ __device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepAr
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
 // Update of site (x, y, z) of one lattice (any shape).  S is the storage
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
-template <int LAT, typename S, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>>
+// Idx is the type of the value offsets i N + site: uint32_t when Q N < 2^32
+// (fewer address instructions), size_t otherwise.
+template <int LAT, typename S, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>, typename Idx = size_t>
 __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a,
                                                  int x, int y, int z, const C &collide = C()) {
   using L = Lattice<LAT>;
@@ -103,23 +105,23 @@ __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *_
     const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
     const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
     const uint32_t so = static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
-    f[i] = Store<S>::get(src[static_cast<size_t>(i) * static_cast<size_t>(a.N) + so], store_offset<LAT, S>(i, a));
+    f[i] = Store<S>::get(src[static_cast<Idx>(i) * static_cast<Idx>(a.N) + so], store_offset<LAT, S>(i, a));
   });
   collide(f, s, a);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    dst[static_cast<size_t>(i) * static_cast<size_t>(a.N) + s] = Store<S>::put(f[i], store_offset<LAT, S>(i, a));
+    dst[static_cast<Idx>(i) * static_cast<Idx>(a.N) + s] = Store<S>::put(f[i], store_offset<LAT, S>(i, a));
   });
 }
 
 // Scalar kernel: one site per thread, any lattice shape.
-template <int LAT, typename S, int NOISE>
+template <int LAT, typename S, int NOISE, typename Idx>
 __global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= a.Lx || y >= a.Ly) return;
-  step_scalar_body<LAT, S, NOISE>(src, dst, a, x, y, z);
+  step_scalar_body<LAT, S, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, Idx>(src, dst, a, x, y, z);
 }
 
 // Vector kernel: VX consecutive sites of a row per thread (needs Lx % VX == 0).
@@ -145,7 +147,8 @@ constexpr int step_min_blocks() {
 }
 
 // Update of sites (x0 .. x0 + VX - 1, y, z) of one lattice (Lx % VX == 0).
-template <int LAT, typename S, int VX, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>>
+template <int LAT, typename S, int VX, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>,
+          typename Idx = size_t>
 __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a, int x0,
                                               int y, int z, const C &collide = C()) {
   using L = Lattice<LAT>;
@@ -166,7 +169,7 @@ __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__re
     const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
     const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
     const uint32_t srow = Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
-    const S *pop = src + static_cast<size_t>(i) * static_cast<size_t>(a.N) + srow;
+    const S *pop = src + (static_cast<Idx>(i) * static_cast<Idx>(a.N) + static_cast<Idx>(srow));
     const R wr = store_offset<LAT, S>(i, a);
     const P pk = *reinterpret_cast<const P *>(pop + x0);
     R v[VX];
@@ -193,19 +196,23 @@ __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__re
     P pk;
 #pragma unroll
     for (int k = 0; k < VX; ++k) pk.v[k] = Store<S>::put(f[k][i], wr);
-    *reinterpret_cast<P *>(dst + static_cast<size_t>(i) * static_cast<size_t>(a.N) + row + x0) = pk;
+    *reinterpret_cast<P *>(dst + (static_cast<Idx>(i) * static_cast<Idx>(a.N) + static_cast<Idx>(row) + static_cast<Idx>(x0))) =
+        pk;
   });
 }
 
-template <int LAT, typename S, int VX, int NOISE>
+template <int LAT, typename S, int VX, int NOISE, typename Idx>
 __global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
     k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x0 >= a.Lx || y >= a.Ly) return;
-  step_vec_body<LAT, S, VX, NOISE>(src, dst, a, x0, y, z);
+  step_vec_body<LAT, S, VX, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, Idx>(src, dst, a, x0, y, z);
 }
+
+// True when every value offset i N + site of a lattice fits 32 bits.
+inline bool offsets_fit_32(int Q, int64_t N) { return static_cast<uint64_t>(Q) * static_cast<uint64_t>(N) <= 0xffffffffull; }
 
 inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block, int vx = 1) {
   const int cols = Lx / vx;
@@ -218,40 +225,37 @@ inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &blo
 }
 
 // Sites per thread of the step kernel (a tuning knob; results do not depend
-// on it).  LBFD_STEP_VX = 1, 2 or 4 overrides the default of 2 when Lx
-// allows (else 1).
+// on it).  LBFD_STEP_VX = 1 or 2 overrides the default of 2 when Lx allows
+// (else 1).
 inline int step_vx_override() {
   static int v = [] {
     const char *e = getenv("LBFD_STEP_VX");
     const int r = e ? atoi(e) : 0;
-    return (r == 1 || r == 2 || r == 4) ? r : 0;
+    return (r == 1 || r == 2) ? r : 0;
   }();
   return v;
 }
 
-template <int LAT, typename S, int NOISE>
-cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
-  using R = typename Store<S>::R;
-  int vx = step_vx_override();
-  if (vx == 0) vx = 2;
-  if (sizeof(R) == 8 && vx == 4) vx = 2;
-  while (vx > 1 && a.Lx % vx != 0) vx /= 2;
+template <int LAT, typename S, int NOISE, typename Idx>
+cudaError_t step_noise_idx(const S *s, S *d, const StepArgs &a, int vx, cudaStream_t stream) {
   dim3 grid, block;
   step_shape(a.Lx, a.Ly, a.Lz, grid, block, vx);
+  if (vx == 2)
+    k_step_vec<LAT, S, 2, NOISE, Idx><<<grid, block, 0, stream>>>(s, d, a);
+  else
+    k_step<LAT, S, NOISE, Idx><<<grid, block, 0, stream>>>(s, d, a);
+  return cudaGetLastError();
+}
+
+template <int LAT, typename S, int NOISE>
+cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
+  int vx = step_vx_override();
+  if (vx == 0) vx = 2;
+  if (a.Lx % vx != 0) vx = 1;
   const S *s = static_cast<const S *>(src);
   S *d = static_cast<S *>(dst);
-  if constexpr (sizeof(R) == 4) {
-    if (vx == 4) {
-      k_step_vec<LAT, S, 4, NOISE><<<grid, block, 0, stream>>>(s, d, a);
-      return cudaGetLastError();
-    }
-  }
-  if (vx == 2) {
-    k_step_vec<LAT, S, 2, NOISE><<<grid, block, 0, stream>>>(s, d, a);
-    return cudaGetLastError();
-  }
-  k_step<LAT, S, NOISE><<<grid, block, 0, stream>>>(s, d, a);
-  return cudaGetLastError();
+  if (offsets_fit_32(Lattice<LAT>::Q, a.N)) return step_noise_idx<LAT, S, NOISE, uint32_t>(s, d, a, vx, stream);
+  return step_noise_idx<LAT, S, NOISE, size_t>(s, d, a, vx, stream);
 }
 
 // Kernel selection by noise configuration: each variant is branch-free in

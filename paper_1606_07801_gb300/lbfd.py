@@ -69,6 +69,7 @@ class ServerOptions(ctypes.Structure):
         ("precision", c_int32), ("noise_mode", c_int32), ("noise_dist", c_int32), ("device", c_int32),
         ("hbm_budget", c_int64), ("max_active_sites", c_int64), ("max_active", c_int32), ("max_ahead", c_int32),
         ("passes", c_int32), ("policy", c_int32), ("occupancy", c_int32), ("reserved", c_int32 * 7),
+        ("solo_sites", c_int64),
     ]
 
 

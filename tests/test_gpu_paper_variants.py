@@ -144,3 +144,31 @@ def test_front_fluctuations(mode):
     for band in (hi, lo):
         r = var[band].mean() / want[band].mean()
         assert abs(r - 1.0) < 0.05, (mode, r)
+
+
+def test_time_correlators_on_the_gpu():
+    """The paper's time-correlator experiment (Sec. IV, eq. TimeCorrEqn): 81x81
+    D2Q5, rho^eq = 120, theta = 1/3, tau = 1 (D = 1/6), local noise.  The
+    normalised <rho_k(s + t) rho_k(s)*> of several modes must follow
+    lambda(k)^t, lambda(k) = sum_i w_i cos(k.v_i), the exact lattice form of the
+    paper's exp(-gamma(k) t)."""
+    from tests.test_oracle_time_correlation import correlations
+
+    L, rho, T = 81, 120.0, 24000
+    v, w, _ = abi.lbfd_lattice_tables(lb.D2Q5, 1.0 / 3.0)
+    modes = [(1, 0), (0, 3), (5, 0), (10, 0), (5, 5)]
+    series = np.empty((T, len(modes)), dtype=complex)
+    with lb.Simulation(lb.D2Q5, (L, L), 1.0, rho, 77) as s:
+        s.step(2000)
+        for t in range(T):
+            s.step(1)
+            rk = np.fft.fft2(s.moments().reshape(L, L))
+            for m, (kx, ky) in enumerate(modes):
+                series[t, m] = rk[ky, kx]
+    lags = [1, 2, 5, 10, 20]
+    for m, (kx, ky) in enumerate(modes):
+        k = np.array([2 * np.pi * kx / L, 2 * np.pi * ky / L])
+        lam = float(np.sum(w * np.cos(v[:, :2] @ k)))
+        got, err = correlations(series[:, m], lags)
+        want = lam ** np.array(lags, dtype=float)
+        assert np.all(np.abs(got - want) < 5 * err + 0.01), ((kx, ky), got, want, err)

@@ -75,10 +75,13 @@ def _mixed_specs(precision):
     return specs
 
 
-@pytest.mark.parametrize("precision", [lb.F32, lb.F64, lb.F32_F16])
-def test_served_results_bit_identical_to_alone(precision):
+@pytest.mark.parametrize("precision,solo", [(lb.F32, 0), (lb.F32, 400), (lb.F64, 400), (lb.F32_F16, 0),
+                                            (lb.F32_F16, 1000)])
+def test_served_results_bit_identical_to_alone(precision, solo):
+    """solo: simulations of at least this many sites take their own
+    single-lattice launch each step (0: all batched)."""
     specs = _mixed_specs(precision)
-    with lb.Server(precision=precision, hbm_budget=256 << 20, max_ahead=3) as srv:
+    with lb.Server(precision=precision, hbm_budget=256 << 20, max_ahead=3, solo_sites=solo) as srv:
         ids = [_submit(srv, sp) for sp in specs[:5]]
         srv.pump(6)                      # the first wave runs ...
         ids += [_submit(srv, sp) for sp in specs[5:9]]   # ... while the second arrives
