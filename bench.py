@@ -355,7 +355,8 @@ def run_served(args):
     sink = torch.empty(args.sink_mb << 20, dtype=torch.uint8).pin_memory()
     policy = lb.POLICY_SHORTEST if args.policy == "shortest" else lb.POLICY_FIFO
     srv = lb.Server(hbm_budget=int(args.budget_gb * (1 << 30)), max_active=4096, max_ahead=4, passes=args.passes,
-                    policy=policy, max_active_sites=args.max_active_sites, occupancy=args.occupancy)
+                    policy=policy, max_active_sites=args.max_active_sites, occupancy=args.occupancy,
+                    solo_sites=args.solo_sites)
     # warm-up: a short trace of small requests (module load, first launches)
     warm = [abi.make_request(k % 3, [(512,), (64, 64), (16, 16, 16)][k % 3], 1.0, 10.0, 99 + k, 20,
                              result=lb.RESULT_RHO) for k in range(max(3, args.warmup))]
@@ -404,6 +405,7 @@ def run_served(args):
                                "32-1024) / D3Q19 (side log-uniform 32-128), steps log-uniform 100-10^4, tau "
                                "U[0.6, 1.5], rho_mean U[0.5, 200], FP32, local Gaussian noise, density result",
                    "hbm_budget_gb": args.budget_gb, "policy": args.policy, "passes": args.passes, "occupancy": args.occupancy,
+                   "solo_sites": args.solo_sites,
                    "max_active_sites": args.max_active_sites, "site_updates": lups,
                    "step": "one bench step = one served request; value = total site updates / makespan"},
         "latency_s": {"p50": p50, "p99": p99, "mean": float(np.mean(lat)), "max": float(np.max(lat))},
@@ -440,6 +442,7 @@ def main():
     ap.add_argument("--policy", default="fifo", choices=["fifo", "shortest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
+    ap.add_argument("--solo-sites", type=int, default=1 << 17)
     ap.add_argument("--max-active-sites", type=int, default=0)
     ap.add_argument("--sink-mb", type=int, default=2048)
     ap.add_argument("--plain-requests", type=int, default=-1)

@@ -2,6 +2,7 @@
 // memory, the step loop and the reductions.  No torch types cross it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -25,6 +26,9 @@ int fail(int code, const std::string &msg) {
 }
 
 int cuda_fail(const char *what, cudaError_t e) {
+  // the runtime keeps a failed call's error as the thread's last error;
+  // clear it so that the next launch check does not report it again
+  (void)cudaGetLastError();
   return fail(e == cudaErrorMemoryAllocation ? LBFD_ENOMEM : LBFD_ECUDA,
               std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }
@@ -294,6 +298,25 @@ int lbfd_step(lbfd_t h, int64_t n) {
   fill_step_params(a, o.tau, o.rho_mean);
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
+  if (!h->mrt && n >= 2 && small_fits(h->Q, h->N, h->elem)) {
+    // a small lattice: many steps per launch in shared memory (bit-identical)
+    constexpr int64_t kChunk = 4096;
+    int64_t launches = 0;
+    for (int64_t done = 0; done < n;) {
+      const int chunk = int(std::min<int64_t>(kChunk, n - done));
+      const int to = h->cur ^ (chunk & 1);
+      a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
+      cudaError_t e = launch_step_small(o.lattice, o.precision, h->f[h->cur], h->f[to], a, o.seed, o.lattice_id,
+                                        uint64_t(h->t), chunk, h->stream);
+      if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
+      h->cur = to;
+      h->t += chunk;
+      done += chunk;
+      launches += 1;
+    }
+    g_launches.fetch_add(launches, std::memory_order_relaxed);
+    return LBFD_OK;
+  }
   for (int64_t k = 0; k < n; ++k) {
     a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
     cudaError_t e = h->mrt ? launch_step_mrt(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->m, h->w,

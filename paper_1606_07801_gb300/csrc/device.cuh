@@ -391,13 +391,8 @@ struct PhiloxStep {
   uint32_t k0[10], k1[10];  // round keys K0[r] = k0 + r W0, K1[r] = k1 + r W1
 };
 
-__host__ __device__ inline PhiloxStep make_philox_step(uint64_t seed, uint32_t lattice_id, uint64_t t) {
-  PhiloxStep P{};
-  const uint32_t key0 = static_cast<uint32_t>(seed), key1 = static_cast<uint32_t>(seed >> 32);
-  for (int r = 0; r < 10; ++r) {
-    P.k0[r] = key0 + static_cast<uint32_t>(r) * Philox::W0;
-    P.k1[r] = key1 + static_cast<uint32_t>(r) * Philox::W1;
-  }
+// The words of P that depend on t (and the lattice id); the round keys stay.
+__host__ __device__ inline void philox_step_set_t(PhiloxStep &P, uint32_t lattice_id, uint64_t t) {
   const uint32_t t_lo = static_cast<uint32_t>(t), t_hi8 = static_cast<uint32_t>(t >> 32) << 3;
   for (int j = 0; j < 8; ++j) P.e[j] = (t_hi8 | static_cast<uint32_t>(j)) ^ P.k1[0];
   const uint64_t u = static_cast<uint64_t>(t_lo) * Philox::M1;
@@ -407,6 +402,16 @@ __host__ __device__ inline PhiloxStep make_philox_step(uint64_t seed, uint32_t l
   P.f = b1 ^ P.k0[1];
   P.g = static_cast<uint32_t>(v >> 32) ^ P.k1[1];
   P.q = static_cast<uint32_t>(v) ^ P.k1[2];
+}
+
+__host__ __device__ inline PhiloxStep make_philox_step(uint64_t seed, uint32_t lattice_id, uint64_t t) {
+  PhiloxStep P{};
+  const uint32_t key0 = static_cast<uint32_t>(seed), key1 = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    P.k0[r] = key0 + static_cast<uint32_t>(r) * Philox::W0;
+    P.k1[r] = key1 + static_cast<uint32_t>(r) * Philox::W1;
+  }
+  philox_step_set_t(P, lattice_id, t);
   return P;
 }
 

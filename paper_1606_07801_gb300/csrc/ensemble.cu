@@ -24,6 +24,9 @@ constexpr int kGraphSteps = 16;  // steps per captured graph
 int ens_fail(int code, const std::string &msg) { return set_last_error(code, msg); }
 
 int ens_cuda(const char *what, cudaError_t e) {
+  // the runtime keeps a failed call's error as the thread's last error;
+  // clear it so that the next launch check does not report it again
+  (void)cudaGetLastError();
   return ens_fail(e == cudaErrorMemoryAllocation ? LBFD_ENOMEM : LBFD_ECUDA,
                   std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }

@@ -101,6 +101,9 @@ double now_s() {
 int srv_fail(int code, const std::string &msg) { return set_last_error(code, msg); }
 
 int srv_cuda(const char *what, cudaError_t e) {
+  // the runtime keeps a failed call's error as the thread's last error;
+  // clear it so that the next launch check does not report it again
+  (void)cudaGetLastError();
   return srv_fail(e == cudaErrorMemoryAllocation ? LBFD_ENOMEM : LBFD_ECUDA,
                   std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
 }

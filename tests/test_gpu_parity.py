@@ -243,3 +243,49 @@ def test_box_muller_grid_edges(precision, tol):
     want = np.stack([rad * np.cos(2 * np.pi * u1), rad * np.sin(2 * np.pi * u1)], 1)
     assert np.all(np.isfinite(z))
     assert np.max(np.abs(z - want)) <= tol * 6.0
+
+
+@pytest.mark.parametrize("lat,dims,precision", [
+    (lb.D1Q3, (256,), lb.F64), (lb.D1Q3, (1001,), lb.F32), (lb.D2Q9, (40, 30), lb.F32), (lb.D2Q9, (13, 7), lb.F64),
+    (lb.D3Q19, (9, 8, 7), lb.F32), (lb.D3Q19, (6, 5, 4), lb.F32_F16), (lb.D2Q9, (1, 1), lb.F32),
+])
+@pytest.mark.parametrize("mode,dist", [(lb.NOISE_LOCAL, lb.GAUSSIAN), (lb.NOISE_GLOBAL, lb.UNIFORM)])
+def test_small_lattice_many_steps_per_launch(lat, dims, precision, mode, dist):
+    """A lattice whose two buffers fit one block's shared memory takes one
+    launch for up to 4096 steps; the result equals one launch per step bit for
+    bit, across launch boundaries and odd and even step counts."""
+    Q, N = lb.Q_OF[lat], int(np.prod(dims))
+    f0 = synth.random_populations(Q, N, 30.0, 0.3, seed=N)
+    kw = dict(precision=precision, noise_mode=mode, noise_dist=dist, init=lb.INIT_NONE, lattice_id=5)
+    with lb.Simulation(lat, dims, 0.9, 30.0, 11, **kw) as a:
+        a.set_f(f0)
+        n0 = abi.lbfd_kernel_launches()
+        a.step(37)
+        a.step(4100)   # two launches: 4096 + 4
+        assert abi.lbfd_kernel_launches() - n0 == 3
+        fa = a.get_f()
+    with lb.Simulation(lat, dims, 0.9, 30.0, 11, **kw) as b:
+        b.set_f(f0)
+        for _ in range(4137):
+            b.step(1)
+        fb = b.get_f()
+    assert np.array_equal(fa, fb)
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    """Failure detection on the host: a lattice whose two buffers exceed the
+    GPU's memory (2 x 19 x 4 B x 2.0e9 sites = 306 GB) and a server whose
+    arena does fail with LBFD_ENOMEM, free what they took, and leave the
+    library usable."""
+    o = abi.lbfd_options_init()
+    o.lattice = lb.D3Q19
+    o.dims[0], o.dims[1], o.dims[2] = 1200, 1200, 1400
+    with pytest.raises(abi.LbfdError) as e:
+        abi.lbfd_create_ex(o)
+    assert e.value.code == abi.ENOMEM
+    with pytest.raises(abi.LbfdError) as e:
+        lb.Server(hbm_budget=1 << 40)
+    assert e.value.code == abi.ENOMEM
+    with lb.Simulation(lb.D2Q9, (16, 8), 0.8, 10.0, 1) as s:
+        s.step(3)
+        assert abs(s.mass() - 10.0 * 128) < 1e-3
