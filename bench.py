@@ -439,11 +439,11 @@ def main():
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--rate", type=float, default=500.0)
     ap.add_argument("--budget-gb", type=float, default=120.0)
-    ap.add_argument("--policy", default="fifo", choices=["fifo", "shortest"])
+    ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
     ap.add_argument("--solo-sites", type=int, default=1 << 17)
-    ap.add_argument("--max-active-sites", type=int, default=0)
+    ap.add_argument("--max-active-sites", type=int, default=20_000_000)
     ap.add_argument("--sink-mb", type=int, default=2048)
     ap.add_argument("--plain-requests", type=int, default=-1)
     args = ap.parse_args()
