@@ -285,6 +285,7 @@ int lbfd_destroy(lbfd_t h) {
 }
 
 int lbfd_step(lbfd_t h, int64_t n) {
+  NvtxRange nvtx_("lbfd_step");
   if (!h) return fail(LBFD_EINVAL, "lbfd_step: null handle");
   if (n < 0) return fail(LBFD_EINVAL, "lbfd_step: n must be >= 0");
   if (n == 0) return LBFD_OK;

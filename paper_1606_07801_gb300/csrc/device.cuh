@@ -325,12 +325,12 @@ __host__ __device__ __forceinline__ float noise_amplitude<float>(float x) {
 // FP32 on the device: the special-function unit.  An odd multiple of 2^-25
 // above 1/2 has no FP32 representation, so the quantities that need it are
 // formed exactly from the integer word instead:
-//   v  = 1 - u0 = ((~r0 >> 8) + 1/2) 2^-24  (exact below 1/2); when
-//        v < 1/64, -2 ln u0 comes from its Taylor series in v (there the
-//        SFU log has only absolute accuracy, which the square root would
-//        amplify); otherwise from the SFU log of u0
-//   u1 - 1/2 = ((r1 >> 8) - 2^23 + 1/2) 2^-24 (exact), so the SFU sine and
-//        cosine see the angle 2 pi u1 - pi in [-pi, pi)
+//   v  = 1 - u0 (exact below 1/2); when v < 1/64, -2 ln u0 comes from its
+//        Taylor series in v (there the SFU log has only absolute accuracy,
+//        which the square root would amplify); otherwise from the SFU log
+//        of u0
+//   the angle 2 pi u1 is taken to [-pi, pi) by whole turns before the SFU
+//        sine and cosine
 // Absolute error of the FP32 variates against FP64: about 1e-6.
 template <typename R>
 struct BoxMuller {
@@ -348,23 +348,26 @@ template <>
 struct BoxMuller<float> {
   __host__ __device__ static __forceinline__ void pair(uint32_t r0, uint32_t r1, float &z0, float &z1) {
 #ifdef __CUDA_ARCH__
-    // each uniform ((r >> 8) + 1/2) 2^-24 is one rounding of k 2^-24 + 2^-25
-    // (exact for v < 1/2)
-    const float v = fmaf(static_cast<float>(~r0 >> 8), 5.9604644775390625e-08f, 2.98023223876953125e-08f);
-    const float u0 = fmaf(static_cast<float>(r0 >> 8), 5.9604644775390625e-08f, 2.98023223876953125e-08f);
+    // u0 = (k + 1/2) 2^-24 is one rounding of k 2^-24 + 2^-25, and v = 1 - u0
+    // = (1 - k 2^-24) - 2^-25: both steps exact wherever v < 1/2 (k 2^-24 has
+    // 24 significant bits at most)
+    const float k0 = static_cast<float>(r0 >> 8);
+    const float u0 = fmaf(k0, 5.9604644775390625e-08f, 2.98023223876953125e-08f);
+    const float v = fmaf(k0, -5.9604644775390625e-08f, 1.0f) - 2.98023223876953125e-08f;
     // -2 ln(1 - v) = v (2 + v (1 + v (2/3 + v/2))) + O(v^5), used below 1/64;
     // above, -2 ln u0 = -2 ln(2) log2(u0)
     const float series = v * fmaf(v, fmaf(v, fmaf(v, 0.5f, 0.6666667f), 1.0f), 2.0f);
     const float x = v < 0.015625f ? series : -1.38629436111989061f * __log2f(u0);  // x >= 2^-24 > 0
     const float rad = sqrt_sfu(x);
-    // angle 2 pi u1 - pi in [-pi, pi) from the exact u1 - 1/2 = (k - 2^23 + 1/2) 2^-24
-    const float angle = fmaf(static_cast<float>(static_cast<int32_t>(r1 >> 8) - 8388608),
+    // angle 2 pi u1 taken to [-pi, pi): the arithmetic shift of the word is
+    // (r1 >> 8) - 2^24 when the top bit is set, an exact turn less
+    const float angle = fmaf(static_cast<float>(static_cast<int32_t>(r1) >> 8),
                              3.7450703871400037e-07f /* 2 pi 2^-24 */,
                              1.8725351935700019e-07f /* pi 2^-24 */);
     float s, c;
     __sincosf(angle, &s, &c);
-    z0 = -rad * c;
-    z1 = -rad * s;
+    z0 = rad * c;
+    z1 = rad * s;
 #else
     const float rad = sqrtf(-2.0f * logf(unit24<float>(r0)));
     float s, c;

@@ -262,6 +262,7 @@ int lbfd_ensemble_destroy(lbfd_ens_t e) {
 }
 
 int lbfd_ensemble_step(lbfd_ens_t e, int64_t n) {
+  NvtxRange nvtx_("lbfd_ensemble_step");
   if (!e) return ens_fail(LBFD_EINVAL, "lbfd_ensemble_step: null handle");
   if (n < 0) return ens_fail(LBFD_EINVAL, "lbfd_ensemble_step: n must be >= 0");
   if (n == 0) return LBFD_OK;
@@ -294,6 +295,7 @@ int lbfd_ensemble_sync(lbfd_ens_t e) {
 
 int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen,
                        int32_t *blocks_per_sm) {
+  NvtxRange nvtx_("lbfd_ensemble_tune");
   if (!e || steps < 1) return ens_fail(LBFD_EINVAL, "lbfd_ensemble_tune: bad argument");
   DevGuard g(e->device);
   ENS_CU(ens_sync_t(e));

@@ -6,12 +6,23 @@
 
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "device.cuh"
 
 #define LBFD_MAX_MODES_DEV 16
 #define LBFD_MAX_Q_DEV 19
 
 namespace lbfd {
+
+// A named NVTX range for the scope (seen by nsys / ncu timelines; a no-op
+// when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Per-launch arguments of the step kernel (passed by value).
 struct StepArgs {

@@ -472,6 +472,7 @@ int upload_tables(lbfd_server *s) {
 
 // One time step of every resident simulation, then results of those done.
 int tick(lbfd_server *s) {
+  NvtxRange nvtx_("server tick");
   if (s->n_active == 0) return LBFD_OK;
   const int ring = int(s->tick_ev.size());
   const int slot = int(s->clock % uint64_t(ring));
@@ -685,6 +686,7 @@ int lbfd_server_submit(lbfd_server_t s, const lbfd_request *req, int64_t *id) {
 }
 
 int lbfd_server_pump(lbfd_server_t s, int32_t max_steps, int64_t *left) {
+  NvtxRange nvtx_("lbfd_server_pump");
   if (!s || max_steps < 0) return srv_fail(LBFD_EINVAL, "lbfd_server_pump: bad argument");
   DevScope scope(s->device);
   const int64_t l0 = s->launches;
@@ -695,6 +697,7 @@ int lbfd_server_pump(lbfd_server_t s, int32_t max_steps, int64_t *left) {
 }
 
 int lbfd_server_drain(lbfd_server_t s) {
+  NvtxRange nvtx_("lbfd_server_drain");
   if (!s) return srv_fail(LBFD_EINVAL, "lbfd_server_drain: null server");
   DevScope scope(s->device);
   const int64_t l0 = s->launches;
@@ -743,6 +746,7 @@ int lbfd_server_get_stats(lbfd_server_t s, lbfd_server_stats *st) {
 
 int lbfd_server_run_trace(lbfd_server_t s, const lbfd_request *reqs, const double *arrival_s, int32_t n,
                           void *sink_host, int64_t sink_bytes, double *latency_s, double *makespan_s) {
+  NvtxRange nvtx_("lbfd_server_run_trace");
   if (!s || n < 0 || (n > 0 && (!reqs || !arrival_s || !latency_s)) || sink_bytes < 0 || (sink_bytes > 0 && !sink_host))
     return srv_fail(LBFD_EINVAL, "lbfd_server_run_trace: bad argument");
   for (int32_t k = 1; k < n; ++k)
