@@ -299,16 +299,23 @@ int lbfd_step(lbfd_t h, int64_t n) {
   fill_step_params(a, o.tau, o.rho_mean);
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
-  if (!h->mrt && n >= 2 && small_fits(h->Q, h->N, h->elem)) {
+  if (!h->mrt && n >= 2 && small_path_fits(o.lattice, o.precision, h->N)) {
     // a small lattice: many steps per launch in shared memory (bit-identical)
     constexpr int64_t kChunk = 4096;
-    int64_t launches = 0;
-    for (int64_t done = 0; done < n;) {
+    int64_t launches = 0, done = 0;
+    bool placed = true;
+    while (done < n) {
       const int chunk = int(std::min<int64_t>(kChunk, n - done));
       const int to = h->cur ^ (chunk & 1);
       a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
       cudaError_t e = launch_step_small(o.lattice, o.precision, h->f[h->cur], h->f[to], a, o.seed, o.lattice_id,
                                         uint64_t(h->t), chunk, h->stream);
+      if (e == cudaErrorNotSupported) {
+        // the cluster cannot be placed on this GPU: one launch per step instead
+        (void)cudaGetLastError();
+        placed = false;
+        break;
+      }
       if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
       h->cur = to;
       h->t += chunk;
@@ -316,7 +323,8 @@ int lbfd_step(lbfd_t h, int64_t n) {
       launches += 1;
     }
     g_launches.fetch_add(launches, std::memory_order_relaxed);
-    return LBFD_OK;
+    if (placed) return LBFD_OK;
+    n -= done;
   }
   for (int64_t k = 0; k < n; ++k) {
     a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));

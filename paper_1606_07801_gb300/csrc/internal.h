@@ -118,13 +118,12 @@ cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t
 cudaError_t launch_step_mrt(int lattice, int precision, const void *src, void *dst, const StepArgs &a, const double *m,
                             const double *w, const double *tau, cudaStream_t stream);
 
-// Many steps of a lattice small enough for one block's shared memory in one
-// launch (step_small.cu): src holds the stored state at step t0, dst receives
-// it after nsteps steps (dst may equal src).
+// Many steps of a small lattice in one launch (step_small.cu), in one
+// block's shared memory or in a thread-block cluster's distributed shared
+// memory (up to 8 x kSmallMaxBytes): src holds the stored state at step t0,
+// dst receives it after nsteps steps (dst may equal src).
 constexpr size_t kSmallMaxBytes = 200 * 1024;
-inline bool small_fits(int Q, int64_t N, int elem) {
-  return N >= 1 && 2 * static_cast<uint64_t>(Q) * static_cast<uint64_t>(N) * static_cast<uint64_t>(elem) <= kSmallMaxBytes;
-}
+bool small_path_fits(int lattice, int precision, int64_t N);
 cudaError_t launch_step_small(int lattice, int precision, const void *src, void *dst, const StepArgs &a, uint64_t seed,
                               uint32_t lattice_id, uint64_t t0, int nsteps, cudaStream_t stream);
 

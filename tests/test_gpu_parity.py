@@ -246,14 +246,20 @@ def test_box_muller_grid_edges(precision, tol):
 
 
 @pytest.mark.parametrize("lat,dims,precision", [
-    (lb.D1Q3, (256,), lb.F64), (lb.D1Q3, (1001,), lb.F32), (lb.D2Q9, (40, 30), lb.F32), (lb.D2Q9, (13, 7), lb.F64),
-    (lb.D3Q19, (9, 8, 7), lb.F32), (lb.D3Q19, (6, 5, 4), lb.F32_F16), (lb.D2Q9, (1, 1), lb.F32),
+    # one block
+    (lb.D1Q3, (1001,), lb.F32), (lb.D2Q9, (40, 30), lb.F32), (lb.D3Q19, (9, 8, 7), lb.F32),
+    (lb.D3Q19, (6, 5, 4), lb.F32_F16), (lb.D2Q9, (1, 1), lb.F32), (lb.D2Q9, (5, 6), lb.F64),
+    # thread-block clusters: FP64 spread one CTA per 32 sites, larger states over several CTAs
+    (lb.D1Q3, (256,), lb.F64), (lb.D1Q3, (65,), lb.F64), (lb.D2Q9, (13, 7), lb.F64), (lb.D2Q9, (64, 64), lb.F32),
+    (lb.D3Q19, (16, 16, 16), lb.F32), (lb.D3Q19, (10, 10, 10), lb.F64), (lb.D2Q9, (100, 100), lb.F32_F16),
+    (lb.D3Q19, (20, 20, 21), lb.F32),
 ])
 @pytest.mark.parametrize("mode,dist", [(lb.NOISE_LOCAL, lb.GAUSSIAN), (lb.NOISE_GLOBAL, lb.UNIFORM)])
 def test_small_lattice_many_steps_per_launch(lat, dims, precision, mode, dist):
-    """A lattice whose two buffers fit one block's shared memory takes one
-    launch for up to 4096 steps; the result equals one launch per step bit for
-    bit, across launch boundaries and odd and even step counts."""
+    """A lattice whose two buffers fit one block's shared memory, or the
+    distributed shared memory of a cluster of up to 8 CTAs, takes one launch
+    for up to 4096 steps; the result equals one launch per step bit for bit,
+    across launch boundaries and odd and even step counts."""
     Q, N = lb.Q_OF[lat], int(np.prod(dims))
     f0 = synth.random_populations(Q, N, 30.0, 0.3, seed=N)
     kw = dict(precision=precision, noise_mode=mode, noise_dist=dist, init=lb.INIT_NONE, lattice_id=5)
