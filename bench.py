@@ -271,8 +271,9 @@ def run_ensemble(args):
         sp["init"] = lb.INIT_UNIFORM
     stream = torch.cuda.Stream()
     ens = lb.Ensemble(lat, specs, stream=stream)
-    n, sites, _, _, _, _ = ens.query()
+    n, sites = ens.query()[:2]
     vx, passes, bps = ens.tune(steps=3)
+    walk = ens.query()[6]
     ens.step(args.warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -316,7 +317,7 @@ def run_ensemble(args):
                                f"[{lo}, {hi}], rho_mean U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian "
                                f"noise",
                    "sites": sites, "sites_per_item_max": vx, "tile_passes": passes, "blocks_per_sm": bps,
-                   "graph_steps": 16,
+                   "tile_walk": "contiguous" if walk == lb.WALK_CONTIGUOUS else "strided", "graph_steps": 16,
                    "l2": "inputs larger than L2: %.0f MB per population buffer" % (4.0 * Q * sites / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "algorithmic_bytes_per_launch": 8 * Q * sites, "kernel": "k_batch_step",
@@ -356,7 +357,8 @@ def run_served(args):
     policy = lb.POLICY_SHORTEST if args.policy == "shortest" else lb.POLICY_FIFO
     srv = lb.Server(hbm_budget=int(args.budget_gb * (1 << 30)), max_active=4096, max_ahead=4, passes=args.passes,
                     policy=policy, max_active_sites=args.max_active_sites, occupancy=args.occupancy,
-                    solo_sites=args.solo_sites)
+                    solo_sites=args.solo_sites,
+                    walk=lb.WALK_CONTIGUOUS if args.walk == "contiguous" else lb.WALK_STRIDED, vx_max=args.vx_max)
     # warm-up: a short trace of small requests (module load, first launches)
     warm = [abi.make_request(k % 3, [(512,), (64, 64), (16, 16, 16)][k % 3], 1.0, 10.0, 99 + k, 20,
                              result=lb.RESULT_RHO) for k in range(max(3, args.warmup))]
@@ -404,7 +406,8 @@ def run_served(args):
                                "lattice uniform over D1Q3 (L log-uniform 256-65536) / D2Q9 (side log-uniform "
                                "32-1024) / D3Q19 (side log-uniform 32-128), steps log-uniform 100-10^4, tau "
                                "U[0.6, 1.5], rho_mean U[0.5, 200], FP32, local Gaussian noise, density result",
-                   "hbm_budget_gb": args.budget_gb, "policy": args.policy, "passes": args.passes, "occupancy": args.occupancy,
+                   "hbm_budget_gb": args.budget_gb, "policy": args.policy, "passes": args.passes,
+                   "occupancy": args.occupancy, "walk": args.walk, "vx_max": args.vx_max,
                    "solo_sites": args.solo_sites,
                    "max_active_sites": args.max_active_sites, "site_updates": lups,
                    "step": "one bench step = one served request; value = total site updates / makespan"},
@@ -442,6 +445,8 @@ def main():
     ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
+    ap.add_argument("--walk", default="strided", choices=["strided", "contiguous"])
+    ap.add_argument("--vx-max", type=int, default=2, choices=[1, 2])
     ap.add_argument("--solo-sites", type=int, default=1 << 17)
     ap.add_argument("--max-active-sites", type=int, default=20_000_000)
     ap.add_argument("--sink-mb", type=int, default=2048)

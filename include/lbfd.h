@@ -277,16 +277,25 @@ int lbfd_ensemble_sync(lbfd_ens_t e);
 
 /* Times the candidate work decompositions (at most 1 or 2 sites per item,
  * times tiles of 1, 2, 4 or 8 passes, times two register/occupancy variants
- * of the kernel) over `steps` launches each that write only the spare
- * buffers, keeps the fastest and reports it: sites per item at most, passes,
- * resident blocks per SM (any output may be NULL).  The state and t are
- * unchanged.  Synchronous. */
+ * of the kernel, times the two tile orders LBFD_WALK_*) over `steps`
+ * launches each that write only the spare buffers, keeps the fastest and
+ * reports it: sites per item at most, passes, resident blocks per SM (any
+ * output may be NULL; lbfd_ensemble_query also gives the tile order).  The
+ * state and t are unchanged.  Synchronous. */
 int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t *passes_chosen,
                        int32_t *blocks_per_sm);
 
-/* Members, total sites, t and the current decomposition (any pointer may be NULL). */
+/* Sets the work decomposition without timing: sites per item at most
+ * (1 or 2), tile passes (1, 2, 4 or 8), register/occupancy variant (0 or 1)
+ * and tile order (LBFD_WALK_*).  Every decomposition gives the same
+ * results.  LBFD_EINVAL on any other value.  Synchronous. */
+int lbfd_ensemble_plan(lbfd_ens_t e, int32_t vx_max, int32_t passes, int32_t occupancy, int32_t walk);
+
+/* Members, total sites, t and the current decomposition: sites per item at
+ * most, tile passes, resident blocks per SM, tile order LBFD_WALK_* (any
+ * pointer may be NULL). */
 int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx,
-                        int32_t *passes, int32_t *blocks_per_sm);
+                        int32_t *passes, int32_t *blocks_per_sm, int32_t *walk);
 
 /* Per-member state in FP64, layout [i][site] (as lbfd_get_f / lbfd_set_f),
  * and FP64 mass.  Synchronous. */
@@ -321,6 +330,8 @@ int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
 
 #define LBFD_POLICY_FIFO 0      /* admit in arrival order (later requests may pass one that does not fit) */
 #define LBFD_POLICY_SHORTEST 1  /* admit the request with the fewest site updates (sites x steps) first */
+#define LBFD_WALK_STRIDED 0
+#define LBFD_WALK_CONTIGUOUS 1
 
 #define LBFD_REQ_UNKNOWN (-1)
 #define LBFD_REQ_QUEUED 0
@@ -339,7 +350,11 @@ typedef struct lbfd_server_options {
     int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
     int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
     int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
-    int32_t reserved[7];
+    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_STRIDED (a block takes every
+                               grid-th tile) or LBFD_WALK_CONTIGUOUS (one run of consecutive tiles) */
+    int32_t vx_max;         /* sites per work item of the batched kernel at most: 2 (members with even Lx
+                               take two) or 1 (a kernel without the two-site path, fewer registers) */
+    int32_t reserved[5];
     int64_t solo_sites;     /* simulations of at least this many sites are stepped by their own
                                single-lattice launch (parameters as kernel arguments) instead of the
                                batched launch; 0 = all batched.  Results are the same either way. */
@@ -377,7 +392,8 @@ typedef struct lbfd_server_stats {
 typedef struct lbfd_server *lbfd_server_t;
 
 /* Defaults: FP32, local Gaussian noise, current device, 1 GiB budget, no
- * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO, solo_sites 2^17. */
+ * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO, occupancy 0, strided
+ * walk, vx_max 2, solo_sites 2^17. */
 int lbfd_server_options_init(lbfd_server_options *opt);
 
 /* Creates a server: one device arena of hbm_budget bytes, two streams

@@ -16,14 +16,15 @@ from . import build as _build_mod
 from .lbfd import (D1Q3, D2Q5, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
                    F64, GAUSSIAN, INIT_HOST, INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL,
                    NOISE_LOCAL, NOISE_OFF, OK, POLICY_FIFO, POLICY_SHORTEST, Q_OF, REQ_DONE, REQ_QUEUED, REQ_RUNNING,
-                   REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, LbfdError, Options, load)
+                   REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, WALK_CONTIGUOUS, WALK_STRIDED, LbfdError,
+                   Options, load)
 from . import lbfd as abi
 
 __all__ = ["Simulation", "Ensemble", "Server", "STORAGE_DTYPE", "abi", "build", "load", "LbfdError", "Options", "D1Q3", "D2Q9", "D3Q19", "D2Q5", "F32", "F64",
            "F32_F16", "F32_BF16",
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
            "INIT_NONE", "INIT_HOST", "RESULT_F", "RESULT_RHO", "RESULT_NONE", "POLICY_FIFO", "POLICY_SHORTEST",
-           "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE", "REQ_UNKNOWN", "Q_OF", "D_OF"]
+           "WALK_STRIDED", "WALK_CONTIGUOUS", "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE", "REQ_UNKNOWN", "Q_OF", "D_OF"]
 
 # numpy type of one stored value per precision (bfloat16 as its raw 16 bits)
 STORAGE_DTYPE = {F32: np.float32, F64: np.float64, F32_F16: np.float16, F32_BF16: np.uint16}
@@ -189,7 +190,12 @@ class Ensemble:
         """Picks the fastest work decomposition; returns (vx, passes, blocks per SM)."""
         return abi.lbfd_ensemble_tune(self.h, steps)
 
+    def plan(self, vx_max: int, passes: int, occupancy: int = 0, walk: int = WALK_STRIDED) -> None:
+        """Sets the work decomposition without timing (results do not depend on it)."""
+        abi.lbfd_ensemble_plan(self.h, vx_max, passes, occupancy, walk)
+
     def query(self):
+        """(members, total sites, t, sites per item at most, tile passes, blocks per SM, tile order)."""
         return abi.lbfd_ensemble_query(self.h)
 
     def get_f(self, member: int) -> np.ndarray:
@@ -210,12 +216,12 @@ class Server:
     def __init__(self, *, precision: int = F32, noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN,
                  hbm_budget: int = 1 << 30, max_active: int = 1024, max_ahead: int = 4, passes: int = 1,
                  policy: int = POLICY_FIFO, max_active_sites: int = 0, occupancy: int = 0,
-                 solo_sites: int = 1 << 17, device: int = -1):
+                 solo_sites: int = 1 << 17, walk: int = 0, vx_max: int = 2, device: int = -1):
         o = abi.lbfd_server_options_init()
         o.precision, o.noise_mode, o.noise_dist, o.device = precision, noise_mode, noise_dist, device
         o.hbm_budget, o.max_active, o.max_ahead, o.passes = int(hbm_budget), max_active, max_ahead, passes
         o.policy, o.max_active_sites, o.occupancy = policy, int(max_active_sites), occupancy
-        o.solo_sites = int(solo_sites)
+        o.solo_sites, o.walk, o.vx_max = int(solo_sites), walk, vx_max
         self.precision = precision
         self._bufs = {}
         self.h = abi.lbfd_server_create(o)

@@ -53,27 +53,27 @@ cudaError_t launch_clock_advance(uint64_t *clock_dev, cudaStream_t stream) {
 }
 
 cudaError_t launch_batch_step(int lattice, int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
-                              int nmembers, int64_t ntiles, int passes, int occ, int noise_mode, int noise_dist,
-                              int grid, cudaStream_t stream) {
+                              int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode,
+                              int noise_dist, int grid, cudaStream_t stream) {
   switch (lattice) {
     case kD1Q3:
-      return launch_batch_step_d1q3(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, noise_mode,
+      return launch_batch_step_d1q3(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
                                     noise_dist, grid, stream);
     case kD2Q9:
-      return launch_batch_step_d2q9(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, noise_mode,
+      return launch_batch_step_d2q9(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
                                     noise_dist, grid, stream);
     case kD3Q19:
-      return launch_batch_step_d3q19(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, noise_mode,
+      return launch_batch_step_d3q19(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
                                      noise_dist, grid, stream);
   }
   return cudaErrorInvalidValue;
 }
 
-int batch_blocks_per_sm(int lattice, int precision, int occ, int noise_mode, int noise_dist) {
+int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int noise_mode, int noise_dist) {
   switch (lattice) {
-    case kD1Q3: return batch_blocks_per_sm_d1q3(precision, occ, noise_mode, noise_dist);
-    case kD2Q9: return batch_blocks_per_sm_d2q9(precision, occ, noise_mode, noise_dist);
-    case kD3Q19: return batch_blocks_per_sm_d3q19(precision, occ, noise_mode, noise_dist);
+    case kD1Q3: return batch_blocks_per_sm_d1q3(precision, occ, vx_max, noise_mode, noise_dist);
+    case kD2Q9: return batch_blocks_per_sm_d2q9(precision, occ, vx_max, noise_mode, noise_dist);
+    case kD3Q19: return batch_blocks_per_sm_d3q19(precision, occ, vx_max, noise_mode, noise_dist);
   }
   return 1;
 }

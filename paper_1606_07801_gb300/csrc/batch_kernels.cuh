@@ -26,6 +26,8 @@
 namespace lbfd {
 
 constexpr int kBatchThreads = 256;
+// Order in which a block of the persistent grid takes its tiles.
+constexpr int kWalkStrided = 0, kWalkContiguous = 1;
 
 // One member, as the host builds it (constant while the member is listed).
 struct BatchMember {
@@ -82,26 +84,53 @@ constexpr int batch_min_blocks() {
   return OCC == 0 ? step_min_blocks<LAT, S>() : (step_min_blocks<LAT, S>() > 1 ? step_min_blocks<LAT, S>() - 1 : 1);
 }
 
-template <int LAT, typename S, int NOISE, int OCC>
+// VXMAX = 1: every member takes one site per item (the two-site path, with
+// its larger register footprint, is not compiled in); VXMAX = 2: members
+// with even Lx take two.
+template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>())
     k_batch_step(S *__restrict__ base, const BatchStep *__restrict__ steps, const int64_t *__restrict__ tile_start,
-                 int nmembers, int64_t ntiles, int passes) {
-  // two copies: the copy for tile k + 1 is written while no thread reads the
-  // copy of tile k - 1 any more (one barrier per tile)
+                 int nmembers, int ntiles, int passes, int walk) {
+  // Tiles of this block: every gridDim.x-th tile from blockIdx.x (strided
+  // walk), or one run of consecutive tiles (contiguous walk), in which the
+  // member changes only where the run crosses a member boundary.
+  int tile, stop, stride;
+  if (walk == kWalkContiguous) {
+    tile = static_cast<int>(int64_t(blockIdx.x) * ntiles / gridDim.x);
+    stop = static_cast<int>(int64_t(blockIdx.x + 1) * ntiles / gridDim.x);
+    stride = 1;
+  } else {
+    tile = blockIdx.x;
+    stop = ntiles;
+    stride = gridDim.x;
+  }
+  // two copies of the member's arguments and tile range: the copy for the
+  // next member is written while no thread reads the copy before the current
+  // one any more (one barrier per change of member)
   __shared__ BatchStep sb[2];
-  int buf = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
-    if (threadIdx.x < 32) {
-      const int m = batch_find_member(tile_start, nmembers, tile);
-      const int4 *g = reinterpret_cast<const int4 *>(steps + m);
-      int4 *s = reinterpret_cast<int4 *>(&sb[buf]);
-      for (int k = threadIdx.x; k < int(sizeof(BatchStep) / 16); k += 32) s[k] = g[k];
+  __shared__ int srange[2][2];
+  int buf = 1, lo = 0, hi = 0;
+  for (; tile < stop; tile += stride) {
+    if (tile < lo || tile >= hi) {
+      buf ^= 1;
+      if (threadIdx.x < 32) {
+        const int m = batch_find_member(tile_start, nmembers, tile);
+        const int4 *g = reinterpret_cast<const int4 *>(steps + m);
+        int4 *s = reinterpret_cast<int4 *>(&sb[buf]);
+        for (int k = threadIdx.x; k < int(sizeof(BatchStep) / 16); k += 32) s[k] = g[k];
+        if (threadIdx.x == 0) {
+          srange[buf][0] = static_cast<int>(__ldg(tile_start + m));
+          srange[buf][1] = m + 1 < nmembers ? static_cast<int>(__ldg(tile_start + m + 1)) : ntiles;
+        }
+      }
+      __syncthreads();
+      lo = srange[buf][0];
+      hi = srange[buf][1];
     }
-    __syncthreads();
     const BatchStep &b = sb[buf];
     const S *src = base + b.src;
     S *dst = base + b.dst;
-    const int first = static_cast<int>(tile - b.tile0) * passes * kBatchThreads + threadIdx.x;
+    const int first = (tile - lo) * passes * kBatchThreads + threadIdx.x;
     for (int p = 0; p < passes; ++p) {
       const int item = first + p * kBatchThreads;
       if (item < b.items) {
@@ -111,7 +140,7 @@ __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>()
         const int y = row - z * b.a.Ly;
         // a member's value offsets fit 32 bits (checked when it is listed)
         using C = SrtCollide<LAT, typename Store<S>::R, NOISE>;
-        if (b.vx == 2)
+        if (VXMAX == 2 && b.vx == 2)
           step_vec_body<LAT, S, 2, NOISE, C, uint32_t>(src, dst, b.a, col * 2, y, z);
         else
           step_scalar_body<LAT, S, NOISE, C, uint32_t>(src, dst, b.a, col, y, z);
@@ -120,49 +149,67 @@ __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>()
   }
 }
 
-template <int LAT, typename S, int OCC>
-cudaError_t batch_step_occ(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int64_t ntiles,
-                           int passes, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
+template <int LAT, typename S, int OCC, int VXMAX>
+cudaError_t batch_step_occ(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int ntiles,
+                           int passes, int walk, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
   if (noise_mode == kNoiseOff)
-    k_batch_step<LAT, S, kStepNoiseOff, OCC><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
-                                                                                 passes);
+    k_batch_step<LAT, S, kStepNoiseOff, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
+                                                                                        ntiles, passes, walk);
   else if (noise_dist == kGaussian)
-    k_batch_step<LAT, S, kStepNoiseGauss, OCC><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
-                                                                                   ntiles, passes);
+    k_batch_step<LAT, S, kStepNoiseGauss, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start,
+                                                                                          nmembers, ntiles, passes, walk);
   else
-    k_batch_step<LAT, S, kStepNoiseFlat, OCC><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
-                                                                                  ntiles, passes);
+    k_batch_step<LAT, S, kStepNoiseFlat, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
+                                                                                         ntiles, passes, walk);
   return cudaGetLastError();
 }
 
+// vx_max: the largest sites per item of any member (1 or 2).
 template <int LAT, typename S>
 cudaError_t batch_step_t(void *base, const BatchStep *steps, const int64_t *tile_start, int nmembers, int64_t ntiles,
-                         int passes, int occ, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
+                         int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
+                         cudaStream_t stream) {
   S *b = static_cast<S *>(base);
+  if (ntiles >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+  const int nt = static_cast<int>(ntiles);
+  if (vx_max == 1) {
+    if (occ == 1)
+      return batch_step_occ<LAT, S, 1, 1>(b, steps, tile_start, nmembers, nt, passes, walk, noise_mode, noise_dist,
+                                          grid, stream);
+    return batch_step_occ<LAT, S, 0, 1>(b, steps, tile_start, nmembers, nt, passes, walk, noise_mode, noise_dist, grid,
+                                        stream);
+  }
   if (occ == 1)
-    return batch_step_occ<LAT, S, 1>(b, steps, tile_start, nmembers, ntiles, passes, noise_mode, noise_dist, grid,
-                                     stream);
-  return batch_step_occ<LAT, S, 0>(b, steps, tile_start, nmembers, ntiles, passes, noise_mode, noise_dist, grid,
-                                   stream);
+    return batch_step_occ<LAT, S, 1, 2>(b, steps, tile_start, nmembers, nt, passes, walk, noise_mode, noise_dist, grid,
+                                        stream);
+  return batch_step_occ<LAT, S, 0, 2>(b, steps, tile_start, nmembers, nt, passes, walk, noise_mode, noise_dist, grid,
+                                      stream);
 }
 
-template <int LAT, typename S, int OCC>
+template <int LAT, typename S, int OCC, int VXMAX>
 int batch_blocks_occ(int noise_mode, int noise_dist) {
   int nb = 0;
   cudaError_t e;
   if (noise_mode == kNoiseOff)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseOff, OCC>, kBatchThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseOff, OCC, VXMAX>,
+                                                      kBatchThreads, 0);
   else if (noise_dist == kGaussian)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseGauss, OCC>, kBatchThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseGauss, OCC, VXMAX>,
+                                                      kBatchThreads, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseFlat, OCC>, kBatchThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseFlat, OCC, VXMAX>,
+                                                      kBatchThreads, 0);
   return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 
 // Resident blocks per SM of the batch kernel (sizes the persistent grid).
 template <int LAT, typename S>
-int batch_blocks_per_sm(int occ, int noise_mode, int noise_dist) {
-  return occ == 1 ? batch_blocks_occ<LAT, S, 1>(noise_mode, noise_dist) : batch_blocks_occ<LAT, S, 0>(noise_mode, noise_dist);
+int batch_blocks_per_sm(int occ, int vx_max, int noise_mode, int noise_dist) {
+  if (vx_max == 1)
+    return occ == 1 ? batch_blocks_occ<LAT, S, 1, 1>(noise_mode, noise_dist)
+                    : batch_blocks_occ<LAT, S, 0, 1>(noise_mode, noise_dist);
+  return occ == 1 ? batch_blocks_occ<LAT, S, 1, 2>(noise_mode, noise_dist)
+                  : batch_blocks_occ<LAT, S, 0, 2>(noise_mode, noise_dist);
 }
 
 }  // namespace lbfd

@@ -56,7 +56,7 @@ int d_of(int lattice) { return lattice == LBFD_D1Q3 ? 1 : (lattice == LBFD_D2Q9 
 
 struct lbfd_ens {
   int lattice = 0, precision = 0, noise_mode = 0, noise_dist = 0, elem = 4, Q = 0, device = 0, n = 0;
-  int vx_max = 2, passes = 1, occ = 0, grid = 1, bps = 1;
+  int vx_max = 2, kvx = 2, passes = 1, occ = 0, walk = 0, grid = 1, bps = 1;  // kvx: largest vx of a member
   int64_t ntiles = 0;
   std::vector<BatchMember> hmem;
   std::vector<int64_t> tile_start;
@@ -80,13 +80,17 @@ struct lbfd_ens {
 
 static cudaError_t ens_launch(lbfd_ens *e) {
   return launch_batch_step(e->lattice, e->precision, e->buf, e->dsteps, e->dtile_start, e->n, e->ntiles, e->passes,
-                           e->occ, e->noise_mode, e->noise_dist, e->grid, e->stream);
+                           e->occ, e->walk, e->kvx, e->noise_mode, e->noise_dist, e->grid, e->stream);
 }
 
-// Work decomposition (sites per item, tile passes, occupancy variant) and
-// persistent grid.
-static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ) {
-  for (BatchMember &m : e->hmem) m.vx = (vx_max >= 2 && m.Lx % 2 == 0) ? 2 : 1;
+// Work decomposition (sites per item, tile passes, occupancy variant, tile
+// order) and persistent grid.
+static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ, int walk) {
+  e->kvx = 1;
+  for (BatchMember &m : e->hmem) {
+    m.vx = (vx_max >= 2 && m.Lx % 2 == 0) ? 2 : 1;
+    e->kvx = std::max(e->kvx, int(m.vx));
+  }
   e->tile_start.assign(e->n, 0);
   e->ntiles = batch_assign_tiles(e->hmem.data(), e->n, passes, e->tile_start.data());
   ENS_CU(cudaMemcpy(e->dmem, e->hmem.data(), sizeof(BatchMember) * e->n, cudaMemcpyHostToDevice));
@@ -94,7 +98,8 @@ static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ) {
   e->vx_max = vx_max;
   e->passes = passes;
   e->occ = occ;
-  e->bps = batch_blocks_per_sm(e->lattice, e->precision, occ, e->noise_mode, e->noise_dist);
+  e->walk = walk;
+  e->bps = batch_blocks_per_sm(e->lattice, e->precision, occ, e->kvx, e->noise_mode, e->noise_dist);
   int sms = 0;
   ENS_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
   e->grid = int(std::max<int64_t>(1, std::min<int64_t>(e->ntiles, int64_t(sms) * e->bps)));
@@ -243,7 +248,7 @@ int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, in
     ens_free(e);
     return rc;
   }
-  int rc = ens_plan(e, 2, 1, 0);
+  int rc = ens_plan(e, 2, 1, 0, kWalkStrided);
   if (rc) {
     ens_free(e);
     return rc;
@@ -300,35 +305,38 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
   DevGuard g(e->device);
   ENS_CU(ens_sync_t(e));
   // candidates: sites per item (1, or 2 where Lx is even) x tile passes x
-  // occupancy variant of the kernel
+  // occupancy variant of the kernel x tile order
   const int vx_cand[2] = {1, 2};
   const int pass_cand[4] = {1, 2, 4, 8};
   float best_ms = -1.0f;
-  int best_vx = e->vx_max, best_passes = e->passes, best_occ = e->occ;
+  int best_vx = e->vx_max, best_passes = e->passes, best_occ = e->occ, best_walk = e->walk;
   cudaEvent_t a = nullptr, b = nullptr;
   ENS_CU(cudaEventCreate(&a));
   ENS_CU(cudaEventCreate(&b));
   // timing launches read the state and write the spare block only (t is not advanced)
   int64_t launched = 0;
-  for (int occ = 0; occ < 2; ++occ) {
-    for (int vx : vx_cand) {
-      for (int passes : pass_cand) {
-        int rc = ens_plan(e, vx, passes, occ);
-        if (rc) return rc;
-        ENS_CU(launch_batch_prep(e->dmem, e->n, e->t_dev, 0, e->noise_mode, e->noise_dist, e->dsteps, e->stream));
-        ENS_CU(ens_launch(e));
-        ENS_CU(cudaEventRecord(a, e->stream));
-        for (int k = 0; k < steps; ++k) ENS_CU(ens_launch(e));
-        ENS_CU(cudaEventRecord(b, e->stream));
-        ENS_CU(cudaEventSynchronize(b));
-        launched += 2 + steps;
-        float ms = 0.0f;
-        ENS_CU(cudaEventElapsedTime(&ms, a, b));
-        if (best_ms < 0.0f || ms < best_ms) {
-          best_ms = ms;
-          best_vx = vx;
-          best_passes = passes;
-          best_occ = occ;
+  for (int walk = 0; walk < 2; ++walk) {
+    for (int occ = 0; occ < 2; ++occ) {
+      for (int vx : vx_cand) {
+        for (int passes : pass_cand) {
+          int rc = ens_plan(e, vx, passes, occ, walk);
+          if (rc) return rc;
+          ENS_CU(launch_batch_prep(e->dmem, e->n, e->t_dev, 0, e->noise_mode, e->noise_dist, e->dsteps, e->stream));
+          ENS_CU(ens_launch(e));
+          ENS_CU(cudaEventRecord(a, e->stream));
+          for (int k = 0; k < steps; ++k) ENS_CU(ens_launch(e));
+          ENS_CU(cudaEventRecord(b, e->stream));
+          ENS_CU(cudaEventSynchronize(b));
+          launched += 2 + steps;
+          float ms = 0.0f;
+          ENS_CU(cudaEventElapsedTime(&ms, a, b));
+          if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best_vx = vx;
+            best_passes = passes;
+            best_occ = occ;
+            best_walk = walk;
+          }
         }
       }
     }
@@ -336,7 +344,7 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   count_launches(launched);
-  int rc = ens_plan(e, best_vx, best_passes, best_occ);
+  int rc = ens_plan(e, best_vx, best_passes, best_occ, best_walk);
   if (rc) return rc;
   if (vx_chosen) *vx_chosen = best_vx;
   if (passes_chosen) *passes_chosen = best_passes;
@@ -344,8 +352,17 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
   return LBFD_OK;
 }
 
+int lbfd_ensemble_plan(lbfd_ens_t e, int32_t vx_max, int32_t passes, int32_t occupancy, int32_t walk) {
+  if (!e || (vx_max != 1 && vx_max != 2) || (passes != 1 && passes != 2 && passes != 4 && passes != 8) ||
+      (occupancy != 0 && occupancy != 1) || (walk != LBFD_WALK_STRIDED && walk != LBFD_WALK_CONTIGUOUS))
+    return ens_fail(LBFD_EINVAL, "lbfd_ensemble_plan: bad argument");
+  DevGuard g(e->device);
+  ENS_CU(ens_sync_t(e));
+  return ens_plan(e, vx_max, passes, occupancy, walk);
+}
+
 int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, int64_t *t, int32_t *vx,
-                        int32_t *passes, int32_t *blocks_per_sm) {
+                        int32_t *passes, int32_t *blocks_per_sm, int32_t *walk) {
   if (!e) return ens_fail(LBFD_EINVAL, "lbfd_ensemble_query: null handle");
   if (n_members) *n_members = e->n;
   if (total_sites) *total_sites = e->total_sites;
@@ -353,6 +370,7 @@ int lbfd_ensemble_query(lbfd_ens_t e, int32_t *n_members, int64_t *total_sites, 
   if (vx) *vx = e->vx_max;
   if (passes) *passes = e->passes;
   if (blocks_per_sm) *blocks_per_sm = e->bps;
+  if (walk) *walk = e->walk;
   return LBFD_OK;
 }
 

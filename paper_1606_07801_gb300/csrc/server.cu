@@ -159,7 +159,7 @@ struct SrvRequest {
 struct lbfd_server {
   lbfd_server_options opt{};
   int device = 0, elem = 4, sms = 1;
-  int bps[3] = {1, 1, 1};
+  int bps[3][2] = {{1, 1}, {1, 1}, {1, 1}};  // per lattice type and largest sites per item (1, 2)
   cudaStream_t cs = nullptr, xs = nullptr;  // compute, copy
   cudaStream_t ls[3] = {nullptr, nullptr, nullptr};  // per lattice type, so the launches of a tick overlap
   cudaEvent_t prep_ev = nullptr, lat_ev[3] = {nullptr, nullptr, nullptr};
@@ -192,7 +192,7 @@ struct lbfd_server {
   std::vector<int64_t> copying;
   std::vector<int64_t> pending;  // results waiting for room in the trace sink
   bool dirty = true;
-  int seg_off[3] = {0, 0, 0}, seg_n[3] = {0, 0, 0};
+  int seg_off[3] = {0, 0, 0}, seg_n[3] = {0, 0, 0}, seg_vx[3] = {1, 1, 1};
   int64_t seg_tiles[3] = {0, 0, 0};
   uint64_t clock = 0;
   int64_t n_done = 0, site_updates = 0, resident_bytes = 0, peak_resident_bytes = 0, resident_sites = 0,
@@ -456,9 +456,11 @@ int upload_tables(lbfd_server *s) {
         continue;
       }
       hm[n++] = make_batch_member(q.r.dims, q.r.tau, q.r.rho_mean, q.r.seed, q.r.lattice_id, q.region / s->elem,
-                                  (q.region + q.block) / s->elem, q.t0, 2);
+                                  (q.region + q.block) / s->elem, q.t0, s->opt.vx_max);
     }
     s->seg_n[L] = n - s->seg_off[L];
+    s->seg_vx[L] = 1;
+    for (int m = s->seg_off[L]; m < n; ++m) s->seg_vx[L] = std::max(s->seg_vx[L], int(hm[m].vx));
     s->seg_tiles[L] = batch_assign_tiles(hm + s->seg_off[L], s->seg_n[L], s->opt.passes, hts + s->seg_off[L]);
   }
   if (n > 0) {
@@ -495,9 +497,11 @@ int tick(lbfd_server *s) {
     if (s->seg_n[L] == 0) continue;
     cudaStream_t st = fork ? s->ls[L] : s->cs;
     if (fork) SRV_CU(cudaStreamWaitEvent(st, s->fork_ev, 0));
-    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L])));
+    const int vx = s->seg_vx[L];
+    const int grid =
+        int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L][vx - 1])));
     SRV_CU(launch_batch_step(L, s->opt.precision, s->arena, s->d_steps + s->seg_off[L], s->d_tile_start + s->seg_off[L],
-                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.noise_mode,
+                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.walk, vx, s->opt.noise_mode,
                              s->opt.noise_dist, grid, st));
     s->launches += 1;
     if (fork) {
@@ -593,6 +597,8 @@ int lbfd_server_options_init(lbfd_server_options *opt) {
   opt->max_ahead = 4;
   opt->passes = 1;
   opt->policy = LBFD_POLICY_FIFO;
+  opt->walk = LBFD_WALK_STRIDED;
+  opt->vx_max = 2;
   opt->solo_sites = int64_t(1) << 17;
   return LBFD_OK;
 }
@@ -613,6 +619,9 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
     return srv_fail(LBFD_EINVAL, "server: passes must be 1, 2, 4 or 8");
   if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST) return srv_fail(LBFD_EINVAL, "server: unknown policy");
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
+  if (o.vx_max != 1 && o.vx_max != 2) return srv_fail(LBFD_EINVAL, "server: vx_max must be 1 or 2");
+  if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS)
+    return srv_fail(LBFD_EINVAL, "server: walk must be LBFD_WALK_STRIDED or LBFD_WALK_CONTIGUOUS");
   if (o.max_active_sites < 0) return srv_fail(LBFD_EINVAL, "server: max_active_sites must be >= 0");
   if (o.solo_sites < 0) return srv_fail(LBFD_EINVAL, "server: solo_sites must be >= 0");
   int dev = o.device;
@@ -656,7 +665,9 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
     server_free(s);
     return rc;
   }
-  for (int L = 0; L < 3; ++L) s->bps[L] = batch_blocks_per_sm(L, o.precision, o.occupancy, o.noise_mode, o.noise_dist);
+  for (int L = 0; L < 3; ++L)
+    for (int vx = 1; vx <= 2; ++vx)
+      s->bps[L][vx - 1] = batch_blocks_per_sm(L, o.precision, o.occupancy, vx, o.noise_mode, o.noise_dist);
   s->largest_free = s->pool->largest_free();
   *out = s;
   return LBFD_OK;

@@ -26,6 +26,7 @@ GAUSSIAN, UNIFORM = 0, 1
 INIT_UNIFORM, INIT_SINE, INIT_NONE, INIT_HOST = 0, 1, 2, 3
 RESULT_F, RESULT_RHO, RESULT_NONE = 0, 1, 2
 POLICY_FIFO, POLICY_SHORTEST = 0, 1
+WALK_STRIDED, WALK_CONTIGUOUS = 0, 1
 REQ_UNKNOWN, REQ_QUEUED, REQ_RUNNING, REQ_DONE = -1, 0, 1, 2
 MAX_Q, MAX_MODES = 19, 16
 
@@ -68,7 +69,8 @@ class ServerOptions(ctypes.Structure):
     _fields_ = [
         ("precision", c_int32), ("noise_mode", c_int32), ("noise_dist", c_int32), ("device", c_int32),
         ("hbm_budget", c_int64), ("max_active_sites", c_int64), ("max_active", c_int32), ("max_ahead", c_int32),
-        ("passes", c_int32), ("policy", c_int32), ("occupancy", c_int32), ("reserved", c_int32 * 7),
+        ("passes", c_int32), ("policy", c_int32), ("occupancy", c_int32), ("walk", c_int32),
+        ("vx_max", c_int32), ("reserved", c_int32 * 5),
         ("solo_sites", c_int64),
     ]
 
@@ -132,8 +134,9 @@ SIGNATURES = {
     "lbfd_ensemble_step": (c_int32, [c_void_p, c_int64]),
     "lbfd_ensemble_sync": (c_int32, [c_void_p]),
     "lbfd_ensemble_tune": (c_int32, [c_void_p, c_int32, P(c_int32), P(c_int32), P(c_int32)]),
+    "lbfd_ensemble_plan": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_int32]),
     "lbfd_ensemble_query": (c_int32, [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int32), P(c_int32),
-                                       P(c_int32)]),
+                                       P(c_int32), P(c_int32)]),
     "lbfd_ensemble_get_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_set_f": (c_int32, [c_void_p, c_int32, c_void_p]),
     "lbfd_ensemble_mass": (c_int32, [c_void_p, c_int32, P(c_double)]),
@@ -398,11 +401,17 @@ def lbfd_ensemble_tune(e: int, steps: int = 3):
     return v.value, p.value, b.value
 
 
+def lbfd_ensemble_plan(e: int, vx_max: int, passes: int, occupancy: int, walk: int) -> None:
+    _check(load().lbfd_ensemble_plan(e, vx_max, passes, occupancy, walk), "lbfd_ensemble_plan")
+
+
 def lbfd_ensemble_query(e: int):
-    n, sites, t, vx, passes, bps = c_int32(), c_int64(), c_int64(), c_int32(), c_int32(), c_int32()
+    """Returns (members, total sites, t, sites per item at most, tile passes, blocks per SM, tile order)."""
+    n, sites, t, vx, passes, bps, walk = c_int32(), c_int64(), c_int64(), c_int32(), c_int32(), c_int32(), c_int32()
     _check(load().lbfd_ensemble_query(e, ctypes.byref(n), ctypes.byref(sites), ctypes.byref(t), ctypes.byref(vx),
-                                      ctypes.byref(passes), ctypes.byref(bps)), "lbfd_ensemble_query")
-    return n.value, sites.value, t.value, vx.value, passes.value, bps.value
+                                      ctypes.byref(passes), ctypes.byref(bps), ctypes.byref(walk)),
+           "lbfd_ensemble_query")
+    return n.value, sites.value, t.value, vx.value, passes.value, bps.value, walk.value
 
 
 def lbfd_ensemble_get_f(e: int, member: int, Q: int, N: int) -> np.ndarray:

@@ -48,6 +48,8 @@ def test_ensemble_rejects_bad_members_without_gpu():
     assert lib.lbfd_ensemble_create(ctypes.byref(h), lb.D2Q9, lb.F32, 0, 0, bad, 1, None) in (abi.EINVAL, abi.ECUDA)
     assert lib.lbfd_ensemble_create(ctypes.byref(h), lb.D2Q9, 9, 0, 0, bad, 1, None) == abi.EINVAL
     assert lib.lbfd_ensemble_create(ctypes.byref(h), lb.D2Q9, lb.F32, 0, 0, bad, 0, None) == abi.EINVAL
+    assert lib.lbfd_ensemble_plan(None, 2, 1, 0, lb.WALK_CONTIGUOUS) == abi.EINVAL
+    assert lib.lbfd_ensemble_query(None, None, None, None, None, None, None, None) == abi.EINVAL
 
 
 def test_options_defaults():

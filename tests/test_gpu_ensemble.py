@@ -44,11 +44,45 @@ def test_members_bit_identical_to_single_lattices(lat, precision):
         e.step(16)   # starts on the odd buffer: single steps, then a chunk
         e.step(1)
         got = [e.get_f(m) for m in range(len(specs))]
-        n, sites, t, vx, passes, bps = e.query()
+        n, sites, t, vx, passes, bps, walk = e.query()
     assert (n, t) == (len(specs), 38)
     assert sites == sum(int(np.prod(s["dims"])) for s in specs)
     for m, sp in enumerate(specs):
         assert np.array_equal(got[m], _alone(lat, sp, precision, 38)), m
+
+
+@pytest.mark.parametrize("lat", [lb.D2Q9, lb.D3Q19])
+@pytest.mark.parametrize("vx,passes,occ,walk", [(1, 1, 0, lb.WALK_CONTIGUOUS), (2, 8, 1, lb.WALK_CONTIGUOUS),
+                                                (2, 1, 0, lb.WALK_CONTIGUOUS), (2, 2, 1, lb.WALK_STRIDED),
+                                                (1, 4, 0, lb.WALK_STRIDED)])
+def test_every_decomposition_bit_identical(lat, vx, passes, occ, walk):
+    """Sites per item, tile passes, occupancy variant and tile order change
+    only which thread computes a site, never its value.  The members are
+    large enough (about 10^6 sites in all) that a block of the persistent
+    grid takes several tiles and, in the contiguous order, crosses members."""
+    g = np.random.default_rng(lat * 100 + passes * 10 + walk)
+    specs = _specs(lat, 7, seed=lat * 3 + passes)
+    for k, sp in enumerate(specs):
+        if lat == lb.D2Q9:
+            sp["dims"] = (int(g.integers(200, 420)), int(g.integers(150, 330)))
+        else:
+            sp["dims"] = (int(g.integers(40, 66)), int(g.integers(30, 50)), int(g.integers(20, 41)))
+    with lb.Ensemble(lat, specs) as e:
+        e.plan(vx, passes, occ, walk)
+        q = e.query()
+        assert (q[3], q[4], q[6]) == (vx, passes, walk) and q[5] >= 1
+        e.step(19)
+        got = [e.get_f(m) for m in range(len(specs))]
+    for m, sp in enumerate(specs):
+        assert np.array_equal(got[m], _alone(lat, sp, lb.F32, 19)), m
+
+
+def test_plan_rejects_bad_values():
+    specs = _specs(lb.D2Q9, 2, seed=1)
+    with lb.Ensemble(lb.D2Q9, specs) as e:
+        for bad in [(3, 1, 0, 0), (2, 3, 0, 0), (2, 1, 2, 0), (2, 1, 0, 2)]:
+            with pytest.raises(lb.LbfdError):
+                e.plan(*bad)
 
 
 @pytest.mark.parametrize("mode,dist", [(lb.NOISE_GLOBAL, lb.UNIFORM), (lb.NOISE_OFF, lb.GAUSSIAN)])

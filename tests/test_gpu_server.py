@@ -75,13 +75,17 @@ def _mixed_specs(precision):
     return specs
 
 
-@pytest.mark.parametrize("precision,solo", [(lb.F32, 0), (lb.F32, 400), (lb.F64, 400), (lb.F32_F16, 0),
-                                            (lb.F32_F16, 1000)])
-def test_served_results_bit_identical_to_alone(precision, solo):
+@pytest.mark.parametrize("precision,solo,walk,vx_max", [
+    (lb.F32, 0, lb.WALK_STRIDED, 2), (lb.F32, 400, lb.WALK_STRIDED, 2), (lb.F64, 400, lb.WALK_CONTIGUOUS, 2),
+    (lb.F32_F16, 0, lb.WALK_CONTIGUOUS, 1), (lb.F32_F16, 1000, lb.WALK_STRIDED, 2), (lb.F32, 0, lb.WALK_CONTIGUOUS, 1),
+    (lb.F32, 0, lb.WALK_CONTIGUOUS, 2)])
+def test_served_results_bit_identical_to_alone(precision, solo, walk, vx_max):
     """solo: simulations of at least this many sites take their own
-    single-lattice launch each step (0: all batched)."""
+    single-lattice launch each step (0: all batched); walk and vx_max: tile
+    order and sites per item of the batched launch."""
     specs = _mixed_specs(precision)
-    with lb.Server(precision=precision, hbm_budget=256 << 20, max_ahead=3, solo_sites=solo) as srv:
+    with lb.Server(precision=precision, hbm_budget=256 << 20, max_ahead=3, solo_sites=solo, walk=walk,
+                   vx_max=vx_max) as srv:
         ids = [_submit(srv, sp) for sp in specs[:5]]
         srv.pump(6)                      # the first wave runs ...
         ids += [_submit(srv, sp) for sp in specs[5:9]]   # ... while the second arrives
