@@ -246,6 +246,8 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+# tile orders of the batched kernel, in the order of the library's LBFD_WALK_* values
+WALKS = ["strided", "contiguous", "per_tile"]
 ENS_LATTICES = {"d1q3": (0, 1, (256, 65536)), "d2q9": (1, 2, (32, 512)), "d3q19": (2, 3, (32, 128))}
 
 
@@ -317,7 +319,7 @@ def run_ensemble(args):
                                f"[{lo}, {hi}], rho_mean U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian "
                                f"noise",
                    "sites": sites, "sites_per_item_max": vx, "tile_passes": passes, "blocks_per_sm": bps,
-                   "tile_walk": "contiguous" if walk == lb.WALK_CONTIGUOUS else "strided", "graph_steps": 16,
+                   "tile_walk": WALKS[walk], "graph_steps": 16,
                    "l2": "inputs larger than L2: %.0f MB per population buffer" % (4.0 * Q * sites / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "algorithmic_bytes_per_launch": 8 * Q * sites, "kernel": "k_batch_step",
@@ -358,7 +360,7 @@ def run_served(args):
     srv = lb.Server(hbm_budget=int(args.budget_gb * (1 << 30)), max_active=4096, max_ahead=4, passes=args.passes,
                     policy=policy, max_active_sites=args.max_active_sites, occupancy=args.occupancy,
                     solo_sites=args.solo_sites,
-                    walk=lb.WALK_CONTIGUOUS if args.walk == "contiguous" else lb.WALK_STRIDED, vx_max=args.vx_max)
+                    walk=WALKS.index(args.walk), vx_max=args.vx_max)
     # warm-up: a short trace of small requests (module load, first launches)
     warm = [abi.make_request(k % 3, [(512,), (64, 64), (16, 16, 16)][k % 3], 1.0, 10.0, 99 + k, 20,
                              result=lb.RESULT_RHO) for k in range(max(3, args.warmup))]
@@ -445,7 +447,7 @@ def main():
     ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
-    ap.add_argument("--walk", default="strided", choices=["strided", "contiguous"])
+    ap.add_argument("--walk", default="strided", choices=WALKS)
     ap.add_argument("--vx-max", type=int, default=2, choices=[1, 2])
     ap.add_argument("--solo-sites", type=int, default=1 << 17)
     ap.add_argument("--max-active-sites", type=int, default=20_000_000)

@@ -277,7 +277,7 @@ int lbfd_ensemble_sync(lbfd_ens_t e);
 
 /* Times the candidate work decompositions (at most 1 or 2 sites per item,
  * times tiles of 1, 2, 4 or 8 passes, times two register/occupancy variants
- * of the kernel, times the two tile orders LBFD_WALK_*) over `steps`
+ * of the kernel, times the three tile orders LBFD_WALK_*) over `steps`
  * launches each that write only the spare buffers, keeps the fastest and
  * reports it: sites per item at most, passes, resident blocks per SM (any
  * output may be NULL; lbfd_ensemble_query also gives the tile order).  The
@@ -330,8 +330,12 @@ int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
 
 #define LBFD_POLICY_FIFO 0      /* admit in arrival order (later requests may pass one that does not fit) */
 #define LBFD_POLICY_SHORTEST 1  /* admit the request with the fewest site updates (sites x steps) first */
+/* Tile order of the batched kernel: a persistent grid whose blocks take every
+ * grid-th tile (STRIDED) or one run of consecutive tiles (CONTIGUOUS), or one
+ * block per tile (PER_TILE).  Results do not depend on it. */
 #define LBFD_WALK_STRIDED 0
 #define LBFD_WALK_CONTIGUOUS 1
+#define LBFD_WALK_PER_TILE 2
 
 #define LBFD_REQ_UNKNOWN (-1)
 #define LBFD_REQ_QUEUED 0
@@ -350,8 +354,7 @@ typedef struct lbfd_server_options {
     int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
     int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
     int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
-    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_STRIDED (a block takes every
-                               grid-th tile) or LBFD_WALK_CONTIGUOUS (one run of consecutive tiles) */
+    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_* */
     int32_t vx_max;         /* sites per work item of the batched kernel at most: 2 (members with even Lx
                                take two) or 1 (a kernel without the two-site path, fewer registers) */
     int32_t reserved[5];

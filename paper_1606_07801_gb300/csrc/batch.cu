@@ -69,11 +69,11 @@ cudaError_t launch_batch_step(int lattice, int precision, void *base, const Batc
   return cudaErrorInvalidValue;
 }
 
-int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int noise_mode, int noise_dist) {
+int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist) {
   switch (lattice) {
-    case kD1Q3: return batch_blocks_per_sm_d1q3(precision, occ, vx_max, noise_mode, noise_dist);
-    case kD2Q9: return batch_blocks_per_sm_d2q9(precision, occ, vx_max, noise_mode, noise_dist);
-    case kD3Q19: return batch_blocks_per_sm_d3q19(precision, occ, vx_max, noise_mode, noise_dist);
+    case kD1Q3: return batch_blocks_per_sm_d1q3(precision, occ, vx_max, walk, noise_mode, noise_dist);
+    case kD2Q9: return batch_blocks_per_sm_d2q9(precision, occ, vx_max, walk, noise_mode, noise_dist);
+    case kD3Q19: return batch_blocks_per_sm_d3q19(precision, occ, vx_max, walk, noise_mode, noise_dist);
   }
   return 1;
 }

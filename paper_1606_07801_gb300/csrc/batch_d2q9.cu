@@ -15,11 +15,11 @@ cudaError_t launch_batch_step_d2q9(int precision, void *base, const BatchStep *s
   });
 }
 
-int batch_blocks_per_sm_d2q9(int precision, int occ, int vx_max, int noise_mode, int noise_dist) {
+int batch_blocks_per_sm_d2q9(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist) {
   int nb = 1;
   dispatch_storage(precision, [&](auto tag) {
     using S = typename decltype(tag)::type;
-    nb = batch_blocks_per_sm<kD2Q9, S>(occ, vx_max, noise_mode, noise_dist);
+    nb = batch_blocks_per_sm<kD2Q9, S>(occ, vx_max, walk, noise_mode, noise_dist);
     return cudaSuccess;
   });
   return nb;

@@ -26,8 +26,10 @@
 namespace lbfd {
 
 constexpr int kBatchThreads = 256;
-// Order in which a block of the persistent grid takes its tiles.
-constexpr int kWalkStrided = 0, kWalkContiguous = 1;
+// Order in which blocks take tiles: a persistent grid whose blocks take every
+// grid-th tile (strided) or one run of consecutive tiles (contiguous), or one
+// block per tile.
+constexpr int kWalkStrided = 0, kWalkContiguous = 1, kWalkPerBlock = 2;
 
 // One member, as the host builds it (constant while the member is listed).
 struct BatchMember {
@@ -84,16 +86,57 @@ constexpr int batch_min_blocks() {
   return OCC == 0 ? step_min_blocks<LAT, S>() : (step_min_blocks<LAT, S>() > 1 ? step_min_blocks<LAT, S>() - 1 : 1);
 }
 
-// VXMAX = 1: every member takes one site per item (the two-site path, with
-// its larger register footprint, is not compiled in); VXMAX = 2: members
-// with even Lx take two.
+// The work items of one tile of member b (rel: the tile's index within the
+// member).  VXMAX = 1: every member takes one site per item (the two-site
+// path, with its larger register footprint, is not compiled in); VXMAX = 2:
+// members with even Lx take two.
+template <int LAT, typename S, int NOISE, int VXMAX>
+__device__ __forceinline__ void batch_tile_items(S *__restrict__ base, const BatchStep &b, int rel, int passes) {
+  const S *src = base + b.src;
+  S *dst = base + b.dst;
+  const int first = rel * passes * kBatchThreads + threadIdx.x;
+  for (int p = 0; p < passes; ++p) {
+    const int item = first + p * kBatchThreads;
+    if (item < b.items) {
+      const int row = static_cast<int>(fastdiv(static_cast<uint32_t>(item), b.div_cols));
+      const int col = item - row * b.cols;
+      const int z = static_cast<int>(fastdiv(static_cast<uint32_t>(row), b.div_Ly));
+      const int y = row - z * b.a.Ly;
+      // a member's value offsets fit 32 bits (checked when it is listed)
+      using C = SrtCollide<LAT, typename Store<S>::R, NOISE>;
+      if (VXMAX == 2 && b.vx == 2)
+        step_vec_body<LAT, S, 2, NOISE, C, uint32_t>(src, dst, b.a, col * 2, y, z);
+      else
+        step_scalar_body<LAT, S, NOISE, C, uint32_t>(src, dst, b.a, col, y, z);
+    }
+  }
+}
+
+// Warp 0 finds the member of `tile`, copies its arguments to *sb and its
+// first tile to *lo (and the end of its tiles to *hi when hi is not null).
+__device__ __forceinline__ void batch_load_member(const BatchStep *__restrict__ steps,
+                                                  const int64_t *__restrict__ tile_start, int nmembers, int ntiles,
+                                                  int tile, BatchStep *sb, int *lo, int *hi) {
+  if (threadIdx.x < 32) {
+    const int m = batch_find_member(tile_start, nmembers, tile);
+    const int4 *g = reinterpret_cast<const int4 *>(steps + m);
+    int4 *s = reinterpret_cast<int4 *>(sb);
+    for (int k = threadIdx.x; k < int(sizeof(BatchStep) / 16); k += 32) s[k] = g[k];
+    if (threadIdx.x == 0) {
+      *lo = static_cast<int>(__ldg(tile_start + m));
+      if (hi) *hi = m + 1 < nmembers ? static_cast<int>(__ldg(tile_start + m + 1)) : ntiles;
+    }
+  }
+}
+
+// Persistent grid: the tiles of this block are every gridDim.x-th tile from
+// blockIdx.x (strided walk) or one run of consecutive tiles (contiguous
+// walk), in which the member changes only where the run crosses a member
+// boundary.
 template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>())
     k_batch_step(S *__restrict__ base, const BatchStep *__restrict__ steps, const int64_t *__restrict__ tile_start,
                  int nmembers, int ntiles, int passes, int walk) {
-  // Tiles of this block: every gridDim.x-th tile from blockIdx.x (strided
-  // walk), or one run of consecutive tiles (contiguous walk), in which the
-  // member changes only where the run crosses a member boundary.
   int tile, stop, stride;
   if (walk == kWalkContiguous) {
     tile = static_cast<int>(int64_t(blockIdx.x) * ntiles / gridDim.x);
@@ -113,55 +156,52 @@ __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>()
   for (; tile < stop; tile += stride) {
     if (tile < lo || tile >= hi) {
       buf ^= 1;
-      if (threadIdx.x < 32) {
-        const int m = batch_find_member(tile_start, nmembers, tile);
-        const int4 *g = reinterpret_cast<const int4 *>(steps + m);
-        int4 *s = reinterpret_cast<int4 *>(&sb[buf]);
-        for (int k = threadIdx.x; k < int(sizeof(BatchStep) / 16); k += 32) s[k] = g[k];
-        if (threadIdx.x == 0) {
-          srange[buf][0] = static_cast<int>(__ldg(tile_start + m));
-          srange[buf][1] = m + 1 < nmembers ? static_cast<int>(__ldg(tile_start + m + 1)) : ntiles;
-        }
-      }
+      batch_load_member(steps, tile_start, nmembers, ntiles, tile, &sb[buf], &srange[buf][0], &srange[buf][1]);
       __syncthreads();
       lo = srange[buf][0];
       hi = srange[buf][1];
     }
-    const BatchStep &b = sb[buf];
-    const S *src = base + b.src;
-    S *dst = base + b.dst;
-    const int first = (tile - lo) * passes * kBatchThreads + threadIdx.x;
-    for (int p = 0; p < passes; ++p) {
-      const int item = first + p * kBatchThreads;
-      if (item < b.items) {
-        const int row = static_cast<int>(fastdiv(static_cast<uint32_t>(item), b.div_cols));
-        const int col = item - row * b.cols;
-        const int z = static_cast<int>(fastdiv(static_cast<uint32_t>(row), b.div_Ly));
-        const int y = row - z * b.a.Ly;
-        // a member's value offsets fit 32 bits (checked when it is listed)
-        using C = SrtCollide<LAT, typename Store<S>::R, NOISE>;
-        if (VXMAX == 2 && b.vx == 2)
-          step_vec_body<LAT, S, 2, NOISE, C, uint32_t>(src, dst, b.a, col * 2, y, z);
-        else
-          step_scalar_body<LAT, S, NOISE, C, uint32_t>(src, dst, b.a, col, y, z);
-      }
-    }
+    batch_tile_items<LAT, S, NOISE, VXMAX>(base, sb[buf], tile - lo, passes);
   }
+}
+
+// One tile per block (grid = number of tiles): no loop state is carried
+// across tiles, which leaves the per-site code the registers it has in the
+// single-lattice kernels.
+template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
+__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>())
+    k_batch_tile(S *__restrict__ base, const BatchStep *__restrict__ steps, const int64_t *__restrict__ tile_start,
+                 int nmembers, int ntiles, int passes) {
+  __shared__ BatchStep sb;
+  __shared__ int lo;
+  batch_load_member(steps, tile_start, nmembers, ntiles, static_cast<int>(blockIdx.x), &sb, &lo, nullptr);
+  __syncthreads();
+  batch_tile_items<LAT, S, NOISE, VXMAX>(base, sb, static_cast<int>(blockIdx.x) - lo, passes);
+}
+
+template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
+cudaError_t batch_step_k(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int ntiles, int passes,
+                         int walk, int grid, cudaStream_t stream) {
+  if (walk == kWalkPerBlock)
+    k_batch_tile<LAT, S, NOISE, OCC, VXMAX><<<ntiles, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
+                                                                                  passes);
+  else
+    k_batch_step<LAT, S, NOISE, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
+                                                                                passes, walk);
+  return cudaGetLastError();
 }
 
 template <int LAT, typename S, int OCC, int VXMAX>
 cudaError_t batch_step_occ(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int ntiles,
                            int passes, int walk, int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
   if (noise_mode == kNoiseOff)
-    k_batch_step<LAT, S, kStepNoiseOff, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
-                                                                                        ntiles, passes, walk);
-  else if (noise_dist == kGaussian)
-    k_batch_step<LAT, S, kStepNoiseGauss, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start,
-                                                                                          nmembers, ntiles, passes, walk);
-  else
-    k_batch_step<LAT, S, kStepNoiseFlat, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
-                                                                                         ntiles, passes, walk);
-  return cudaGetLastError();
+    return batch_step_k<LAT, S, kStepNoiseOff, OCC, VXMAX>(b, steps, tile_start, nmembers, ntiles, passes, walk, grid,
+                                                           stream);
+  if (noise_dist == kGaussian)
+    return batch_step_k<LAT, S, kStepNoiseGauss, OCC, VXMAX>(b, steps, tile_start, nmembers, ntiles, passes, walk, grid,
+                                                             stream);
+  return batch_step_k<LAT, S, kStepNoiseFlat, OCC, VXMAX>(b, steps, tile_start, nmembers, ntiles, passes, walk, grid,
+                                                          stream);
 }
 
 // vx_max: the largest sites per item of any member (1 or 2).
@@ -186,30 +226,31 @@ cudaError_t batch_step_t(void *base, const BatchStep *steps, const int64_t *tile
                                       stream);
 }
 
-template <int LAT, typename S, int OCC, int VXMAX>
-int batch_blocks_occ(int noise_mode, int noise_dist) {
+template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
+int batch_blocks_k(int walk) {
   int nb = 0;
-  cudaError_t e;
-  if (noise_mode == kNoiseOff)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseOff, OCC, VXMAX>,
-                                                      kBatchThreads, 0);
-  else if (noise_dist == kGaussian)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseGauss, OCC, VXMAX>,
-                                                      kBatchThreads, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, kStepNoiseFlat, OCC, VXMAX>,
-                                                      kBatchThreads, 0);
+  const cudaError_t e =
+      walk == kWalkPerBlock
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_tile<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0);
   return e == cudaSuccess && nb > 0 ? nb : 1;
+}
+
+template <int LAT, typename S, int OCC, int VXMAX>
+int batch_blocks_occ(int walk, int noise_mode, int noise_dist) {
+  if (noise_mode == kNoiseOff) return batch_blocks_k<LAT, S, kStepNoiseOff, OCC, VXMAX>(walk);
+  if (noise_dist == kGaussian) return batch_blocks_k<LAT, S, kStepNoiseGauss, OCC, VXMAX>(walk);
+  return batch_blocks_k<LAT, S, kStepNoiseFlat, OCC, VXMAX>(walk);
 }
 
 // Resident blocks per SM of the batch kernel (sizes the persistent grid).
 template <int LAT, typename S>
-int batch_blocks_per_sm(int occ, int vx_max, int noise_mode, int noise_dist) {
+int batch_blocks_per_sm(int occ, int vx_max, int walk, int noise_mode, int noise_dist) {
   if (vx_max == 1)
-    return occ == 1 ? batch_blocks_occ<LAT, S, 1, 1>(noise_mode, noise_dist)
-                    : batch_blocks_occ<LAT, S, 0, 1>(noise_mode, noise_dist);
-  return occ == 1 ? batch_blocks_occ<LAT, S, 1, 2>(noise_mode, noise_dist)
-                  : batch_blocks_occ<LAT, S, 0, 2>(noise_mode, noise_dist);
+    return occ == 1 ? batch_blocks_occ<LAT, S, 1, 1>(walk, noise_mode, noise_dist)
+                    : batch_blocks_occ<LAT, S, 0, 1>(walk, noise_mode, noise_dist);
+  return occ == 1 ? batch_blocks_occ<LAT, S, 1, 2>(walk, noise_mode, noise_dist)
+                  : batch_blocks_occ<LAT, S, 0, 2>(walk, noise_mode, noise_dist);
 }
 
 }  // namespace lbfd

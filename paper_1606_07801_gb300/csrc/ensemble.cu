@@ -99,7 +99,7 @@ static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ, int walk) {
   e->passes = passes;
   e->occ = occ;
   e->walk = walk;
-  e->bps = batch_blocks_per_sm(e->lattice, e->precision, occ, e->kvx, e->noise_mode, e->noise_dist);
+  e->bps = batch_blocks_per_sm(e->lattice, e->precision, occ, e->kvx, walk, e->noise_mode, e->noise_dist);
   int sms = 0;
   ENS_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
   e->grid = int(std::max<int64_t>(1, std::min<int64_t>(e->ntiles, int64_t(sms) * e->bps)));
@@ -315,7 +315,7 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
   ENS_CU(cudaEventCreate(&b));
   // timing launches read the state and write the spare block only (t is not advanced)
   int64_t launched = 0;
-  for (int walk = 0; walk < 2; ++walk) {
+  for (int walk = 0; walk < 3; ++walk) {
     for (int occ = 0; occ < 2; ++occ) {
       for (int vx : vx_cand) {
         for (int passes : pass_cand) {
@@ -354,7 +354,8 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
 
 int lbfd_ensemble_plan(lbfd_ens_t e, int32_t vx_max, int32_t passes, int32_t occupancy, int32_t walk) {
   if (!e || (vx_max != 1 && vx_max != 2) || (passes != 1 && passes != 2 && passes != 4 && passes != 8) ||
-      (occupancy != 0 && occupancy != 1) || (walk != LBFD_WALK_STRIDED && walk != LBFD_WALK_CONTIGUOUS))
+      (occupancy != 0 && occupancy != 1) ||
+      (walk != LBFD_WALK_STRIDED && walk != LBFD_WALK_CONTIGUOUS && walk != LBFD_WALK_PER_TILE))
     return ens_fail(LBFD_EINVAL, "lbfd_ensemble_plan: bad argument");
   DevGuard g(e->device);
   ENS_CU(ens_sync_t(e));

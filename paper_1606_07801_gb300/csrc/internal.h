@@ -175,18 +175,19 @@ cudaError_t launch_batch_step_d2q9(int precision, void *base, const BatchStep *s
 cudaError_t launch_batch_step_d3q19(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
                                     int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
                                     cudaStream_t stream);
-int batch_blocks_per_sm_d1q3(int precision, int occ, int vx_max, int noise_mode, int noise_dist);
-int batch_blocks_per_sm_d2q9(int precision, int occ, int vx_max, int noise_mode, int noise_dist);
-int batch_blocks_per_sm_d3q19(int precision, int occ, int vx_max, int noise_mode, int noise_dist);
+int batch_blocks_per_sm_d1q3(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
+int batch_blocks_per_sm_d2q9(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
+int batch_blocks_per_sm_d3q19(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
 
 // batch.cu: lattice dispatch of the above, the per-launch argument kernel
-// and the tile assignment.  walk: 0 = a block takes every grid-th tile,
-// 1 = a block takes one run of consecutive tiles; vx_max: the largest sites
+// and the tile assignment.  walk: 0 = a block of the persistent grid takes
+// every grid-th tile, 1 = one run of consecutive tiles, 2 = one block per
+// tile (grid ignored); vx_max: the largest sites
 // per item of any member (1 selects a kernel without the two-site path).
 cudaError_t launch_batch_step(int lattice, int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
                               int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
                               cudaStream_t stream);
-int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int noise_mode, int noise_dist);
+int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
 // Step arguments of members[0..n) for the clock *clock_dev (clock when null).
 cudaError_t launch_batch_prep(const BatchMember *members, int n, const uint64_t *clock_dev, uint64_t clock,
                               int noise_mode, int noise_dist, BatchStep *out, cudaStream_t stream);

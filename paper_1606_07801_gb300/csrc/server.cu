@@ -620,8 +620,8 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST) return srv_fail(LBFD_EINVAL, "server: unknown policy");
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.vx_max != 1 && o.vx_max != 2) return srv_fail(LBFD_EINVAL, "server: vx_max must be 1 or 2");
-  if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS)
-    return srv_fail(LBFD_EINVAL, "server: walk must be LBFD_WALK_STRIDED or LBFD_WALK_CONTIGUOUS");
+  if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS && o.walk != LBFD_WALK_PER_TILE)
+    return srv_fail(LBFD_EINVAL, "server: walk must be one of LBFD_WALK_*");
   if (o.max_active_sites < 0) return srv_fail(LBFD_EINVAL, "server: max_active_sites must be >= 0");
   if (o.solo_sites < 0) return srv_fail(LBFD_EINVAL, "server: solo_sites must be >= 0");
   int dev = o.device;
@@ -667,7 +667,7 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   }
   for (int L = 0; L < 3; ++L)
     for (int vx = 1; vx <= 2; ++vx)
-      s->bps[L][vx - 1] = batch_blocks_per_sm(L, o.precision, o.occupancy, vx, o.noise_mode, o.noise_dist);
+      s->bps[L][vx - 1] = batch_blocks_per_sm(L, o.precision, o.occupancy, vx, o.walk, o.noise_mode, o.noise_dist);
   s->largest_free = s->pool->largest_free();
   *out = s;
   return LBFD_OK;
