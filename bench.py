@@ -55,27 +55,32 @@ DTYPE_NAME = {0: "f32", 1: "f64", 2: "f32 (f16 storage)", 3: "f32 (bf16 storage)
 Q_OF = {0: 3, 1: 9, 2: 19}
 KERNEL_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_07801_gb300/csrc/device.cuh",
                   "paper_1606_07801_gb300/csrc/step_d2q9.cu", "paper_1606_07801_gb300/csrc/step_d3q19.cu"]
+# sources of the batched kernel (k_batch_tile / k_batch_step)
+BATCH_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_07801_gb300/csrc/device.cuh",
+                 "paper_1606_07801_gb300/csrc/batch_kernels.cuh", "paper_1606_07801_gb300/csrc/fastdiv.cuh",
+                 "paper_1606_07801_gb300/csrc/batch_d2q9.cu", "paper_1606_07801_gb300/csrc/batch_d3q19.cu"]
 
 
-def kernel_hash() -> str:
+def kernel_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources:
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled(workload: str, key: str):
-    """A figure of the committed ncu summary of k_step on this workload
-    (traffic_bytes_per_launch, instructions_per_site), or None if there is
-    none or the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"k_step_{workload}.md")
+def profiled(workload: str, key: str, name: str = "", sources=KERNEL_SOURCES):
+    """A figure of a committed ncu summary (profiles/k_step_<workload>.md, or
+    profiles/<name>.md) such as traffic_bytes_per_launch or
+    instructions_per_site, or None if there is none or the kernel sources
+    changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", (name or f"k_step_{workload}") + ".md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_hash = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
     m_val = re.search(key + r":\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_val or m_hash.group(1) != kernel_hash():
+    if not m_hash or not m_val or m_hash.group(1) != kernel_hash(sources):
         return None
     return float(m_val.group(1))
 
@@ -274,8 +279,13 @@ def run_ensemble(args):
     stream = torch.cuda.Stream()
     ens = lb.Ensemble(lat, specs, stream=stream)
     n, sites = ens.query()[:2]
-    vx, passes, bps = ens.tune(steps=3)
-    walk = ens.query()[6]
+    if args.plan:
+        # a fixed decomposition (sites per item, passes, occupancy variant, tile order) instead of the tuner's
+        pv, pp, po, pw = args.plan.split(",")
+        ens.plan(int(pv), int(pp), int(po), WALKS.index(pw))
+    else:
+        ens.tune(steps=3)
+    _, _, _, vx, passes, bps, walk = ens.query()
     ens.step(args.warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -311,6 +321,11 @@ def run_ensemble(args):
         s_.close()
     peak, peak_kind = measured_peaks()
     achieved = 8.0 * Q * sites / (ms / args.steps * 1e-3) / 1e9
+    kname = "k_batch_tile" if WALKS[walk] == "per_tile" else "k_batch_step"
+    # DRAM bytes per site of one launch from the committed ncu capture (same kernel sources), scaled to this ensemble
+    per_site = profiled(args.ens_lattice, f"traffic_bytes_per_site_{args.ens_lattice}", "k_batch_tile_ensemble",
+                        BATCH_SOURCES) if kname == "k_batch_tile" else None
+    traffic = None if per_site is None else per_site * sites
     line = {
         "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -319,10 +334,11 @@ def run_ensemble(args):
                                f"[{lo}, {hi}], rho_mean U[0.5, 200], tau U[0.6, 1.5], distinct seeds, local Gaussian "
                                f"noise",
                    "sites": sites, "sites_per_item_max": vx, "tile_passes": passes, "blocks_per_sm": bps,
-                   "tile_walk": WALKS[walk], "graph_steps": 16,
+                   "tile_walk": WALKS[walk], "decomposition": args.plan or "tuned",
+                   "graph_steps": 16,
                    "l2": "inputs larger than L2: %.0f MB per population buffer" % (4.0 * Q * sites / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": 8 * Q * sites, "kernel": "k_batch_step",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": 8 * Q * sites, "kernel": kname,
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "per_sim_baseline": {"value": per_sim, "unit": UNIT, "sims": len(sub), "steps": args.per_sim_steps,
                              "how": "one lbfd handle and one k_step launch per simulation per step, same stream"},
@@ -438,6 +454,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=int, default=4096)
+    ap.add_argument("--plan", default="", help="ensemble decomposition vx,passes,occupancy,walk (default: tuned)")
     ap.add_argument("--ens-lattice", default="d2q9", choices=sorted(ENS_LATTICES))
     ap.add_argument("--per-sim-members", type=int, default=256)
     ap.add_argument("--per-sim-steps", type=int, default=20)
