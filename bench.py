@@ -464,7 +464,7 @@ def main():
     ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
-    ap.add_argument("--walk", default="strided", choices=WALKS)
+    ap.add_argument("--walk", default="per_tile", choices=WALKS)
     ap.add_argument("--vx-max", type=int, default=2, choices=[1, 2])
     ap.add_argument("--solo-sites", type=int, default=1 << 17)
     ap.add_argument("--max-active-sites", type=int, default=20_000_000)

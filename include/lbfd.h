@@ -265,7 +265,9 @@ typedef struct lbfd_ens *lbfd_ens_t;
 /* Creates an ensemble of n members on the current device (all populations in
  * two device buffers allocated here).  stream: a cudaStream_t other than the
  * legacy default stream (graphs are captured on it); NULL makes the ensemble
- * create and own a non-blocking stream. */
+ * create and own a non-blocking stream.  The initial decomposition is two
+ * sites per item where Lx is even, 4 passes, occupancy variant 0, one block
+ * per tile (lbfd_ensemble_tune / lbfd_ensemble_plan change it). */
 int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, int32_t noise_mode, int32_t noise_dist,
                          const lbfd_member *members, int32_t n, void *stream);
 int lbfd_ensemble_destroy(lbfd_ens_t e);
@@ -395,8 +397,8 @@ typedef struct lbfd_server_stats {
 typedef struct lbfd_server *lbfd_server_t;
 
 /* Defaults: FP32, local Gaussian noise, current device, 1 GiB budget, no
- * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO, occupancy 0, strided
- * walk, vx_max 2, solo_sites 2^17. */
+ * site limit, 1024 slots, 4 steps ahead, 1 pass, FIFO, occupancy 0, one
+ * block per tile (LBFD_WALK_PER_TILE), vx_max 2, solo_sites 2^17. */
 int lbfd_server_options_init(lbfd_server_options *opt);
 
 /* Creates a server: one device arena of hbm_budget bytes, two streams

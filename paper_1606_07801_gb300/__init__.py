@@ -190,7 +190,7 @@ class Ensemble:
         """Picks the fastest work decomposition; returns (vx, passes, blocks per SM)."""
         return abi.lbfd_ensemble_tune(self.h, steps)
 
-    def plan(self, vx_max: int, passes: int, occupancy: int = 0, walk: int = WALK_STRIDED) -> None:
+    def plan(self, vx_max: int, passes: int, occupancy: int = 0, walk: int = WALK_PER_TILE) -> None:
         """Sets the work decomposition without timing (results do not depend on it)."""
         abi.lbfd_ensemble_plan(self.h, vx_max, passes, occupancy, walk)
 
@@ -216,7 +216,7 @@ class Server:
     def __init__(self, *, precision: int = F32, noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN,
                  hbm_budget: int = 1 << 30, max_active: int = 1024, max_ahead: int = 4, passes: int = 1,
                  policy: int = POLICY_FIFO, max_active_sites: int = 0, occupancy: int = 0,
-                 solo_sites: int = 1 << 17, walk: int = 0, vx_max: int = 2, device: int = -1):
+                 solo_sites: int = 1 << 17, walk: int = WALK_PER_TILE, vx_max: int = 2, device: int = -1):
         o = abi.lbfd_server_options_init()
         o.precision, o.noise_mode, o.noise_dist, o.device = precision, noise_mode, noise_dist, device
         o.hbm_budget, o.max_active, o.max_ahead, o.passes = int(hbm_budget), max_active, max_ahead, passes

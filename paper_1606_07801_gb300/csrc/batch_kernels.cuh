@@ -29,7 +29,7 @@ constexpr int kBatchThreads = 256;
 // Order in which blocks take tiles: a persistent grid whose blocks take every
 // grid-th tile (strided) or one run of consecutive tiles (contiguous), or one
 // block per tile.
-constexpr int kWalkStrided = 0, kWalkContiguous = 1, kWalkPerBlock = 2;
+constexpr int kWalkStrided = 0, kWalkContiguous = 1, kWalkPerTile = 2;
 
 // One member, as the host builds it (constant while the member is listed).
 struct BatchMember {
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>()
 template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 cudaError_t batch_step_k(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int ntiles, int passes,
                          int walk, int grid, cudaStream_t stream) {
-  if (walk == kWalkPerBlock)
+  if (walk == kWalkPerTile)
     k_batch_tile<LAT, S, NOISE, OCC, VXMAX><<<ntiles, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
                                                                                   passes);
   else
@@ -230,7 +230,7 @@ template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 int batch_blocks_k(int walk) {
   int nb = 0;
   const cudaError_t e =
-      walk == kWalkPerBlock
+      walk == kWalkPerTile
           ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_tile<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0)
           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0);
   return e == cudaSuccess && nb > 0 ? nb : 1;

@@ -248,7 +248,7 @@ int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, in
     ens_free(e);
     return rc;
   }
-  int rc = ens_plan(e, 2, 1, 0, kWalkStrided);
+  int rc = ens_plan(e, 2, 4, 0, kWalkPerTile);
   if (rc) {
     ens_free(e);
     return rc;

@@ -597,7 +597,7 @@ int lbfd_server_options_init(lbfd_server_options *opt) {
   opt->max_ahead = 4;
   opt->passes = 1;
   opt->policy = LBFD_POLICY_FIFO;
-  opt->walk = LBFD_WALK_STRIDED;
+  opt->walk = LBFD_WALK_PER_TILE;
   opt->vx_max = 2;
   opt->solo_sites = int64_t(1) << 17;
   return LBFD_OK;

@@ -99,7 +99,7 @@ def test_server_option_defaults_and_checks():
     o = abi.lbfd_server_options_init()
     assert (o.precision, o.noise_mode, o.noise_dist, o.device) == (lb.F32, lb.NOISE_LOCAL, lb.GAUSSIAN, -1)
     assert (o.hbm_budget, o.max_active, o.max_ahead, o.passes, o.policy) == (1 << 30, 1024, 4, 1, lb.POLICY_FIFO)
-    assert o.solo_sites == 1 << 17 and o.occupancy == 0 and o.walk == lb.WALK_STRIDED and o.vx_max == 2
+    assert o.solo_sites == 1 << 17 and o.occupancy == 0 and o.walk == lb.WALK_PER_TILE and o.vx_max == 2
     lib = abi.load()
     h = ctypes.c_void_p()
     for field, bad in [("passes", 3), ("max_active", 0), ("max_ahead", 0), ("policy", 7), ("precision", 9),
