@@ -252,7 +252,7 @@ def run_reference(args, wl):
 
 
 # tile orders of the batched kernel, in the order of the library's LBFD_WALK_* values
-WALKS = ["strided", "contiguous", "per_tile"]
+WALKS = ["strided", "contiguous", "per_tile", "param"]
 ENS_LATTICES = {"d1q3": (0, 1, (256, 65536)), "d2q9": (1, 2, (32, 512)), "d3q19": (2, 3, (32, 128))}
 
 

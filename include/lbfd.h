@@ -279,7 +279,7 @@ int lbfd_ensemble_sync(lbfd_ens_t e);
 
 /* Times the candidate work decompositions (at most 1 or 2 sites per item,
  * times tiles of 1, 2, 4 or 8 passes, times two register/occupancy variants
- * of the kernel, times the three tile orders LBFD_WALK_*) over `steps`
+ * of the kernel, times the four tile orders LBFD_WALK_*) over `steps`
  * launches each that write only the spare buffers, keeps the fastest and
  * reports it: sites per item at most, passes, resident blocks per SM (any
  * output may be NULL; lbfd_ensemble_query also gives the tile order).  The
@@ -333,11 +333,14 @@ int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
 #define LBFD_POLICY_FIFO 0      /* admit in arrival order (later requests may pass one that does not fit) */
 #define LBFD_POLICY_SHORTEST 1  /* admit the request with the fewest site updates (sites x steps) first */
 /* Tile order of the batched kernel: a persistent grid whose blocks take every
- * grid-th tile (STRIDED) or one run of consecutive tiles (CONTIGUOUS), or one
- * block per tile (PER_TILE).  Results do not depend on it. */
+ * grid-th tile (STRIDED) or one run of consecutive tiles (CONTIGUOUS); one
+ * block per tile (PER_TILE); or one block per tile with the members'
+ * arguments in the kernel parameters, one launch per group of up to 112
+ * members (PARAM).  Results do not depend on it. */
 #define LBFD_WALK_STRIDED 0
 #define LBFD_WALK_CONTIGUOUS 1
 #define LBFD_WALK_PER_TILE 2
+#define LBFD_WALK_PARAM 3
 
 #define LBFD_REQ_UNKNOWN (-1)
 #define LBFD_REQ_QUEUED 0

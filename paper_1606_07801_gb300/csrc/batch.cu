@@ -3,6 +3,9 @@
 // the ensemble and the server share.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "batch.h"
 
 namespace lbfd {
@@ -10,29 +13,8 @@ namespace lbfd {
 __global__ void k_batch_prep(const BatchMember *__restrict__ members, int n, const uint64_t *__restrict__ clock_dev,
                              uint64_t clock, int noise_mode, int noise_dist, BatchStep *__restrict__ out) {
   const uint64_t now = clock_dev ? *clock_dev : clock;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
-    const BatchMember mb = members[m];
-    BatchStep s{};
-    s.a.Lx = mb.Lx;
-    s.a.Ly = mb.Ly;
-    s.a.Lz = mb.Lz;
-    s.a.N = mb.N;
-    fill_step_params(s.a, mb.tau, mb.rho_mean);
-    s.a.noise_mode = noise_mode;
-    s.a.noise_dist = noise_dist;
-    const uint64_t t = now - mb.t0;  // the member's own step counter
-    s.a.ph = make_philox_step(mb.seed, mb.lattice_id, t);
-    const int p = static_cast<int>(t & 1);
-    s.src = mb.off[p];
-    s.dst = mb.off[p ^ 1];
-    s.tile0 = mb.tile0;
-    s.vx = mb.vx;
-    s.cols = mb.Lx / mb.vx;
-    s.items = static_cast<int32_t>(static_cast<int64_t>(s.cols) * mb.Ly * mb.Lz);
-    s.div_cols = make_fastdiv(static_cast<uint32_t>(s.cols));
-    s.div_Ly = make_fastdiv(static_cast<uint32_t>(mb.Ly));
-    out[m] = s;
-  }
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+    out[m] = batch_step_of(members[m], now, noise_mode, noise_dist);
 }
 
 __global__ void k_clock_advance(uint64_t *clock_dev) {
@@ -69,6 +51,23 @@ cudaError_t launch_batch_step(int lattice, int precision, void *base, const Batc
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_batch_param(int lattice, int precision, void *base, const BatchParams *groups, int ngroups,
+                               const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode, int noise_dist,
+                               cudaStream_t stream) {
+  switch (lattice) {
+    case kD1Q3:
+      return launch_batch_param_d1q3(precision, base, groups, ngroups, steps, passes, occ, vx_max, noise_mode,
+                                     noise_dist, stream);
+    case kD2Q9:
+      return launch_batch_param_d2q9(precision, base, groups, ngroups, steps, passes, occ, vx_max, noise_mode,
+                                     noise_dist, stream);
+    case kD3Q19:
+      return launch_batch_param_d3q19(precision, base, groups, ngroups, steps, passes, occ, vx_max, noise_mode,
+                                      noise_dist, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
 int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist) {
   switch (lattice) {
     case kD1Q3: return batch_blocks_per_sm_d1q3(precision, occ, vx_max, walk, noise_mode, noise_dist);
@@ -94,6 +93,26 @@ BatchMember make_batch_member(const int64_t dims[3], double tau, double rho_mean
   m.tau = tau;
   m.rho_mean = rho_mean;
   return m;
+}
+
+int batch_build_params(const BatchMember *members, int n, int64_t ntiles, int noise_mode, int noise_dist,
+                       std::vector<BatchParams> &groups) {
+  groups.clear();
+  for (int first = 0; first < n; first += kParamMembers) {
+    BatchParams p{};
+    p.first = first;
+    p.n = std::min(kParamMembers, n - first);
+    const int64_t base = members[first].tile0;
+    for (int k = 0; k < p.n; ++k) {
+      const BatchMember &mb = members[first + k];
+      p.tile_start[k] = static_cast<int32_t>(mb.tile0 - base);
+      p.mem[k] = batch_step_of(mb, mb.t0, noise_mode, noise_dist);
+    }
+    const int64_t end = first + p.n < n ? members[first + p.n].tile0 : ntiles;
+    p.tile_start[p.n] = static_cast<int32_t>(end - base);
+    groups.push_back(p);
+  }
+  return static_cast<int>(groups.size());
 }
 
 int64_t batch_assign_tiles(BatchMember *members, int n, int passes, int64_t *tile_start) {

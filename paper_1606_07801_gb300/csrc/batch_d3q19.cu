@@ -15,6 +15,15 @@ cudaError_t launch_batch_step_d3q19(int precision, void *base, const BatchStep *
   });
 }
 
+cudaError_t launch_batch_param_d3q19(int precision, void *base, const BatchParams *groups, int ngroups,
+                                 const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode,
+                                 int noise_dist, cudaStream_t stream) {
+  return dispatch_storage(precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    return batch_param_t<kD3Q19, S>(base, groups, ngroups, steps, passes, occ, vx_max, noise_mode, noise_dist, stream);
+  });
+}
+
 int batch_blocks_per_sm_d3q19(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist) {
   int nb = 1;
   dispatch_storage(precision, [&](auto tag) {

@@ -27,9 +27,10 @@ namespace lbfd {
 
 constexpr int kBatchThreads = 256;
 // Order in which blocks take tiles: a persistent grid whose blocks take every
-// grid-th tile (strided) or one run of consecutive tiles (contiguous), or one
-// block per tile.
-constexpr int kWalkStrided = 0, kWalkContiguous = 1, kWalkPerTile = 2;
+// grid-th tile (strided) or one run of consecutive tiles (contiguous), one
+// block per tile, or one block per tile with the members' arguments in the
+// kernel parameters (one launch per group of members).
+constexpr int kWalkStrided = 0, kWalkContiguous = 1, kWalkPerTile = 2, kWalkParam = 3;
 
 // One member, as the host builds it (constant while the member is listed).
 struct BatchMember {
@@ -53,6 +54,34 @@ struct alignas(16) BatchStep {
   FastDiv div_cols, div_Ly;  // division by cols and by Ly
 };
 static_assert(sizeof(BatchStep) % 16 == 0, "BatchStep is copied as int4 words");
+
+// What one launch needs of member mb at clock value `now` (its own step
+// counter is now - t0).  Host and device share it, so the arguments a launch
+// takes from kernel parameters and the ones k_batch_prep writes agree bit for
+// bit.
+__host__ __device__ inline BatchStep batch_step_of(const BatchMember &mb, uint64_t now, int noise_mode,
+                                                   int noise_dist) {
+  BatchStep s{};
+  s.a.Lx = mb.Lx;
+  s.a.Ly = mb.Ly;
+  s.a.Lz = mb.Lz;
+  s.a.N = mb.N;
+  fill_step_params(s.a, mb.tau, mb.rho_mean);
+  s.a.noise_mode = noise_mode;
+  s.a.noise_dist = noise_dist;
+  const uint64_t t = now - mb.t0;  // the member's own step counter
+  s.a.ph = make_philox_step(mb.seed, mb.lattice_id, t);
+  const int p = static_cast<int>(t & 1);
+  s.src = mb.off[p];
+  s.dst = mb.off[p ^ 1];
+  s.tile0 = mb.tile0;
+  s.vx = mb.vx;
+  s.cols = mb.Lx / mb.vx;
+  s.items = static_cast<int32_t>(static_cast<int64_t>(s.cols) * mb.Ly * mb.Lz);
+  s.div_cols = make_fastdiv(static_cast<uint32_t>(s.cols));
+  s.div_Ly = make_fastdiv(static_cast<uint32_t>(mb.Ly));
+  return s;
+}
 
 // Step arguments of every member for the clock value *clock_dev (or `clock`
 // when clock_dev is null).
@@ -179,6 +208,81 @@ __global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>()
   batch_tile_items<LAT, S, NOISE, VXMAX>(base, sb, static_cast<int>(blockIdx.x) - lo, passes);
 }
 
+// Members of one parameter-space launch (tile order LBFD_WALK_PARAM): the
+// t-independent arguments of at most kParamMembers consecutive members travel
+// as a kernel parameter (30.9 KB of the 32 KB parameter space), so the
+// per-site code reads them as uniform operands, as the single-lattice kernels
+// read theirs.  Only the Philox words of the member's t and the parity of its
+// blocks come from the BatchStep that k_batch_prep writes for the launch.
+constexpr int kParamMembers = 112;
+struct BatchParams {
+  int32_t n, first;                      // members first .. first + n - 1 of the batch
+  int32_t tile_start[kParamMembers + 1];  // first tile of each, relative to the launch; [n] = tiles
+  BatchStep mem[kParamMembers];          // arguments at t = 0 (the t words are replaced)
+};
+static_assert(sizeof(BatchParams) + 64 <= 32764, "kernel parameters are limited to 32764 bytes");
+
+template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
+__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<LAT, S, OCC>())
+    k_batch_param(S *__restrict__ base, const __grid_constant__ BatchParams p, const BatchStep *__restrict__ steps,
+                  int passes) {
+  const int tile = static_cast<int>(blockIdx.x);
+  // the member of this block: a search of uniform (parameter) words
+  int lo = 0, hi = p.n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (p.tile_start[mid] <= tile)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  BatchStep b = p.mem[lo];
+  const BatchStep &s = steps[p.first + lo];
+  // the t words: e[j] = ((t_hi << 3) | j) ^ K1[0] = e[0] ^ j for j < 8
+  const uint32_t e0 = s.a.ph.e[0];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) b.a.ph.e[j] = e0 ^ static_cast<uint32_t>(j);
+  b.a.ph.f = s.a.ph.f;
+  b.a.ph.g = s.a.ph.g;
+  b.a.ph.q = s.a.ph.q;
+  b.src = s.src;
+  b.dst = s.dst;
+  batch_tile_items<LAT, S, NOISE, VXMAX>(base, b, tile - p.tile_start[lo], passes);
+}
+
+template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
+cudaError_t batch_param_k(S *b, const BatchParams *groups, int ngroups, const BatchStep *steps, int passes,
+                          cudaStream_t stream) {
+  for (int g = 0; g < ngroups; ++g) {
+    const int tiles = groups[g].tile_start[groups[g].n];
+    if (tiles > 0)
+      k_batch_param<LAT, S, NOISE, OCC, VXMAX><<<tiles, kBatchThreads, 0, stream>>>(b, groups[g], steps, passes);
+  }
+  return cudaGetLastError();
+}
+
+template <int LAT, typename S, int OCC, int VXMAX>
+cudaError_t batch_param_occ(S *b, const BatchParams *groups, int ngroups, const BatchStep *steps, int passes,
+                            int noise_mode, int noise_dist, cudaStream_t stream) {
+  if (noise_mode == kNoiseOff)
+    return batch_param_k<LAT, S, kStepNoiseOff, OCC, VXMAX>(b, groups, ngroups, steps, passes, stream);
+  if (noise_dist == kGaussian)
+    return batch_param_k<LAT, S, kStepNoiseGauss, OCC, VXMAX>(b, groups, ngroups, steps, passes, stream);
+  return batch_param_k<LAT, S, kStepNoiseFlat, OCC, VXMAX>(b, groups, ngroups, steps, passes, stream);
+}
+
+// One launch per group of at most kParamMembers members.
+template <int LAT, typename S>
+cudaError_t batch_param_t(void *base, const BatchParams *groups, int ngroups, const BatchStep *steps, int passes,
+                          int occ, int vx_max, int noise_mode, int noise_dist, cudaStream_t stream) {
+  S *b = static_cast<S *>(base);
+  if (vx_max == 1)
+    return occ == 1 ? batch_param_occ<LAT, S, 1, 1>(b, groups, ngroups, steps, passes, noise_mode, noise_dist, stream)
+                    : batch_param_occ<LAT, S, 0, 1>(b, groups, ngroups, steps, passes, noise_mode, noise_dist, stream);
+  return occ == 1 ? batch_param_occ<LAT, S, 1, 2>(b, groups, ngroups, steps, passes, noise_mode, noise_dist, stream)
+                  : batch_param_occ<LAT, S, 0, 2>(b, groups, ngroups, steps, passes, noise_mode, noise_dist, stream);
+}
+
 template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 cudaError_t batch_step_k(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int ntiles, int passes,
                          int walk, int grid, cudaStream_t stream) {
@@ -229,10 +333,13 @@ cudaError_t batch_step_t(void *base, const BatchStep *steps, const int64_t *tile
 template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 int batch_blocks_k(int walk) {
   int nb = 0;
-  const cudaError_t e =
-      walk == kWalkPerTile
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_tile<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0);
+  cudaError_t e;
+  if (walk == kWalkParam)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_param<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0);
+  else if (walk == kWalkPerTile)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_tile<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch_step<LAT, S, NOISE, OCC, VXMAX>, kBatchThreads, 0);
   return e == cudaSuccess && nb > 0 ? nb : 1;
 }
 

@@ -60,6 +60,7 @@ struct lbfd_ens {
   int64_t ntiles = 0;
   std::vector<BatchMember> hmem;
   std::vector<int64_t> tile_start;
+  std::vector<BatchParams> groups;  // parameter-space launches (tile order 3)
   BatchMember *dmem = nullptr;
   int64_t *dtile_start = nullptr;
   BatchStep *dsteps = nullptr;
@@ -71,6 +72,12 @@ struct lbfd_ens {
   double *partials = nullptr, *d_mass = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool owns_stream = false;
+  // side streams for the parameter-space launches: the groups of a step run
+  // concurrently (parallel branches of the captured graph), joined before the
+  // clock advances
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   // member m's block holding its stored state (which = 0) or the spare one (1)
   char *block(int m, int which) const {
     const int p = static_cast<int>(t & 1) ^ which;
@@ -78,7 +85,30 @@ struct lbfd_ens {
   }
 };
 
+// Kernel launches of one step of the batched kernel.
+static int ens_step_launches(const lbfd_ens *e) {
+  return e->walk == kWalkParam ? static_cast<int>(e->groups.size()) : 1;
+}
+
 static cudaError_t ens_launch(lbfd_ens *e) {
+  if (e->walk == kWalkParam) {
+    // groups k, k + kSide, ... on side stream k, forked from and joined to the ensemble's stream
+    const int G = static_cast<int>(e->groups.size());
+    const int nside = std::min(G, int(lbfd_ens::kSide));
+    if (nside <= 1)
+      return launch_batch_param(e->lattice, e->precision, e->buf, e->groups.data(), G, e->dsteps, e->passes, e->occ,
+                                e->kvx, e->noise_mode, e->noise_dist, e->stream);
+    cudaError_t err = cudaEventRecord(e->fork_ev, e->stream);
+    for (int k = 0; k < nside && err == cudaSuccess; ++k) {
+      err = cudaStreamWaitEvent(e->side[k], e->fork_ev, 0);
+      for (int g = k; g < G && err == cudaSuccess; g += nside)
+        err = launch_batch_param(e->lattice, e->precision, e->buf, &e->groups[g], 1, e->dsteps, e->passes, e->occ,
+                                 e->kvx, e->noise_mode, e->noise_dist, e->side[k]);
+      if (err == cudaSuccess) err = cudaEventRecord(e->join_ev[k], e->side[k]);
+      if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->join_ev[k], 0);
+    }
+    return err;
+  }
   return launch_batch_step(e->lattice, e->precision, e->buf, e->dsteps, e->dtile_start, e->n, e->ntiles, e->passes,
                            e->occ, e->walk, e->kvx, e->noise_mode, e->noise_dist, e->grid, e->stream);
 }
@@ -99,6 +129,8 @@ static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ, int walk) {
   e->passes = passes;
   e->occ = occ;
   e->walk = walk;
+  e->groups.clear();
+  if (walk == kWalkParam) batch_build_params(e->hmem.data(), e->n, e->ntiles, e->noise_mode, e->noise_dist, e->groups);
   e->bps = batch_blocks_per_sm(e->lattice, e->precision, occ, e->kvx, walk, e->noise_mode, e->noise_dist);
   int sms = 0;
   ENS_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
@@ -120,6 +152,11 @@ static void ens_free(lbfd_ens *e) {
   cudaFree(e->t_dev);
   cudaFree(e->partials);
   cudaFree(e->d_mass);
+  for (int k = 0; k < lbfd_ens::kSide; ++k) {
+    if (e->side[k]) cudaStreamDestroy(e->side[k]);
+    if (e->join_ev[k]) cudaEventDestroy(e->join_ev[k]);
+  }
+  if (e->fork_ev) cudaEventDestroy(e->fork_ev);
   if (e->owns_stream) cudaStreamDestroy(e->stream);
   delete e;
 }
@@ -225,6 +262,11 @@ int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, in
     err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
     e->owns_stream = err == cudaSuccess;
   }
+  for (int k = 0; k < lbfd_ens::kSide && err == cudaSuccess; ++k) {
+    err = cudaStreamCreateWithFlags(&e->side[k], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->join_ev[k], cudaEventDisableTiming);
+  }
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork_ev, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaMalloc(&e->buf, size_t(2 * off) * e->elem);
   if (err == cudaSuccess) err = cudaMalloc(&e->dmem, sizeof(BatchMember) * n);
   if (err == cudaSuccess) err = cudaMalloc(&e->dtile_start, sizeof(int64_t) * n);
@@ -286,7 +328,7 @@ int lbfd_ensemble_step(lbfd_ens_t e, int64_t n) {
       done += 1;
     }
   }
-  count_launches(3 * n);
+  count_launches(n * (2 + ens_step_launches(e)));
   e->t += n;
   return LBFD_OK;
 }
@@ -315,7 +357,7 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
   ENS_CU(cudaEventCreate(&b));
   // timing launches read the state and write the spare block only (t is not advanced)
   int64_t launched = 0;
-  for (int walk = 0; walk < 3; ++walk) {
+  for (int walk = 0; walk < 4; ++walk) {
     for (int occ = 0; occ < 2; ++occ) {
       for (int vx : vx_cand) {
         for (int passes : pass_cand) {
@@ -327,7 +369,7 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
           for (int k = 0; k < steps; ++k) ENS_CU(ens_launch(e));
           ENS_CU(cudaEventRecord(b, e->stream));
           ENS_CU(cudaEventSynchronize(b));
-          launched += 2 + steps;
+          launched += 1 + int64_t(1 + steps) * ens_step_launches(e);
           float ms = 0.0f;
           ENS_CU(cudaEventElapsedTime(&ms, a, b));
           if (best_ms < 0.0f || ms < best_ms) {
@@ -355,7 +397,8 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
 int lbfd_ensemble_plan(lbfd_ens_t e, int32_t vx_max, int32_t passes, int32_t occupancy, int32_t walk) {
   if (!e || (vx_max != 1 && vx_max != 2) || (passes != 1 && passes != 2 && passes != 4 && passes != 8) ||
       (occupancy != 0 && occupancy != 1) ||
-      (walk != LBFD_WALK_STRIDED && walk != LBFD_WALK_CONTIGUOUS && walk != LBFD_WALK_PER_TILE))
+      (walk != LBFD_WALK_STRIDED && walk != LBFD_WALK_CONTIGUOUS && walk != LBFD_WALK_PER_TILE &&
+       walk != LBFD_WALK_PARAM))
     return ens_fail(LBFD_EINVAL, "lbfd_ensemble_plan: bad argument");
   DevGuard g(e->device);
   ENS_CU(ens_sync_t(e));

@@ -175,6 +175,16 @@ cudaError_t launch_batch_step_d2q9(int precision, void *base, const BatchStep *s
 cudaError_t launch_batch_step_d3q19(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
                                     int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
                                     cudaStream_t stream);
+struct BatchParams;
+cudaError_t launch_batch_param_d1q3(int precision, void *base, const BatchParams *groups, int ngroups,
+                                    const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode,
+                                    int noise_dist, cudaStream_t stream);
+cudaError_t launch_batch_param_d2q9(int precision, void *base, const BatchParams *groups, int ngroups,
+                                    const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode,
+                                    int noise_dist, cudaStream_t stream);
+cudaError_t launch_batch_param_d3q19(int precision, void *base, const BatchParams *groups, int ngroups,
+                                     const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode,
+                                     int noise_dist, cudaStream_t stream);
 int batch_blocks_per_sm_d1q3(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
 int batch_blocks_per_sm_d2q9(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
 int batch_blocks_per_sm_d3q19(int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
@@ -187,6 +197,11 @@ int batch_blocks_per_sm_d3q19(int precision, int occ, int vx_max, int walk, int 
 cudaError_t launch_batch_step(int lattice, int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
                               int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
                               cudaStream_t stream);
+// One launch per group of at most kParamMembers members, their arguments in
+// the kernel parameters (tile order 3); steps holds k_batch_prep's output.
+cudaError_t launch_batch_param(int lattice, int precision, void *base, const BatchParams *groups, int ngroups,
+                               const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode, int noise_dist,
+                               cudaStream_t stream);
 int batch_blocks_per_sm(int lattice, int precision, int occ, int vx_max, int walk, int noise_mode, int noise_dist);
 // Step arguments of members[0..n) for the clock *clock_dev (clock when null).
 cudaError_t launch_batch_prep(const BatchMember *members, int n, const uint64_t *clock_dev, uint64_t clock,

@@ -55,7 +55,8 @@ def test_members_bit_identical_to_single_lattices(lat, precision):
 @pytest.mark.parametrize("vx,passes,occ,walk", [(1, 1, 0, lb.WALK_CONTIGUOUS), (2, 8, 1, lb.WALK_CONTIGUOUS),
                                                 (2, 1, 0, lb.WALK_CONTIGUOUS), (2, 2, 1, lb.WALK_STRIDED),
                                                 (1, 4, 0, lb.WALK_STRIDED), (2, 4, 0, lb.WALK_PER_TILE),
-                                                (1, 2, 1, lb.WALK_PER_TILE)])
+                                                (1, 2, 1, lb.WALK_PER_TILE), (2, 4, 0, lb.WALK_PARAM),
+                                                (1, 1, 1, lb.WALK_PARAM)])
 def test_every_decomposition_bit_identical(lat, vx, passes, occ, walk):
     """Sites per item, tile passes, occupancy variant and tile order change
     only which thread computes a site, never its value.  The members are
@@ -81,7 +82,7 @@ def test_every_decomposition_bit_identical(lat, vx, passes, occ, walk):
 def test_plan_rejects_bad_values():
     specs = _specs(lb.D2Q9, 2, seed=1)
     with lb.Ensemble(lb.D2Q9, specs) as e:
-        for bad in [(3, 1, 0, 0), (2, 3, 0, 0), (2, 1, 2, 0), (2, 1, 0, 3), (2, 1, 0, -1)]:
+        for bad in [(3, 1, 0, 0), (2, 3, 0, 0), (2, 1, 2, 0), (2, 1, 0, 4), (2, 1, 0, -1)]:
             with pytest.raises(lb.LbfdError):
                 e.plan(*bad)
 
