@@ -321,10 +321,11 @@ def run_ensemble(args):
         s_.close()
     peak, peak_kind = measured_peaks()
     achieved = 8.0 * Q * sites / (ms / args.steps * 1e-3) / 1e9
-    kname = "k_batch_tile" if WALKS[walk] == "per_tile" else "k_batch_step"
-    # DRAM bytes per site of one launch from the committed ncu capture (same kernel sources), scaled to this ensemble
-    per_site = profiled(args.ens_lattice, f"traffic_bytes_per_site_{args.ens_lattice}", "k_batch_tile_ensemble",
-                        BATCH_SOURCES) if kname == "k_batch_tile" else None
+    kname = {"per_tile": "k_batch_tile", "param": "k_batch_param"}.get(WALKS[walk], "k_batch_step")
+    # DRAM bytes per site of one launch from the committed ncu capture of this kernel (same kernel sources),
+    # scaled to this ensemble
+    per_site = profiled(args.ens_lattice, f"traffic_bytes_per_site_{args.ens_lattice}", f"{kname}_ensemble",
+                        BATCH_SOURCES)
     traffic = None if per_site is None else per_site * sites
     line = {
         "metric": METRIC, "value": glups, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
