@@ -114,12 +114,22 @@ __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *_
   });
 }
 
+// Programmatic dependent launch.  A step kernel lets the next kernel of its
+// stream launch once all of its own blocks have started, so the next step's
+// blocks take the SM slots that this step's last blocks free; each block then
+// waits for the previous grid's completion (and memory) before its first
+// load.  Without the launch attribute both instructions do nothing.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Scalar kernel: one site per thread, any lattice shape.
 template <int LAT, typename S, int NOISE, typename Idx>
 __global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
+  pdl_launch_dependents();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
+  pdl_wait();
   if (x >= a.Lx || y >= a.Ly) return;
   step_scalar_body<LAT, S, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, Idx>(src, dst, a, x, y, z);
 }
@@ -204,9 +214,11 @@ __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__re
 template <int LAT, typename S, int VX, int NOISE, typename Idx>
 __global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
     k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
+  pdl_launch_dependents();
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
+  pdl_wait();
   if (x0 >= a.Lx || y >= a.Ly) return;
   step_vec_body<LAT, S, VX, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, Idx>(src, dst, a, x0, y, z);
 }
@@ -236,15 +248,32 @@ inline int step_vx_override() {
   return v;
 }
 
+// Programmatic dependent launch of the step kernels (a tuning knob; results
+// do not depend on it).  LBFD_STEP_PDL = 0 launches them plainly.
+inline bool step_pdl() {
+  static bool v = [] {
+    const char *e = getenv("LBFD_STEP_PDL");
+    return !(e && atoi(e) == 0);
+  }();
+  return v;
+}
+
 template <int LAT, typename S, int NOISE, typename Idx>
 cudaError_t step_noise_idx(const S *s, S *d, const StepArgs &a, int vx, cudaStream_t stream) {
   dim3 grid, block;
   step_shape(a.Lx, a.Ly, a.Lz, grid, block, vx);
-  if (vx == 2)
-    k_step_vec<LAT, S, 2, NOISE, Idx><<<grid, block, 0, stream>>>(s, d, a);
-  else
-    k_step<LAT, S, NOISE, Idx><<<grid, block, 0, stream>>>(s, d, a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = step_pdl() ? 1 : 0;
+  if (vx == 2) return cudaLaunchKernelEx(&cfg, k_step_vec<LAT, S, 2, NOISE, Idx>, s, d, a);
+  return cudaLaunchKernelEx(&cfg, k_step<LAT, S, NOISE, Idx>, s, d, a);
 }
 
 template <int LAT, typename S, int NOISE>
