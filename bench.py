@@ -61,11 +61,19 @@ BATCH_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_078
                  "paper_1606_07801_gb300/csrc/batch_d2q9.cu", "paper_1606_07801_gb300/csrc/batch_d3q19.cu"]
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and blank lines, so that editing a comment
+    does not invalidate a committed capture of unchanged code."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
     for p in sources:
-        with open(os.path.join(ROOT, p), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -9,15 +9,23 @@
 // counter is t = clock - t0, where clock counts the launches of the batch;
 // the stored state is in block t & 1 and the step writes block (t & 1) ^ 1.
 //
-// Work.  A launch walks a flat list of tiles with a persistent grid.  Member m
-// owns tiles [tile_start[m], tile_start[m + 1]); a tile is `passes` x 256
-// consecutive work items of one member, and an item is vx sites of a row
-// (vx = 2 for even Lx, else 1).  Per tile, warp 0 finds the member by a
-// 32-way search of tile_start and copies that member's step arguments into
-// shared memory; every item then runs the per-site code of the single-lattice
-// kernels, so a member evolves bit-identically to the same lattice stepped
-// alone.  The step arguments (relaxation constants and the Philox words of
-// the member's t) are written once per launch and member by k_batch_prep.
+// Work.  Member m owns tiles [tile_start[m], tile_start[m + 1]) of a flat
+// tile list; a tile is `passes` x 256 consecutive work items of one member,
+// and an item is vx sites of a row (vx = 2 for even Lx, else 1).  Every item
+// runs the per-site code of the single-lattice kernels, so a member evolves
+// bit-identically to the same lattice stepped alone.  The step arguments
+// (relaxation constants and the Philox words of the member's t) are written
+// once per launch and member by k_batch_prep.  Three kernels take the tiles:
+//   k_batch_tile   one block per tile; warp 0 finds the member by a 32-way
+//                  search of tile_start and copies its arguments to shared
+//                  memory;
+//   k_batch_param  one block per tile, one launch per group of up to
+//                  kParamMembers members whose t-independent arguments are a
+//                  kernel parameter (uniform operands, fewer registers); only
+//                  the t words come from k_batch_prep's output;
+//   k_batch_step   a persistent grid whose blocks take every grid-th tile or
+//                  one run of consecutive tiles, reloading the arguments when
+//                  the member changes.
 #pragma once
 
 #include "fastdiv.cuh"
