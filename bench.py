@@ -508,6 +508,8 @@ def main():
     ap.add_argument("--workload", default="d2q9", choices=sorted(WORKLOADS) + ["ensemble", "served"])
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--sample-every", type=int, default=10,
+                    help="step workloads: also time the sampled observables, one sample per this many steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=int, default=4096)
     ap.add_argument("--plan", default="", help="ensemble decomposition vx,passes,occupancy,walk (default: tuned)")
@@ -564,8 +566,12 @@ def main():
     stream = torch.cuda.Stream()
     init = lb.INIT_SINE if args.workload == "d1q3" else lb.INIT_UNIFORM
     rep = replica(rank)
+    # four structure-factor modes for the sampled observables (they do not touch the step)
+    modes = [(1, 0, 0), (2, 0, 0), (0, 1, 0), (1, 1, 1)][: {1: 2, 2: 3, 3: 4}[len(dims)]]
+    if len(dims) < 3:
+        modes = [tuple(k if d < len(dims) else 0 for d, k in enumerate(m)) for m in modes]
     sim = lb.Simulation(lat, dims, tau, rho, rep["seed"], precision=prec, lattice_id=rep["lattice_id"], stream=stream,
-                        torch_buffers=True, device=local, init=init, sine_amp=1.0, sine_k=(1, 0, 0))
+                        torch_buffers=True, device=local, init=init, sine_amp=1.0, sine_k=(1, 0, 0), modes=modes)
 
     def barrier():
         torch.cuda.synchronize()
@@ -602,6 +608,27 @@ def main():
                "frac": a_alu / ISSUE_PEAK, "instructions_per_site": ipsite,
                "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz"}
 
+    # the sampled FP64 observables (mass, density variance, S(k), <f_i>, <f_i f_j>):
+    # time per sample, and the throughput when a sample follows every
+    # --sample-every steps (the fluctuation statistics of a long run)
+    obs = None
+    if args.sample_every > 0:
+        n_samp = 5
+        sim.sample()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_samp):
+            sim.sample()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sample = e0.elapsed_time(e1) / n_samp
+        k = args.sample_every
+        obs = {"ms_per_sample": ms_sample, "sample_every": k, "modes": len(modes),
+               "value_with_sampling": job_glups(world, N, k, (k * ms_per_step + ms_sample) * 1e-3),
+               "algorithmic_bytes_per_sample": Q * elem * N,
+               "achieved_gbs": Q * elem * N / (ms_sample * 1e-3) / 1e9}
+
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device (pinned), one step runs, the density comes back
     h_f = torch.empty(Q * N * elem, dtype=torch.uint8).pin_memory()
@@ -633,7 +660,7 @@ def main():
                          "algorithmic_bytes_per_launch": bytes_per_launch, "kernel": "k_step",
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "roofline_alu": alu,
-            "e2e": e2e,
+            "e2e": e2e, "observables": obs,
             "gpu_launches": launches,
             "clocks": clocks,
         }

@@ -241,7 +241,8 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   }
   h->acc_n = 2 + h->Q + h->Q * h->Q + LBFD_MAX_MODES;
   if (e == cudaSuccess)
-    e = cudaMalloc(&h->partials, sizeof(double) * size_t(kReduceBlocks) * obs_quantities(h->Q, LBFD_MAX_MODES));
+    e = cudaMalloc(&h->partials, sizeof(double) * size_t(std::max(kReduceBlocks, kObsBlocks)) *
+                                     obs_quantities(h->Q, LBFD_MAX_MODES));
   if (e == cudaSuccess) e = cudaMalloc(&h->acc, sizeof(double) * h->acc_n);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mass, sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream);
@@ -451,10 +452,18 @@ int lbfd_sample(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_sample: null handle");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
-  LBFD_CU(materialize_f(h));
-  LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                             int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials, h->acc,
-                             h->stream));
+  if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
+    // FP32 arithmetic: pulled straight from the stored state
+    LBFD_CU(launch_observables_pull(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                                    int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials,
+                                    h->acc, h->stream));
+  } else {
+    // FP64 storage: FP64 throughout, on the streamed copy of the state
+    LBFD_CU(materialize_f(h));
+    LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                               int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials, h->acc,
+                               h->stream));
+  }
   h->n_samples += 1;
   return LBFD_OK;
 }

@@ -149,6 +149,7 @@ cudaError_t launch_box_muller_probe(int precision, const uint32_t *words, int64_
 //   stores them when accumulate == 0).
 constexpr int kReduceBlocks = 304;   // 2 x 152 SMs
 constexpr int kReduceThreads = 256;
+constexpr int kObsBlocks = 608;      // 4 x 152 SMs: the FP32 observable pass (partials sized for it)
 
 // Number of FP64 quantities the observable pass produces for a lattice and mode count.
 int obs_quantities(int Q, int n_modes);
@@ -159,6 +160,13 @@ cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, do
 cudaError_t launch_observables(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
                                double rho_mean, int n_modes, const int32_t *modes /*device, n_modes*3*/,
                                double *partials, double *acc, cudaStream_t stream);
+
+// The same observables for FP32 arithmetic (FP32, FP16, BF16 storage; not
+// FP64) from the stored post-collision state g, pulled per population (no
+// streamed copy); N < 2^31.  Per-tile FP32 sums of deviations, FP64 beyond.
+cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
+                                    double rho_mean, int n_modes, const int32_t *modes, double *partials, double *acc,
+                                    cudaStream_t stream);
 
 // Records msg as the calling thread's lbfd_last_error() and returns code.
 int set_last_error(int code, const std::string &msg);

@@ -10,7 +10,11 @@
 // the partials in block order.  The result does not depend on timing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "device.cuh"
+#include "fastdiv.cuh"
 #include "internal.h"
 
 namespace lbfd {
@@ -225,6 +229,242 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
     constexpr int LAT = decltype(lat)::value;
     using S = typename decltype(tag)::type;
     return obs_t<LAT, S>(f, Lx, Ly, Lz, rho_mean, ma, partials, acc, stream);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Observables of a lattice in FP32 arithmetic (FP32, FP16 and BF16 storage),
+// straight from the stored post-collision state g: population i at site x
+// is f_i(x, t) = g_i(x - v_i), pulled as the step pulls it, so no streamed
+// copy of the state is made.  The GPU has few FP64 units, so per site the
+// kernel works in FP32 on deviations e_i = f_i - c_i from the constants
+// c_i = w_i rho_mean (what the 16-bit formats store), delta = sum_i e_i, and
+// d = rho - rho_mean; each block reduces a tile of 256 sites in FP32 and adds
+// the tile totals to FP64 accumulators.  A tile total has at most 256 terms
+// of one sign-mixed quantity, so its relative error is at most 256 x 2^-24 of
+// the sum of the terms' magnitudes; everything after it is FP64.  The final
+// pass restores the sums of f and rho from the deviations in FP64.
+// ---------------------------------------------------------------------------
+constexpr int kObsThreads = 256;
+
+template <int LAT>
+__device__ __forceinline__ float obs_offset(int i, float rho_f) {
+  return static_cast<float>(Lattice<LAT>::w(i)) * rho_f;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sizes of the lattice with their fast divisions and FP32 inverses.
+struct ObsDims {
+  int32_t Lx, Ly, Lz;
+  FastDiv div_x, div_y, div_z;  // exact for numerators below 2^31
+  float inv_x, inv_y, inv_z;
+  int32_t big;                  // some side >= 46341: k x may not fit 31 bits
+};
+
+// (k x) mod L for 0 <= k, x < L
+__device__ __forceinline__ uint32_t obs_mulmod(uint32_t k, uint32_t x, uint32_t L, FastDiv dv, bool big) {
+  if (big) return static_cast<uint32_t>((static_cast<uint64_t>(k) * x) % L);
+  const uint32_t n = k * x;
+  return n - fastdiv(n, dv) * L;
+}
+
+template <int LAT, typename S>
+__global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ g, const ObsDims dm, float rho_f,
+                                                         float d_off, const ModeArgs modes,
+                                                         double *__restrict__ partials) {
+  using L = Lattice<LAT>;
+  constexpr int Q = L::Q;
+  constexpr int NPAIR = Q * (Q + 1) / 2;
+  constexpr int NW = kObsThreads / 32;
+  __shared__ float tile[Q][kObsThreads + 1];
+  __shared__ float wsum[NW][2 + Q + 2 * LBFD_MAX_MODES_DEV];
+  const int32_t Lx = dm.Lx, Ly = dm.Ly, Lz = dm.Lz;
+  const uint32_t N = static_cast<uint32_t>(Lx) * static_cast<uint32_t>(Ly) * static_cast<uint32_t>(Lz);
+  const int K = modes.n;
+  const int nq1 = 2 + Q + 2 * K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this thread's pair (i, j), i <= j
+  int pi = 0, pj = 0;
+  {
+    int p = threadIdx.x, i = 0;
+    while (p >= Q - i && i < Q) {
+      p -= Q - i;
+      ++i;
+    }
+    pi = i;
+    pj = i + p;
+  }
+  double acc_q = 0.0, acc_pair = 0.0;  // quantity threadIdx.x (< nq1) and pair threadIdx.x (< NPAIR)
+
+  for (uint32_t base = blockIdx.x * kObsThreads; base < N; base += gridDim.x * kObsThreads) {
+    const uint32_t s = base + threadIdx.x;
+    float e[Q];
+    float delta = 0.0f;
+    uint32_t x = 0, y = 0, z = 0;
+    if (s < N) {
+      const uint32_t r = fastdiv(s, dm.div_x);
+      x = s - r * static_cast<uint32_t>(Lx);
+      z = fastdiv(r, dm.div_y);
+      y = r - z * static_cast<uint32_t>(Ly);
+      const uint32_t xm = (x == 0 ? Lx : x) - 1, xp = (x + 1 == static_cast<uint32_t>(Lx)) ? 0 : x + 1;
+      const uint32_t ym = (y == 0 ? Ly : y) - 1, yp = (y + 1 == static_cast<uint32_t>(Ly)) ? 0 : y + 1;
+      const uint32_t zm = (z == 0 ? Lz : z) - 1, zp = (z + 1 == static_cast<uint32_t>(Lz)) ? 0 : z + 1;
+      const uint32_t Lxu = static_cast<uint32_t>(Lx), Lxy = Lxu * static_cast<uint32_t>(Ly);
+      static_for<Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int vx = L::v(i, 0), vy = L::v(i, 1), vz = L::v(i, 2);
+        const uint32_t xs = vx == 0 ? x : (vx > 0 ? xm : xp);
+        const uint32_t ys = vy == 0 ? y : (vy > 0 ? ym : yp);
+        const uint32_t zs = vz == 0 ? z : (vz > 0 ? zm : zp);
+        const S v = g[static_cast<size_t>(i) * N + xs + Lxu * ys + Lxy * zs];
+        // 16-bit formats store the deviation itself; FP32 stores f
+        e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f) : Store<S>::get(v, 0.0f) - obs_offset<LAT>(i, rho_f);
+        delta += e[i];
+      });
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) e[i] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) tile[i][threadIdx.x] = e[i];
+    // per-tile FP32 sums of the per-site quantities, one warp total each
+    auto put = [&](int q, float v) {
+      v = warp_sum_f(v);
+      if (lane == 0) wsum[warp][q] = v;
+    };
+    put(0, delta);
+    put(1, delta * delta);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) put(2 + i, e[i]);
+    if (K > 0) {
+      const float d = s < N ? delta + d_off : 0.0f;
+      for (int m = 0; m < K; ++m) {
+        const uint32_t px = obs_mulmod(static_cast<uint32_t>(modes.k[m][0]), x, Lx, dm.div_x, dm.big);
+        const uint32_t py = obs_mulmod(static_cast<uint32_t>(modes.k[m][1]), y, Ly, dm.div_y, dm.big);
+        const uint32_t pz = obs_mulmod(static_cast<uint32_t>(modes.k[m][2]), z, Lz, dm.div_z, dm.big);
+        // each term is below 1 and exact to FP32 rounding; sincospif reduces exactly
+        const float frac = fmaf(static_cast<float>(px), dm.inv_x,
+                                fmaf(static_cast<float>(py), dm.inv_y, static_cast<float>(pz) * dm.inv_z));
+        float sn, cs;
+        sincospif(2.0f * frac, &sn, &cs);
+        put(2 + Q + 2 * m, d * cs);
+        put(3 + Q + 2 * m, -d * sn);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nq1) {
+      float t = 0.0f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) t += wsum[w][threadIdx.x];
+      acc_q += static_cast<double>(t);
+    }
+    if (threadIdx.x < NPAIR) {
+      float a = 0.0f;
+#pragma unroll 8
+      for (int k = 0; k < kObsThreads; ++k) a = fmaf(tile[pi][k], tile[pj][k], a);
+      acc_pair += static_cast<double>(a);
+    }
+    __syncthreads();
+  }
+  double *out = partials + static_cast<size_t>(blockIdx.x) * (nq1 + NPAIR);
+  if (threadIdx.x < nq1) out[threadIdx.x] = acc_q;
+  if (threadIdx.x < NPAIR) out[nq1 + threadIdx.x] = acc_pair;
+}
+
+// Stage 2 of the FP32 pass: sums the block partials in block order (FP64),
+// restores the sums of rho, f and f f from the deviation sums with
+// c_i = w_i rho_mean (the kernel's own FP32 constants) and adds them to acc:
+//   sum rho   = S_delta + N C,            C = sum_i c_i
+//   sum rho^2 = S_delta2 + 2 C S_delta + N C^2
+//   sum f_i   = E_i + N c_i
+//   sum f_i f_j = P_ij + c_j E_i + c_i E_j + N c_i c_j
+template <int LAT>
+__global__ void k_obs_pull_finalize(const double *__restrict__ partials, int nblocks, int K, double Nd, float rho_f,
+                                    double *__restrict__ acc) {
+  constexpr int Q = Lattice<LAT>::Q;
+  extern __shared__ double tot[];
+  const int nq1 = 2 + Q + 2 * K, npair = Q * (Q + 1) / 2, nq = nq1 + npair;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[static_cast<int64_t>(b) * nq + q];
+    tot[q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c[Q], C = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      c[i] = static_cast<double>(obs_offset<LAT>(i, rho_f));
+      C += c[i];
+    }
+    const double Sd = tot[0], Sd2 = tot[1];
+    acc[0] += Sd + Nd * C;
+    acc[1] += Sd2 + 2.0 * C * Sd + Nd * C * C;
+    for (int i = 0; i < Q; ++i) acc[2 + i] += tot[2 + i] + Nd * c[i];
+    int p = 0;
+    for (int i = 0; i < Q; ++i)
+      for (int j = i; j < Q; ++j, ++p) {
+        const double v = tot[nq1 + p] + c[j] * tot[2 + i] + c[i] * tot[2 + j] + Nd * c[i] * c[j];
+        acc[2 + Q + i * Q + j] += v;
+        if (j != i) acc[2 + Q + j * Q + i] += v;
+      }
+    for (int m = 0; m < K; ++m) {
+      const double re = tot[2 + Q + 2 * m], im = tot[3 + Q + 2 * m];
+      acc[2 + Q + Q * Q + m] += re * re + im * im;
+    }
+  }
+}
+
+int obs_pull_blocks(int64_t N) {
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kObsBlocks, (N + kObsThreads - 1) / kObsThreads)));
+}
+
+cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
+                                    double rho_mean, int n_modes, const int32_t *modes, double *partials, double *acc,
+                                    cudaStream_t stream) {
+  if (n_modes < 0 || n_modes > LBFD_MAX_MODES_DEV || precision == kStoreF64) return cudaErrorInvalidValue;
+  const int64_t N = int64_t(Lx) * Ly * Lz;
+  if (N >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+  const int32_t L3[3] = {Lx, Ly, Lz};
+  ModeArgs ma{};
+  ma.n = n_modes;
+  for (int m = 0; m < n_modes; ++m)
+    for (int k = 0; k < 3; ++k) ma.k[m][k] = static_cast<int32_t>(((int64_t(modes[3 * m + k]) % L3[k]) + L3[k]) % L3[k]);
+  ObsDims dm{};
+  dm.Lx = Lx;
+  dm.Ly = Ly;
+  dm.Lz = Lz;
+  dm.div_x = make_fastdiv(uint32_t(Lx));
+  dm.div_y = make_fastdiv(uint32_t(Ly));
+  dm.div_z = make_fastdiv(uint32_t(Lz));
+  dm.inv_x = 1.0f / float(Lx);
+  dm.inv_y = 1.0f / float(Ly);
+  dm.inv_z = 1.0f / float(Lz);
+  dm.big = (Lx >= 46341 || Ly >= 46341 || Lz >= 46341) ? 1 : 0;
+  const float rho_f = static_cast<float>(rho_mean);
+  const int nblocks = obs_pull_blocks(N);
+  return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
+    constexpr int LAT = decltype(lat)::value;
+    using S = typename decltype(tag)::type;
+    if constexpr (std::is_same_v<S, double>) {
+      return cudaErrorInvalidValue;
+    } else {
+      constexpr int Q = Lattice<LAT>::Q;
+      // d = rho - rho_mean = delta + (C - rho_mean), C from the same FP32 constants
+      double C = 0.0;
+      for (int i = 0; i < Q; ++i) C += static_cast<double>(static_cast<float>(Lattice<LAT>::w(i)) * rho_f);
+      const float d_off = static_cast<float>(C - rho_mean);
+      k_obs_pull<LAT, S><<<nblocks, kObsThreads, 0, stream>>>(static_cast<const S *>(g), dm, rho_f, d_off, ma,
+                                                              partials);
+      const int nq = obs_quantities(Q, n_modes);
+      k_obs_pull_finalize<LAT><<<1, 256, nq * sizeof(double), stream>>>(partials, nblocks, n_modes, double(N), rho_f,
+                                                                       acc);
+      return cudaGetLastError();
+    }
   });
 }
 

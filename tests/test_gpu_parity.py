@@ -206,6 +206,56 @@ def test_moments_mass_and_observables(lat, dims):
         assert abs(ob["sum_sk"][mi] - sk) < 1e-5 * max(sk, 1.0)
 
 
+@pytest.mark.parametrize("lat,dims,prec", [(lb.D1Q3, (77,), lb.F32), (lb.D2Q9, (31, 17), lb.F32),
+                                           (lb.D3Q19, (7, 6, 5), lb.F32), (lb.D2Q9, (300, 261), lb.F32),
+                                           (lb.D3Q19, (40, 33, 21), lb.F32_F16), (lb.D2Q9, (64, 48), lb.F32_BF16),
+                                           (lb.D1Q3, (50001,), lb.F32), (lb.D2Q5, (45, 38), lb.F32)])
+def test_fp32_observables_match_fp64_sums(lat, dims, prec):
+    """FP32-arithmetic formats sample from the stored state directly (no
+    streamed copy), in FP32 per 256-site tile on deviations from w_i rho_mean
+    and FP64 beyond.  The restored sums must match FP64 sums over get_f()
+    (the same stored values) to what FP32 tiles allow; the central moments
+    (density variance, covariance of the f_i) and S(k) are checked directly.
+    The 50001-site line takes the 64-bit phase path (k x may pass 2^31)."""
+    Q, N = lb.Q_OF[lat], int(np.prod(dims))
+    modes = [(1, 0, 0), (2, 1, 0), (0, 1, 1), (3, 2, 1)][: 2 + (lat == lb.D3Q19)]
+    if len(dims) == 1:
+        modes = [(1, 0, 0), (7, 0, 0)]
+    rho_mean = 30.0
+    kw = dict(theta=0.3) if lat == lb.D2Q5 else {}
+    with lb.Simulation(lat, dims, 0.8, rho_mean, 4, precision=prec, modes=modes, **kw) as s:
+        s.step(13)
+        f1 = s.get_f()
+        s.sample()
+        s.step(3)
+        f2 = s.get_f()
+        s.sample()
+        ob = s.observables()
+    fs = (f1, f2)
+    n = 2 * N
+    rho_sum = sum(f.sum() for f in fs)
+    rho2_sum = sum((f.sum(0) ** 2).sum() for f in fs)
+    f_sum = sum(f.sum(1) for f in fs)
+    ff_sum = sum(f @ f.T for f in fs)
+    assert ob["n_samples"] == 2
+    assert abs(ob["sum_rho"] - rho_sum) <= 5e-7 * rho_sum
+    var_ref = rho2_sum / n - (rho_sum / n) ** 2
+    var_gpu = ob["sum_rho2"] / n - (ob["sum_rho"] / n) ** 2
+    assert abs(var_gpu - var_ref) <= 1e-4 * var_ref
+    assert np.max(np.abs(ob["sum_f"] - f_sum)) <= 5e-7 * np.max(f_sum)
+    cov_ref = ff_sum / n - np.outer(f_sum, f_sum) / n ** 2
+    cov_gpu = np.asarray(ob["sum_ff"]) / n - np.outer(ob["sum_f"], ob["sum_f"]) / n ** 2
+    assert np.max(np.abs(cov_gpu - cov_ref)) <= 1e-4 * np.max(np.abs(cov_ref))
+    d3 = list(dims) + [1] * (3 - len(dims))
+    for mi, k in enumerate(modes):
+        sk = 0.0
+        for f in fs:
+            field = (f.sum(0) - rho_mean).reshape(d3[2], d3[1], d3[0])
+            ft = np.fft.fftn(field)
+            sk += abs(ft[k[2] % d3[2], k[1] % d3[1], k[0] % d3[0]]) ** 2
+        assert abs(ob["sum_sk"][mi] - sk) <= 1e-4 * sk + 1e-3 * N * var_ref, (mi, k)
+
+
 def test_torch_buffers_and_stream_give_same_result():
     import torch
 
