@@ -178,16 +178,40 @@ __global__ void __launch_bounds__(kReduceThreads) k_obs_partials(const S *__rest
   if (threadIdx.x < NPAIR) out[nq1 + threadIdx.x] = a_ff;
 }
 
+// Stage-2 sum of per-block partials[b][q] (b < nblocks, q < nq) in a fixed
+// order, by kFinalThreads threads: warp w adds the blocks w, w + W, ... of 32
+// quantities at a time (coalesced rows), then thread q adds the W warp sums.
+// tot needs nq + W * nq doubles of shared memory.
+constexpr int kFinalThreads = 512;
+__device__ __forceinline__ void sum_partials_ordered(const double *__restrict__ partials, int nblocks, int nq,
+                                                     double *tot) {
+  constexpr int W = kFinalThreads / 32;
+  double *part = tot + nq;  // [W][nq]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q0 = 0; q0 < nq; q0 += 32) {
+    const int q = q0 + lane;
+    if (q < nq) {
+      double t = 0.0;
+      for (int b = warp; b < nblocks; b += W) t += partials[static_cast<int64_t>(b) * nq + q];
+      part[warp * nq + q] = t;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < W; ++w) t += part[w * nq + q];
+    tot[q] = t;
+  }
+  __syncthreads();
+}
+
+inline size_t final_smem(int nq) { return sizeof(double) * size_t(nq) * (1 + kFinalThreads / 32); }
+
 // acc layout: [sum_rho, sum_rho2, sum_f[Q], sum_ff[Q*Q] (full, symmetric), sum_sk[K]]
 __global__ void k_obs_finalize(const double *__restrict__ partials, int nblocks, int Q, int K, double *__restrict__ acc) {
   extern __shared__ double tot[];
   const int nq1 = 2 + Q + 2 * K, npair = Q * (Q + 1) / 2, nq = nq1 + npair;
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    double t = 0.0;
-    for (int b = 0; b < nblocks; ++b) t += partials[static_cast<int64_t>(b) * nq + q];
-    tot[q] = t;
-  }
-  __syncthreads();
+  sum_partials_ordered(partials, nblocks, nq, tot);
   if (threadIdx.x == 0) {
     acc[0] += tot[0];
     acc[1] += tot[1];
@@ -213,7 +237,7 @@ static cudaError_t obs_t(const void *f, int32_t Lx, int32_t Ly, int32_t Lz, doub
   k_obs_partials<LAT, S><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const S *>(f), Lx, Ly, Lz, rho_mean,
                                                                        ma, partials);
   const int nq = obs_quantities(Q, ma.n);
-  k_obs_finalize<<<1, 256, nq * sizeof(double), stream>>>(partials, kReduceBlocks, Q, ma.n, acc);
+  k_obs_finalize<<<1, kFinalThreads, final_smem(nq), stream>>>(partials, kReduceBlocks, Q, ma.n, acc);
   return cudaGetLastError();
 }
 
@@ -273,6 +297,21 @@ __device__ __forceinline__ uint32_t obs_mulmod(uint32_t k, uint32_t x, uint32_t 
   return n - fastdiv(n, dv) * L;
 }
 
+// Pair sums sum_x e_i e_j by register blocks: the rows i are padded to QP =
+// 4 G and grouped by four; a thread owns one block (I, J), I <= J, of 4 x 4
+// pairs and one slice of the tile's sites (sites sl, sl + SL, ...), and reads
+// each site's two row groups as two 16-byte shared loads for 16 FMAs.  Its
+// FP32 block sums cover SL tiles (256 products each) before they go to FP64.
+template <int Q>
+struct ObsPairPlan {
+  static constexpr int QP = (Q + 3) / 4 * 4;
+  static constexpr int G = QP / 4;
+  static constexpr int NB = G * (G + 1) / 2;
+  static constexpr int SL = NB <= 1 ? 256 : NB <= 2 ? 128 : NB <= 4 ? 64 : NB <= 8 ? 32 : NB <= 16 ? 16 : 8;
+  static constexpr int SPS = kObsThreads / SL;  // sites of a slice in one tile
+  static_assert(NB * SL <= kObsThreads && NB * 16 <= kObsThreads, "pair plan exceeds the block");
+};
+
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ g, const ObsDims dm, float rho_f,
                                                          float d_off, const ModeArgs modes,
@@ -281,29 +320,59 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
   constexpr int Q = L::Q;
   constexpr int NPAIR = Q * (Q + 1) / 2;
   constexpr int NW = kObsThreads / 32;
-  __shared__ float tile[Q][kObsThreads + 1];
+  using P = ObsPairPlan<Q>;
+  constexpr int QP = P::QP, SL = P::SL, SPS = P::SPS;
+  __shared__ __align__(16) float tile[kObsThreads][QP];
+  __shared__ float red[P::NB * SL][16];
   __shared__ float wsum[NW][2 + Q + 2 * LBFD_MAX_MODES_DEV];
   const int32_t Lx = dm.Lx, Ly = dm.Ly, Lz = dm.Lz;
   const uint32_t N = static_cast<uint32_t>(Lx) * static_cast<uint32_t>(Ly) * static_cast<uint32_t>(Lz);
   const int K = modes.n;
   const int nq1 = 2 + Q + 2 * K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // this thread's pair (i, j), i <= j
-  int pi = 0, pj = 0;
+  // this thread's pair block (I, J) and slice, when it has one
+  const bool has_block = threadIdx.x < P::NB * SL;
+  const int blk = threadIdx.x / SL, sl = threadIdx.x % SL;
+  int bI = 0, bJ = 0;
   {
-    int p = threadIdx.x, i = 0;
-    while (p >= Q - i && i < Q) {
-      p -= Q - i;
+    int b = has_block ? blk : 0, i = 0;
+    while (b >= P::G - i) {
+      b -= P::G - i;
       ++i;
     }
-    pi = i;
-    pj = i + p;
+    bI = i;
+    bJ = i + b;
   }
-  double acc_q = 0.0, acc_pair = 0.0;  // quantity threadIdx.x (< nq1) and pair threadIdx.x (< NPAIR)
+  float pa[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) pa[e] = 0.0f;
+  double acc_q = 0.0, acc_pair = 0.0;  // quantity threadIdx.x (< nq1), pair slot threadIdx.x (< NB * 16)
+  int tiles = 0;
+
+  // FP32 block sums of the last tiles into the FP64 slot sums (in slice order)
+  auto flush_pairs = [&]() {
+    if (has_block) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        red[threadIdx.x][e] = pa[e];
+        pa[e] = 0.0f;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < P::NB * 16) {
+      const int b = threadIdx.x >> 4, e = threadIdx.x & 15;
+      double t = 0.0;
+      for (int k = 0; k < SL; ++k) t += static_cast<double>(red[b * SL + k][e]);
+      acc_pair += t;
+    }
+    __syncthreads();
+  };
 
   for (uint32_t base = blockIdx.x * kObsThreads; base < N; base += gridDim.x * kObsThreads) {
     const uint32_t s = base + threadIdx.x;
-    float e[Q];
+    float e[QP];
+#pragma unroll
+    for (int i = 0; i < QP; ++i) e[i] = 0.0f;
     float delta = 0.0f;
     uint32_t x = 0, y = 0, z = 0;
     if (s < N) {
@@ -326,12 +395,10 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
         e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f) : Store<S>::get(v, 0.0f) - obs_offset<LAT>(i, rho_f);
         delta += e[i];
       });
-    } else {
-#pragma unroll
-      for (int i = 0; i < Q; ++i) e[i] = 0.0f;
     }
 #pragma unroll
-    for (int i = 0; i < Q; ++i) tile[i][threadIdx.x] = e[i];
+    for (int i = 0; i < QP; i += 4)
+      *reinterpret_cast<float4 *>(&tile[threadIdx.x][i]) = make_float4(e[i], e[i + 1], e[i + 2], e[i + 3]);
     // per-tile FP32 sums of the per-site quantities, one warp total each
     auto put = [&](int q, float v) {
       v = warp_sum_f(v);
@@ -363,17 +430,39 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
       for (int w = 0; w < NW; ++w) t += wsum[w][threadIdx.x];
       acc_q += static_cast<double>(t);
     }
-    if (threadIdx.x < NPAIR) {
-      float a = 0.0f;
-#pragma unroll 8
-      for (int k = 0; k < kObsThreads; ++k) a = fmaf(tile[pi][k], tile[pj][k], a);
-      acc_pair += static_cast<double>(a);
+    if (has_block) {
+#pragma unroll 4
+      for (int kk = 0; kk < SPS; ++kk) {
+        const int k = sl + kk * SL;
+        const float4 u = *reinterpret_cast<const float4 *>(&tile[k][4 * bI]);
+        const float4 v = *reinterpret_cast<const float4 *>(&tile[k][4 * bJ]);
+        const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) pa[4 * a + c] = fmaf(uu[a], vv[c], pa[4 * a + c]);
+      }
     }
     __syncthreads();
+    if (++tiles == SL) {
+      flush_pairs();
+      tiles = 0;
+    }
   }
+  if (tiles > 0) flush_pairs();
   double *out = partials + static_cast<size_t>(blockIdx.x) * (nq1 + NPAIR);
   if (threadIdx.x < nq1) out[threadIdx.x] = acc_q;
-  if (threadIdx.x < NPAIR) out[nq1 + threadIdx.x] = acc_pair;
+  if (threadIdx.x < P::NB * 16) {
+    // slot (block b, element e) holds the pair (4 I + e / 4, 4 J + e % 4)
+    int b = threadIdx.x >> 4, i0 = 0;
+    const int el = threadIdx.x & 15;
+    while (b >= P::G - i0) {
+      b -= P::G - i0;
+      ++i0;
+    }
+    const int i = 4 * i0 + (el >> 2), j = 4 * (i0 + b) + (el & 3);
+    if (i < Q && j < Q && i <= j) out[nq1 + i * Q - i * (i - 1) / 2 + (j - i)] = acc_pair;
+  }
 }
 
 // Stage 2 of the FP32 pass: sums the block partials in block order (FP64),
@@ -389,12 +478,7 @@ __global__ void k_obs_pull_finalize(const double *__restrict__ partials, int nbl
   constexpr int Q = Lattice<LAT>::Q;
   extern __shared__ double tot[];
   const int nq1 = 2 + Q + 2 * K, npair = Q * (Q + 1) / 2, nq = nq1 + npair;
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    double t = 0.0;
-    for (int b = 0; b < nblocks; ++b) t += partials[static_cast<int64_t>(b) * nq + q];
-    tot[q] = t;
-  }
-  __syncthreads();
+  sum_partials_ordered(partials, nblocks, nq, tot);
   if (threadIdx.x == 0) {
     double c[Q], C = 0.0;
     for (int i = 0; i < Q; ++i) {
@@ -461,8 +545,8 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
       k_obs_pull<LAT, S><<<nblocks, kObsThreads, 0, stream>>>(static_cast<const S *>(g), dm, rho_f, d_off, ma,
                                                               partials);
       const int nq = obs_quantities(Q, n_modes);
-      k_obs_pull_finalize<LAT><<<1, 256, nq * sizeof(double), stream>>>(partials, nblocks, n_modes, double(N), rho_f,
-                                                                       acc);
+      k_obs_pull_finalize<LAT><<<1, kFinalThreads, final_smem(nq), stream>>>(partials, nblocks, n_modes, double(N),
+                                                                                 rho_f, acc);
       return cudaGetLastError();
     }
   });
