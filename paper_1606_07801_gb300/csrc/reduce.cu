@@ -180,32 +180,41 @@ __global__ void __launch_bounds__(kReduceThreads) k_obs_partials(const S *__rest
 
 // Stage-2 sum of per-block partials[b][q] (b < nblocks, q < nq) in a fixed
 // order, by kFinalThreads threads: warp w adds the blocks w, w + W, ... of 32
-// quantities at a time (coalesced rows), then thread q adds the W warp sums.
-// tot needs nq + W * nq doubles of shared memory.
+// quantities at a time (coalesced rows; all its loads issued before the
+// adds), then thread q adds the W warp sums.  tot needs nq + W * nq doubles
+// of shared memory.
 constexpr int kFinalThreads = 512;
+constexpr int kFinalWarps = kFinalThreads / 32;
+constexpr int kFinalPer = ((kObsBlocks > kReduceBlocks ? kObsBlocks : kReduceBlocks) + kFinalWarps - 1) / kFinalWarps;
 __device__ __forceinline__ void sum_partials_ordered(const double *__restrict__ partials, int nblocks, int nq,
                                                      double *tot) {
-  constexpr int W = kFinalThreads / 32;
   double *part = tot + nq;  // [W][nq]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q0 = 0; q0 < nq; q0 += 32) {
     const int q = q0 + lane;
     if (q < nq) {
+      double v[kFinalPer];
+#pragma unroll
+      for (int j = 0; j < kFinalPer; ++j) {
+        const int b = warp + j * kFinalWarps;
+        v[j] = b < nblocks ? partials[static_cast<int64_t>(b) * nq + q] : 0.0;
+      }
       double t = 0.0;
-      for (int b = warp; b < nblocks; b += W) t += partials[static_cast<int64_t>(b) * nq + q];
+#pragma unroll
+      for (int j = 0; j < kFinalPer; ++j) t += v[j];
       part[warp * nq + q] = t;
     }
   }
   __syncthreads();
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     double t = 0.0;
-    for (int w = 0; w < W; ++w) t += part[w * nq + q];
+    for (int w = 0; w < kFinalWarps; ++w) t += part[w * nq + q];
     tot[q] = t;
   }
   __syncthreads();
 }
 
-inline size_t final_smem(int nq) { return sizeof(double) * size_t(nq) * (1 + kFinalThreads / 32); }
+inline size_t final_smem(int nq) { return sizeof(double) * size_t(nq) * (1 + kFinalWarps); }
 
 // acc layout: [sum_rho, sum_rho2, sum_f[Q], sum_ff[Q*Q] (full, symmetric), sum_sk[K]]
 __global__ void k_obs_finalize(const double *__restrict__ partials, int nblocks, int Q, int K, double *__restrict__ acc) {
@@ -302,9 +311,12 @@ __device__ __forceinline__ uint32_t obs_mulmod(uint32_t k, uint32_t x, uint32_t 
 // pairs and one slice of the tile's sites (sites sl, sl + SL, ...), and reads
 // each site's two row groups as two 16-byte shared loads for 16 FMAs.  Its
 // FP32 block sums cover SL tiles (256 products each) before they go to FP64.
+// Row Q (always padding) holds 1 at every site, so the pairs (i, Q) give
+// sum_x e_i, and sum delta = sum_i sum_x e_i, sum delta^2 = sum_ij sum_x e_i e_j
+// follow without per-site reductions.
 template <int Q>
 struct ObsPairPlan {
-  static constexpr int QP = (Q + 3) / 4 * 4;
+  static constexpr int QP = (Q / 4 + 1) * 4;
   static constexpr int G = QP / 4;
   static constexpr int NB = G * (G + 1) / 2;
   static constexpr int SL = NB <= 1 ? 256 : NB <= 2 ? 128 : NB <= 4 ? 64 : NB <= 8 ? 32 : NB <= 16 ? 16 : 8;
@@ -324,7 +336,8 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
   constexpr int QP = P::QP, SL = P::SL, SPS = P::SPS;
   __shared__ __align__(16) float tile[kObsThreads][QP];
   __shared__ float red[P::NB * SL][16];
-  __shared__ float wsum[NW][2 + Q + 2 * LBFD_MAX_MODES_DEV];
+  __shared__ float wsum[NW][2 * LBFD_MAX_MODES_DEV];
+  __shared__ double slot_sum[P::NB * 16];
   const int32_t Lx = dm.Lx, Ly = dm.Ly, Lz = dm.Lz;
   const uint32_t N = static_cast<uint32_t>(Lx) * static_cast<uint32_t>(Ly) * static_cast<uint32_t>(Lz);
   const int K = modes.n;
@@ -346,7 +359,7 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
   float pa[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) pa[e] = 0.0f;
-  double acc_q = 0.0, acc_pair = 0.0;  // quantity threadIdx.x (< nq1), pair slot threadIdx.x (< NB * 16)
+  double acc_q = 0.0, acc_pair = 0.0;  // mode sum threadIdx.x (< 2 K), pair slot threadIdx.x (< NB * 16)
   int tiles = 0;
 
   // FP32 block sums of the last tiles into the FP64 slot sums (in slice order)
@@ -395,19 +408,16 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
         e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f) : Store<S>::get(v, 0.0f) - obs_offset<LAT>(i, rho_f);
         delta += e[i];
       });
+      e[Q] = 1.0f;
     }
 #pragma unroll
     for (int i = 0; i < QP; i += 4)
       *reinterpret_cast<float4 *>(&tile[threadIdx.x][i]) = make_float4(e[i], e[i + 1], e[i + 2], e[i + 3]);
-    // per-tile FP32 sums of the per-site quantities, one warp total each
+    // per-tile FP32 sums of the mode quantities, one warp total each
     auto put = [&](int q, float v) {
       v = warp_sum_f(v);
       if (lane == 0) wsum[warp][q] = v;
     };
-    put(0, delta);
-    put(1, delta * delta);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) put(2 + i, e[i]);
     if (K > 0) {
       const float d = s < N ? delta + d_off : 0.0f;
       for (int m = 0; m < K; ++m) {
@@ -419,12 +429,12 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
                                 fmaf(static_cast<float>(py), dm.inv_y, static_cast<float>(pz) * dm.inv_z));
         float sn, cs;
         sincospif(2.0f * frac, &sn, &cs);
-        put(2 + Q + 2 * m, d * cs);
-        put(3 + Q + 2 * m, -d * sn);
+        put(2 * m, d * cs);
+        put(2 * m + 1, -d * sn);
       }
     }
     __syncthreads();
-    if (threadIdx.x < nq1) {
+    if (threadIdx.x < 2 * K) {
       float t = 0.0f;
 #pragma unroll
       for (int w = 0; w < NW; ++w) t += wsum[w][threadIdx.x];
@@ -450,18 +460,34 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
     }
   }
   if (tiles > 0) flush_pairs();
+  // gather the slot sums, then write the block's partials in the layout of
+  // k_obs_partials: [sum delta, sum delta^2, sum e_i, modes, pairs i <= j]
+  if (threadIdx.x < P::NB * 16) slot_sum[threadIdx.x] = acc_pair;
+  __syncthreads();
+  auto slot_of = [](int i, int j) {  // i <= j < QP
+    const int I = i >> 2, J = j >> 2;
+    return (I * P::G - I * (I - 1) / 2 + (J - I)) * 16 + (i & 3) * 4 + (j & 3);
+  };
   double *out = partials + static_cast<size_t>(blockIdx.x) * (nq1 + NPAIR);
-  if (threadIdx.x < nq1) out[threadIdx.x] = acc_q;
-  if (threadIdx.x < P::NB * 16) {
-    // slot (block b, element e) holds the pair (4 I + e / 4, 4 J + e % 4)
-    int b = threadIdx.x >> 4, i0 = 0;
-    const int el = threadIdx.x & 15;
-    while (b >= P::G - i0) {
-      b -= P::G - i0;
-      ++i0;
+  if (threadIdx.x < NPAIR) {
+    int p = threadIdx.x, i = 0;
+    while (p >= Q - i) {
+      p -= Q - i;
+      ++i;
     }
-    const int i = 4 * i0 + (el >> 2), j = 4 * (i0 + b) + (el & 3);
-    if (i < Q && j < Q && i <= j) out[nq1 + i * Q - i * (i - 1) / 2 + (j - i)] = acc_pair;
+    out[nq1 + threadIdx.x] = slot_sum[slot_of(i, i + p)];
+  }
+  if (threadIdx.x < Q) out[2 + threadIdx.x] = slot_sum[slot_of(threadIdx.x, Q)];
+  if (threadIdx.x < 2 * K) out[2 + Q + threadIdx.x] = acc_q;
+  if (threadIdx.x == 0) {
+    double sd = 0.0, sd2 = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      sd += slot_sum[slot_of(i, Q)];
+      sd2 += slot_sum[slot_of(i, i)];
+      for (int j = i + 1; j < Q; ++j) sd2 += 2.0 * slot_sum[slot_of(i, j)];
+    }
+    out[0] = sd;
+    out[1] = sd2;
   }
 }
 
