@@ -81,6 +81,7 @@ struct lbfd_sim {
   double *mom = nullptr;  // rho and j for lbfd_moments, allocated on first use
   int64_t n_samples = 0;
   int32_t modes_host[LBFD_MAX_MODES][3] = {};
+  void *phase = nullptr;  // per-axis structure-factor factors (FP32 sampling), or null
   // moment-space (multiple-relaxation-time) kernel: taken for D2Q5 and when
   // any tau^a differs from tau; tables of the lattice at its theta
   bool mrt = false;
@@ -188,6 +189,7 @@ static void free_sim(lbfd_sim *h) {
     cudaFree(h->f[1]);
   }
   cudaFree(h->partials);
+  cudaFree(h->phase);
   cudaFree(h->acc);
   cudaFree(h->d_mass);
   cudaFree(h->mom);
@@ -245,6 +247,16 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
                                      obs_quantities(h->Q, LBFD_MAX_MODES));
   if (e == cudaSuccess) e = cudaMalloc(&h->acc, sizeof(double) * h->acc_n);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mass, sizeof(double));
+  // the structure-factor phases of FP32 sampling as per-axis tables (when small)
+  const size_t nphase = obs_phase_values(opt->n_modes, int32_t(opt->dims[0]), int32_t(opt->dims[1]),
+                                         int32_t(opt->dims[2]));
+  if (e == cudaSuccess && opt->precision != LBFD_F64 && nphase > 0 && nphase <= (size_t(1) << 22)) {
+    std::vector<float> tab(2 * nphase);
+    obs_phase_fill(opt->n_modes, &h->modes_host[0][0], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
+                   int32_t(opt->dims[2]), tab.data());
+    e = cudaMalloc(&h->phase, sizeof(float) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(h->phase, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream);
   if (e == cudaSuccess && opt->init != LBFD_INIT_NONE) {
     // f(x, 0) into the spare buffer, then stored as g = f shifted back
@@ -455,8 +467,8 @@ int lbfd_sample(lbfd_t h) {
   if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
     // FP32 arithmetic: pulled straight from the stored state
     LBFD_CU(launch_observables_pull(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                                    int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials,
-                                    h->acc, h->stream));
+                                    int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->phase,
+                                    h->partials, h->acc, h->stream));
   } else {
     // FP64 storage: FP64 throughout, on the streamed copy of the state
     LBFD_CU(materialize_f(h));

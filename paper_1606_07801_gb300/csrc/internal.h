@@ -164,9 +164,14 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
 // The same observables for FP32 arithmetic (FP32, FP16, BF16 storage; not
 // FP64) from the stored post-collision state g, pulled per population (no
 // streamed copy); N < 2^31.  Per-tile FP32 sums of deviations, FP64 beyond.
+// phase (optional): the per-axis factors of the structure-factor modes,
+// obs_phase_values() float pairs filled by obs_phase_fill(); without it the
+// kernel evaluates each phase with sincospif.
 cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
-                                    double rho_mean, int n_modes, const int32_t *modes, double *partials, double *acc,
-                                    cudaStream_t stream);
+                                    double rho_mean, int n_modes, const int32_t *modes, const void *phase,
+                                    double *partials, double *acc, cudaStream_t stream);
+size_t obs_phase_values(int n_modes, int32_t Lx, int32_t Ly, int32_t Lz);
+void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out);
 
 // Records msg as the calling thread's lbfd_last_error() and returns code.
 int set_last_error(int code, const std::string &msg);

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 
 #include "device.cuh"
@@ -327,6 +328,7 @@ struct ObsPairPlan {
 template <int LAT, typename S>
 __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ g, const ObsDims dm, float rho_f,
                                                          float d_off, const ModeArgs modes,
+                                                         const float2 *__restrict__ phase,
                                                          double *__restrict__ partials) {
   using L = Lattice<LAT>;
   constexpr int Q = L::Q;
@@ -421,14 +423,24 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
     if (K > 0) {
       const float d = s < N ? delta + d_off : 0.0f;
       for (int m = 0; m < K; ++m) {
-        const uint32_t px = obs_mulmod(static_cast<uint32_t>(modes.k[m][0]), x, Lx, dm.div_x, dm.big);
-        const uint32_t py = obs_mulmod(static_cast<uint32_t>(modes.k[m][1]), y, Ly, dm.div_y, dm.big);
-        const uint32_t pz = obs_mulmod(static_cast<uint32_t>(modes.k[m][2]), z, Lz, dm.div_z, dm.big);
-        // each term is below 1 and exact to FP32 rounding; sincospif reduces exactly
-        const float frac = fmaf(static_cast<float>(px), dm.inv_x,
-                                fmaf(static_cast<float>(py), dm.inv_y, static_cast<float>(pz) * dm.inv_z));
-        float sn, cs;
-        sincospif(2.0f * frac, &sn, &cs);
+        float cs, sn;
+        if (phase) {
+          // e^{-2 pi i k.x / L} as the product of its three per-axis factors
+          const float2 fx = phase[m * Lx + x];
+          const float2 fy = phase[K * Lx + m * Ly + y];
+          const float2 fz = phase[K * (Lx + Ly) + m * Lz + z];
+          const float ar = fx.x * fy.x - fx.y * fy.y, ai = fx.x * fy.y + fx.y * fy.x;
+          cs = ar * fz.x - ai * fz.y;
+          sn = -(ar * fz.y + ai * fz.x);
+        } else {
+          const uint32_t px = obs_mulmod(static_cast<uint32_t>(modes.k[m][0]), x, Lx, dm.div_x, dm.big);
+          const uint32_t py = obs_mulmod(static_cast<uint32_t>(modes.k[m][1]), y, Ly, dm.div_y, dm.big);
+          const uint32_t pz = obs_mulmod(static_cast<uint32_t>(modes.k[m][2]), z, Lz, dm.div_z, dm.big);
+          // each term is below 1 and exact to FP32 rounding; sincospif reduces exactly
+          const float frac = fmaf(static_cast<float>(px), dm.inv_x,
+                                  fmaf(static_cast<float>(py), dm.inv_y, static_cast<float>(pz) * dm.inv_z));
+          sincospif(2.0f * frac, &sn, &cs);
+        }
         put(2 * m, d * cs);
         put(2 * m + 1, -d * sn);
       }
@@ -534,8 +546,8 @@ int obs_pull_blocks(int64_t N) {
 }
 
 cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
-                                    double rho_mean, int n_modes, const int32_t *modes, double *partials, double *acc,
-                                    cudaStream_t stream) {
+                                    double rho_mean, int n_modes, const int32_t *modes, const void *phase,
+                                    double *partials, double *acc, cudaStream_t stream) {
   if (n_modes < 0 || n_modes > LBFD_MAX_MODES_DEV || precision == kStoreF64) return cudaErrorInvalidValue;
   const int64_t N = int64_t(Lx) * Ly * Lz;
   if (N >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
@@ -569,13 +581,32 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
       for (int i = 0; i < Q; ++i) C += static_cast<double>(static_cast<float>(Lattice<LAT>::w(i)) * rho_f);
       const float d_off = static_cast<float>(C - rho_mean);
       k_obs_pull<LAT, S><<<nblocks, kObsThreads, 0, stream>>>(static_cast<const S *>(g), dm, rho_f, d_off, ma,
-                                                              partials);
+                                                              static_cast<const float2 *>(phase), partials);
       const int nq = obs_quantities(Q, n_modes);
       k_obs_pull_finalize<LAT><<<1, kFinalThreads, final_smem(nq), stream>>>(partials, nblocks, n_modes, double(N),
                                                                                  rho_f, acc);
       return cudaGetLastError();
     }
   });
+}
+
+size_t obs_phase_values(int n_modes, int32_t Lx, int32_t Ly, int32_t Lz) {
+  return size_t(n_modes) * (size_t(Lx) + size_t(Ly) + size_t(Lz));
+}
+
+void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out) {
+  // per axis d and mode m: e^{-2 pi i r / L_d}, r = (k_d u) mod L_d, u < L_d, in FP64 then rounded
+  const int32_t L3[3] = {Lx, Ly, Lz};
+  size_t at = 0;
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < n_modes; ++m) {
+      const int64_t L = L3[d], k = ((int64_t(modes[3 * m + d]) % L) + L) % L;
+      for (int64_t u = 0; u < L; ++u, ++at) {
+        const double a = 2.0 * 3.14159265358979323846 * double((k * u) % L) / double(L);
+        out[2 * at] = static_cast<float>(std::cos(a));
+        out[2 * at + 1] = static_cast<float>(-std::sin(a));
+      }
+    }
 }
 
 }  // namespace lbfd

@@ -209,14 +209,17 @@ def test_moments_mass_and_observables(lat, dims):
 @pytest.mark.parametrize("lat,dims,prec", [(lb.D1Q3, (77,), lb.F32), (lb.D2Q9, (31, 17), lb.F32),
                                            (lb.D3Q19, (7, 6, 5), lb.F32), (lb.D2Q9, (300, 261), lb.F32),
                                            (lb.D3Q19, (40, 33, 21), lb.F32_F16), (lb.D2Q9, (64, 48), lb.F32_BF16),
-                                           (lb.D1Q3, (50001,), lb.F32), (lb.D2Q5, (45, 38), lb.F32)])
+                                           (lb.D1Q3, (50001,), lb.F32), (lb.D2Q5, (45, 38), lb.F32),
+                                           (lb.D1Q3, (2200001,), lb.F32)])
 def test_fp32_observables_match_fp64_sums(lat, dims, prec):
     """FP32-arithmetic formats sample from the stored state directly (no
     streamed copy), in FP32 per 256-site tile on deviations from w_i rho_mean
     and FP64 beyond.  The restored sums must match FP64 sums over get_f()
     (the same stored values) to what FP32 tiles allow; the central moments
     (density variance, covariance of the f_i) and S(k) are checked directly.
-    The 50001-site line takes the 64-bit phase path (k x may pass 2^31)."""
+    The structure-factor phases come from per-axis tables, except on the
+    2200001-site line (tables too large), which evaluates them directly with
+    64-bit products (k x may pass 2^31)."""
     Q, N = lb.Q_OF[lat], int(np.prod(dims))
     modes = [(1, 0, 0), (2, 1, 0), (0, 1, 1), (3, 2, 1)][: 2 + (lat == lb.D3Q19)]
     if len(dims) == 1:
