@@ -431,6 +431,12 @@ int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev) {
   if (!h || !rho_dev) return fail(LBFD_EINVAL, "lbfd_moments_device: null argument");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
+  if (!j_dev) {
+    // density only: pulled from the stored state, no streamed copy
+    LBFD_CU(launch_density_of_state(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                                    int32_t(o.dims[2]), o.rho_mean, rho_dev, h->stream));
+    return LBFD_OK;
+  }
   LBFD_CU(materialize_f(h));
   LBFD_CU(launch_moments(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
                          int32_t(o.dims[2]), o.rho_mean, rho_dev, j_dev, h->stream));

@@ -130,6 +130,11 @@ cudaError_t launch_step_small(int lattice, int precision, const void *src, void 
 // D2Q5 weights and moment basis (m[a*5 + i]) for second moment theta.
 void d2q5_tables(double theta, double *w, double *m);
 
+// rho(x) of the paper's f(x, t) straight from the stored post-collision state
+// g (populations pulled, FP64 sum in velocity order): the same values as a
+// streaming shift followed by launch_moments, without the shift.
+cudaError_t launch_density_of_state(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
+                                    double rho_mean, double *rho, cudaStream_t stream);
 // rho(x) = sum_i f_i, j_a(x) = sum_i f_i v_ia (FP64 outputs; j may be null).
 // rho_mean decodes the 16-bit deviation formats.
 cudaError_t launch_moments(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,

@@ -40,52 +40,6 @@
 
 using namespace lbfd;
 
-namespace lbfd {
-
-// rho(x) = sum_i g_i(x - v_i): the density of the paper's f(x, t) computed
-// from the stored post-collision state g, summed in FP64 in velocity order
-// (the same values and order as a streaming shift followed by k_moments).
-template <int LAT, typename S>
-__global__ void k_density_of_state(const S *__restrict__ g, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
-                                   double *__restrict__ rho) {
-  using L = Lattice<LAT>;
-  const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
-  for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < N;
-       s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(s % Lx);
-    const int64_t r = s / Lx;
-    const int y = static_cast<int>(r % Ly), z = static_cast<int>(r / Ly);
-    const int xm = (x == 0 ? Lx : x) - 1, xp = (x + 1 == Lx) ? 0 : x + 1;
-    const int ym = (y == 0 ? Ly : y) - 1, yp = (y + 1 == Ly) ? 0 : y + 1;
-    const int zm = (z == 0 ? Lz : z) - 1, zp = (z + 1 == Lz) ? 0 : z + 1;
-    double acc = 0.0;
-    static_for<L::Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int vx = L::v(i, 0), vy = L::v(i, 1), vz = L::v(i, 2);
-      const int xs = vx == 0 ? x : (vx > 0 ? xm : xp);
-      const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
-      const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
-      const int64_t so = xs + static_cast<int64_t>(Lx) * (ys + static_cast<int64_t>(Ly) * zs);
-      acc += Store<S>::getd(g[i * N + so], L::w(i) * rho_mean);
-    });
-    rho[s] = acc;
-  }
-}
-
-static cudaError_t launch_density_of_state(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly,
-                                           int32_t Lz, double rho_mean, double *rho, cudaStream_t stream) {
-  return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
-    constexpr int LAT = decltype(lat)::value;
-    using S = typename decltype(tag)::type;
-    const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
-    const int64_t blocks = (N + 255) / 256;
-    const int grid = static_cast<int>(blocks < 152 * 16 ? blocks : 152 * 16);
-    k_density_of_state<LAT, S><<<grid, 256, 0, stream>>>(static_cast<const S *>(g), Lx, Ly, Lz, rho_mean, rho);
-    return cudaGetLastError();
-  });
-}
-
-}  // namespace lbfd
 
 namespace {
 
