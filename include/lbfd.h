@@ -247,7 +247,8 @@ int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void *f_dev, int
  * same noise keys).  Members share one precision, noise mode and law, and
  * each member has Q * sites < 2^32.  Work decomposition: a work item is 1
  * or 2 sites of a row (2 only where Lx is even), a tile is `passes` x 256
- * items of one member, and a persistent grid walks the tiles. */
+ * items of one member, and the tiles go to blocks in one of the orders
+ * LBFD_WALK_* (see lbfd_ensemble_tune / lbfd_ensemble_plan). */
 typedef struct lbfd_member {
     int64_t dims[3];    /* Lx, Ly, Lz; trailing dims of lower-D lattices must be 1 */
     double tau;         /* > 1/2 */
@@ -359,7 +360,8 @@ typedef struct lbfd_server_options {
     int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
     int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
     int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
-    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_* */
+    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_STRIDED, _CONTIGUOUS or
+                               _PER_TILE (LBFD_WALK_PARAM is for ensembles only) */
     int32_t vx_max;         /* sites per work item of the batched kernel at most: 2 (members with even Lx
                                take two) or 1 (a kernel without the two-site path, fewer registers) */
     int32_t reserved[5];

@@ -114,7 +114,8 @@ static cudaError_t ens_launch(lbfd_ens *e) {
 }
 
 // Work decomposition (sites per item, tile passes, occupancy variant, tile
-// order) and persistent grid.
+// order), the grid of the persistent orders and the parameter blocks of the
+// parameter-bank order.
 static int ens_plan(lbfd_ens *e, int vx_max, int passes, int occ, int walk) {
   e->kvx = 1;
   for (BatchMember &m : e->hmem) {

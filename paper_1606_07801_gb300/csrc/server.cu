@@ -13,7 +13,8 @@
 // One time step (tick) of the server, on the compute stream:
 //   [table upload, when the resident set changed]  one copy from pinned staging
 //   k_batch_prep                                   step arguments of every member
-//   k_batch_step per lattice type                  one launch covers all members of that type
+//   batched step per lattice type                  one launch covers all members of that type
+//                                                  (k_batch_tile or k_batch_step, by the walk option)
 //   k_step per simulation of >= solo_sites sites   the single-lattice kernel, parameters as
 //                                                  kernel arguments
 // (forked onto side streams when there is more than one launch, joined after)
@@ -575,7 +576,7 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.vx_max != 1 && o.vx_max != 2) return srv_fail(LBFD_EINVAL, "server: vx_max must be 1 or 2");
   if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS && o.walk != LBFD_WALK_PER_TILE)
-    return srv_fail(LBFD_EINVAL, "server: walk must be one of LBFD_WALK_*");
+    return srv_fail(LBFD_EINVAL, "server: walk must be LBFD_WALK_STRIDED, _CONTIGUOUS or _PER_TILE");
   if (o.max_active_sites < 0) return srv_fail(LBFD_EINVAL, "server: max_active_sites must be >= 0");
   if (o.solo_sites < 0) return srv_fail(LBFD_EINVAL, "server: solo_sites must be >= 0");
   int dev = o.device;
