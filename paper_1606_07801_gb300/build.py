@@ -21,7 +21,11 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbfd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# -ffp-contract=off: the host compiler may not fuse a multiply and an add
+# into an FMA (its default on Arm), so host-side decoding and parameter
+# arithmetic round the same way at every call site and on every host.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE,
+         "-I", CSRC]
 
 
 def _nvcc() -> str:

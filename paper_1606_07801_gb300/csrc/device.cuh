@@ -30,6 +30,47 @@ enum NoiseDist : int { kGaussian = 0, kUniform = 1 };
 // ---------------------------------------------------------------------------
 enum StorageId : int { kStoreF32 = 0, kStoreF64 = 1, kStoreF16 = 2, kStoreBF16 = 3 };
 
+// Rounded adds, subtracts and multiplies that the device compiler may not
+// fuse into an FMA with a neighbouring operation: the offset w_i rho_mean and
+// its add to a decoded deviation then round the same way in every kernel, so
+// a lattice evolves bit-identically whichever kernel steps it.  (The library's
+// host code is compiled with FMA contraction off.)
+__host__ __device__ __forceinline__ float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;  // host code is compiled without FMA contraction
+#endif
+}
+__host__ __device__ __forceinline__ float sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;  // host code is compiled without FMA contraction
+#endif
+}
+__host__ __device__ __forceinline__ float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;  // host code is compiled without FMA contraction
+#endif
+}
+__host__ __device__ __forceinline__ double add_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;  // host code is compiled without FMA contraction
+#endif
+}
+__host__ __device__ __forceinline__ double sub_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dsub_rn(a, b);
+#else
+  return a - b;  // host code is compiled without FMA contraction
+#endif
+}
+
 template <typename S>
 struct Store;
 template <>
@@ -54,28 +95,30 @@ template <>
 struct Store<__half> {
   using R = float;
   static constexpr bool kDeviation = true;
-  __host__ __device__ static __forceinline__ float get(__half v, float wr) { return __half2float(v) + wr; }
-  __host__ __device__ static __forceinline__ __half put(float f, float wr) { return __float2half_rn(f - wr); }
+  __host__ __device__ static __forceinline__ float get(__half v, float wr) { return add_rn(__half2float(v), wr); }
+  __host__ __device__ static __forceinline__ __half put(float f, float wr) { return __float2half_rn(sub_rn(f, wr)); }
   __host__ __device__ static __forceinline__ double getd(__half v, double wr) {
-    return static_cast<double>(__half2float(v)) + wr;
+    return add_rn(static_cast<double>(__half2float(v)), wr);
   }
   __host__ __device__ static __forceinline__ __half putd(double f, double wr) {
-    return __float2half_rn(static_cast<float>(f - wr));
+    return __float2half_rn(static_cast<float>(sub_rn(f, wr)));
   }
 };
 template <>
 struct Store<__nv_bfloat16> {
   using R = float;
   static constexpr bool kDeviation = true;
-  __host__ __device__ static __forceinline__ float get(__nv_bfloat16 v, float wr) { return __bfloat162float(v) + wr; }
+  __host__ __device__ static __forceinline__ float get(__nv_bfloat16 v, float wr) {
+    return add_rn(__bfloat162float(v), wr);
+  }
   __host__ __device__ static __forceinline__ __nv_bfloat16 put(float f, float wr) {
-    return __float2bfloat16_rn(f - wr);
+    return __float2bfloat16_rn(sub_rn(f, wr));
   }
   __host__ __device__ static __forceinline__ double getd(__nv_bfloat16 v, double wr) {
-    return static_cast<double>(__bfloat162float(v)) + wr;
+    return add_rn(static_cast<double>(__bfloat162float(v)), wr);
   }
   __host__ __device__ static __forceinline__ __nv_bfloat16 putd(double f, double wr) {
-    return __float2bfloat16_rn(static_cast<float>(f - wr));
+    return __float2bfloat16_rn(static_cast<float>(sub_rn(f, wr)));
   }
 };
 

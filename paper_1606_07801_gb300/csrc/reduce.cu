@@ -283,7 +283,7 @@ constexpr int kObsThreads = 256;
 
 template <int LAT>
 __device__ __forceinline__ float obs_offset(int i, float rho_f) {
-  return static_cast<float>(Lattice<LAT>::w(i)) * rho_f;
+  return mul_rn(static_cast<float>(Lattice<LAT>::w(i)), rho_f);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
         const uint32_t zs = vz == 0 ? z : (vz > 0 ? zm : zp);
         const S v = g[static_cast<size_t>(i) * N + xs + Lxu * ys + Lxy * zs];
         // 16-bit formats store the deviation itself; FP32 stores f
-        e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f) : Store<S>::get(v, 0.0f) - obs_offset<LAT>(i, rho_f);
+        e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f) : sub_rn(Store<S>::get(v, 0.0f), obs_offset<LAT>(i, rho_f));
         delta += e[i];
       });
       e[Q] = 1.0f;

@@ -72,7 +72,7 @@ template <int LAT, typename S>
 __device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepArgs &a) {
   using R = typename Store<S>::R;
   if constexpr (Store<S>::kDeviation)
-    return static_cast<R>(Lattice<LAT>::w(i)) * step_param<R>(a.rho_eq, a.rho_eq_f);
+    return mul_rn(static_cast<R>(Lattice<LAT>::w(i)), step_param<R>(a.rho_eq, a.rho_eq_f));
   else
     return R(0);
 }

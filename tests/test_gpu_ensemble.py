@@ -79,6 +79,22 @@ def test_every_decomposition_bit_identical(lat, vx, passes, occ, walk):
         assert np.array_equal(got[m], _alone(lat, sp, lb.F32, 19)), m
 
 
+@pytest.mark.parametrize("lat,precision,walk", [(lb.D1Q3, lb.F64, lb.WALK_PARAM), (lb.D2Q9, lb.F32_F16, lb.WALK_PARAM),
+                                                (lb.D3Q19, lb.F32_BF16, lb.WALK_PARAM), (lb.D2Q9, lb.F64, lb.WALK_PER_TILE),
+                                                (lb.D1Q3, lb.F32, lb.WALK_CONTIGUOUS)])
+def test_tile_orders_bit_identical_in_every_format(lat, precision, walk):
+    """The parameter-bank and other tile orders in the FP64 and 16-bit
+    formats and on D1Q3: members equal the same lattices stepped alone.  Over
+    112 members so that the parameter order takes more than one launch."""
+    specs = _specs(lat, 130, seed=lat * 7 + precision)
+    with lb.Ensemble(lat, specs, precision=precision) as e:
+        e.plan(2, 2, 0, walk)
+        e.step(18)
+        got = [e.get_f(m) for m in range(0, len(specs), 9)]
+    for k, m in enumerate(range(0, len(specs), 9)):
+        assert np.array_equal(got[k], _alone(lat, specs[m], precision, 18)), m
+
+
 def test_plan_rejects_bad_values():
     specs = _specs(lb.D2Q9, 2, seed=1)
     with lb.Ensemble(lb.D2Q9, specs) as e:
