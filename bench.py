@@ -62,11 +62,11 @@ BATCH_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_078
 
 
 def _code_only(text: str) -> str:
-    """Source text without comments and blank lines, so that editing a comment
-    does not invalidate a committed capture of unchanged code."""
+    """Source text without comments and whitespace, so that editing a comment
+    or the layout does not invalidate a committed capture of unchanged code."""
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     text = re.sub(r"//[^\n]*", "", text)
-    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+    return re.sub(r"\s+", "", text)
 
 
 def kernel_hash(sources=KERNEL_SOURCES) -> str:

@@ -39,14 +39,14 @@ cudaError_t launch_batch_step(int lattice, int precision, void *base, const Batc
                               int noise_dist, int grid, cudaStream_t stream) {
   switch (lattice) {
     case kD1Q3:
-      return launch_batch_step_d1q3(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
-                                    noise_dist, grid, stream);
+      return launch_batch_step_d1q3(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max,
+                                    noise_mode, noise_dist, grid, stream);
     case kD2Q9:
-      return launch_batch_step_d2q9(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
-                                    noise_dist, grid, stream);
+      return launch_batch_step_d2q9(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max,
+                                    noise_mode, noise_dist, grid, stream);
     case kD3Q19:
-      return launch_batch_step_d3q19(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
-                                     noise_dist, grid, stream);
+      return launch_batch_step_d3q19(precision, base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max,
+                                     noise_mode, noise_dist, grid, stream);
   }
   return cudaErrorInvalidValue;
 }

@@ -5,13 +5,12 @@
 namespace lbfd {
 
 cudaError_t launch_batch_step_d1q3(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
-                                 int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist,
-                                 int grid,
-                                 cudaStream_t stream) {
+                                 int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max,
+                                 int noise_mode, int noise_dist, int grid, cudaStream_t stream) {
   return dispatch_storage(precision, [&](auto tag) {
     using S = typename decltype(tag)::type;
-    return batch_step_t<kD1Q3, S>(base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode, noise_dist, grid,
-                                  stream);
+    return batch_step_t<kD1Q3, S>(base, steps, tile_start, nmembers, ntiles, passes, occ, walk, vx_max, noise_mode,
+                                  noise_dist, grid, stream);
   });
 }
 

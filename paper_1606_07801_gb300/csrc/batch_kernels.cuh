@@ -295,8 +295,8 @@ template <int LAT, typename S, int NOISE, int OCC, int VXMAX>
 cudaError_t batch_step_k(S *b, const BatchStep *steps, const int64_t *tile_start, int nmembers, int ntiles, int passes,
                          int walk, int grid, cudaStream_t stream) {
   if (walk == kWalkPerTile)
-    k_batch_tile<LAT, S, NOISE, OCC, VXMAX><<<ntiles, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
-                                                                                  passes);
+    k_batch_tile<LAT, S, NOISE, OCC, VXMAX><<<ntiles, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers,
+                                                                                  ntiles, passes);
   else
     k_batch_step<LAT, S, NOISE, OCC, VXMAX><<<grid, kBatchThreads, 0, stream>>>(b, steps, tile_start, nmembers, ntiles,
                                                                                 passes, walk);

@@ -185,14 +185,14 @@ int set_last_error(int code, const std::string &msg);
 struct BatchMember;
 struct BatchStep;
 cudaError_t launch_batch_step_d1q3(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
-                                   int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
-                                   cudaStream_t stream);
+                                   int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max,
+                                   int noise_mode, int noise_dist, int grid, cudaStream_t stream);
 cudaError_t launch_batch_step_d2q9(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
-                                   int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
-                                   cudaStream_t stream);
+                                   int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max,
+                                   int noise_mode, int noise_dist, int grid, cudaStream_t stream);
 cudaError_t launch_batch_step_d3q19(int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
-                                    int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
-                                    cudaStream_t stream);
+                                    int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max,
+                                    int noise_mode, int noise_dist, int grid, cudaStream_t stream);
 struct BatchParams;
 cudaError_t launch_batch_param_d1q3(int precision, void *base, const BatchParams *groups, int ngroups,
                                     const BatchStep *steps, int passes, int occ, int vx_max, int noise_mode,
@@ -213,8 +213,8 @@ int batch_blocks_per_sm_d3q19(int precision, int occ, int vx_max, int walk, int 
 // tile (grid ignored); vx_max: the largest sites
 // per item of any member (1 selects a kernel without the two-site path).
 cudaError_t launch_batch_step(int lattice, int precision, void *base, const BatchStep *steps, const int64_t *tile_start,
-                              int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode, int noise_dist, int grid,
-                              cudaStream_t stream);
+                              int nmembers, int64_t ntiles, int passes, int occ, int walk, int vx_max, int noise_mode,
+                              int noise_dist, int grid, cudaStream_t stream);
 // One launch per group of at most kParamMembers members, their arguments in
 // the kernel parameters (tile order 3); steps holds k_batch_prep's output.
 cudaError_t launch_batch_param(int lattice, int precision, void *base, const BatchParams *groups, int ngroups,

@@ -407,7 +407,8 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
         const uint32_t zs = vz == 0 ? z : (vz > 0 ? zm : zp);
         const S v = g[static_cast<size_t>(i) * N + xs + Lxu * ys + Lxy * zs];
         // 16-bit formats store the deviation itself; FP32 stores f
-        e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f) : sub_rn(Store<S>::get(v, 0.0f), obs_offset<LAT>(i, rho_f));
+        e[i] = Store<S>::kDeviation ? Store<S>::get(v, 0.0f)
+                                    : sub_rn(Store<S>::get(v, 0.0f), obs_offset<LAT>(i, rho_f));
         delta += e[i];
       });
       e[Q] = 1.0f;
@@ -555,7 +556,8 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
   ModeArgs ma{};
   ma.n = n_modes;
   for (int m = 0; m < n_modes; ++m)
-    for (int k = 0; k < 3; ++k) ma.k[m][k] = static_cast<int32_t>(((int64_t(modes[3 * m + k]) % L3[k]) + L3[k]) % L3[k]);
+    for (int k = 0; k < 3; ++k)
+      ma.k[m][k] = static_cast<int32_t>(((int64_t(modes[3 * m + k]) % L3[k]) + L3[k]) % L3[k]);
   ObsDims dm{};
   dm.Lx = Lx;
   dm.Ly = Ly;

@@ -456,8 +456,8 @@ int tick(lbfd_server *s) {
     const int grid =
         int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L][vx - 1])));
     SRV_CU(launch_batch_step(L, s->opt.precision, s->arena, s->d_steps + s->seg_off[L], s->d_tile_start + s->seg_off[L],
-                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.walk, vx, s->opt.noise_mode,
-                             s->opt.noise_dist, grid, st));
+                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.walk, vx,
+                             s->opt.noise_mode, s->opt.noise_dist, grid, st));
     s->launches += 1;
     if (fork) {
       SRV_CU(cudaEventRecord(s->lat_ev[L], st));
