@@ -144,8 +144,10 @@ int lbfd_options_init(lbfd_options *o) {
 static int validate(const lbfd_options *o) {
   if (o->lattice < LBFD_D1Q3 || o->lattice > LBFD_D2Q5) return fail(LBFD_EINVAL, "unknown lattice");
   if (o->precision < LBFD_F32 || o->precision > LBFD_F32_BF16) return fail(LBFD_EINVAL, "unknown precision");
-  if (o->noise_mode < LBFD_NOISE_LOCAL || o->noise_mode > LBFD_NOISE_OFF) return fail(LBFD_EINVAL, "unknown noise mode");
-  if (o->noise_dist != LBFD_GAUSSIAN && o->noise_dist != LBFD_UNIFORM) return fail(LBFD_EINVAL, "unknown noise distribution");
+  if (o->noise_mode < LBFD_NOISE_LOCAL || o->noise_mode > LBFD_NOISE_OFF)
+    return fail(LBFD_EINVAL, "unknown noise mode");
+  if (o->noise_dist != LBFD_GAUSSIAN && o->noise_dist != LBFD_UNIFORM)
+    return fail(LBFD_EINVAL, "unknown noise distribution");
   if (o->init < LBFD_INIT_UNIFORM || o->init > LBFD_INIT_NONE) return fail(LBFD_EINVAL, "unknown init");
   const int D = lattice_dims(o->lattice);
   for (int a = 0; a < 3; ++a) {
@@ -157,10 +159,12 @@ static int validate(const lbfd_options *o) {
   const double n = double(o->dims[0]) * double(o->dims[1]) * double(o->dims[2]);
   if (n >= 2147483648.0) return fail(LBFD_EINVAL, "lattice has 2^31 sites or more");
   if (!(o->tau > 0.5) || !std::isfinite(o->tau)) return fail(LBFD_EINVAL, "tau must be a finite number > 1/2");
-  if (!(o->rho_mean >= 0.0) || !std::isfinite(o->rho_mean)) return fail(LBFD_EINVAL, "rho_mean must be finite and >= 0");
+  if (!(o->rho_mean >= 0.0) || !std::isfinite(o->rho_mean))
+    return fail(LBFD_EINVAL, "rho_mean must be finite and >= 0");
   if (!std::isfinite(o->sine_amp)) return fail(LBFD_EINVAL, "sine_amp must be finite");
   if (o->n_modes < 0 || o->n_modes > LBFD_MAX_MODES) return fail(LBFD_EINVAL, "n_modes out of range");
-  if ((o->f_dev[0] == nullptr) != (o->f_dev[1] == nullptr)) return fail(LBFD_EINVAL, "give both f_dev buffers or neither");
+  if ((o->f_dev[0] == nullptr) != (o->f_dev[1] == nullptr))
+    return fail(LBFD_EINVAL, "give both f_dev buffers or neither");
   if (o->lattice == LBFD_D2Q5) {
     if (!(o->theta == 0.0 || (o->theta > 0.0 && o->theta < 0.5)))
       return fail(LBFD_EINVAL, "theta of D2Q5 must be in (0, 1/2) (or 0 for 1/3)");

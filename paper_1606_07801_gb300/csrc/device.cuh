@@ -164,7 +164,9 @@ struct Lattice<kD2Q9> {
     constexpr int t[9][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}, {1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
     return a < 2 ? t[i][a] : 0;
   }
-  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
   // v_x^p v_y^q, p-major: a = 3p + q
   __host__ __device__ static constexpr int mono(int a, int k) { return k == 0 ? a / 3 : (k == 1 ? a % 3 : 0); }
 };
@@ -178,7 +180,9 @@ struct Lattice<kD3Q19> {
                               {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
     return t[i][a];
   }
-  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
   // v_x^p v_y^q v_z^r with p, q, r <= 2 and at most two of them non-zero,
   // by total degree, then (p, q, r) descending
   __host__ __device__ static constexpr int mono(int a, int k) {

@@ -200,7 +200,8 @@ int lbfd_ensemble_create(lbfd_ens_t *out, int32_t lattice, int32_t precision, in
   if (lattice < LBFD_D1Q3 || lattice > LBFD_D3Q19) return ens_fail(LBFD_EINVAL, "unknown lattice");
   if (precision < LBFD_F32 || precision > LBFD_F32_BF16) return ens_fail(LBFD_EINVAL, "unknown precision");
   if (noise_mode < LBFD_NOISE_LOCAL || noise_mode > LBFD_NOISE_OFF) return ens_fail(LBFD_EINVAL, "unknown noise mode");
-  if (noise_dist != LBFD_GAUSSIAN && noise_dist != LBFD_UNIFORM) return ens_fail(LBFD_EINVAL, "unknown noise distribution");
+  if (noise_dist != LBFD_GAUSSIAN && noise_dist != LBFD_UNIFORM)
+    return ens_fail(LBFD_EINVAL, "unknown noise distribution");
   const int D = d_of(lattice);
   int dev = 0;
   ENS_CU(cudaGetDevice(&dev));

@@ -79,7 +79,9 @@ inline cudaError_t dispatch_lattice(int lattice, F &&f) {
 }
 template <class F>
 inline cudaError_t dispatch_lattice_storage(int lattice, int precision, F &&f) {
-  return dispatch_lattice(lattice, [&](auto lat) { return dispatch_storage(precision, [&](auto tag) { return f(lat, tag); }); });
+  return dispatch_lattice(lattice, [&](auto lat) {
+    return dispatch_storage(precision, [&](auto tag) { return f(lat, tag); });
+  });
 }
 
 // Bytes of one stored value for a storage id.

@@ -143,6 +143,7 @@ extern "C" int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void 
               : mass_tiles<kD3Q19, float>(f_dev, n_sites, scratch, mass_dev, s);
       break;
   }
-  if (e != cudaSuccess) return set_last_error(LBFD_ECUDA, std::string("lbfd_mass_noalloc: launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return set_last_error(LBFD_ECUDA, std::string("lbfd_mass_noalloc: launch: ") + cudaGetErrorString(e));
   return LBFD_OK;
 }

@@ -216,12 +216,14 @@ int prepare_request(lbfd_server *s, const lbfd_request &r, SrvRequest &q, bool i
   if (sites >= 2147483648.0) return srv_fail(LBFD_EINVAL, "request: 2^31 sites or more");
   if (double(q_of(r.lattice)) * sites > 4294967295.0) return srv_fail(LBFD_EINVAL, "request: Q * sites must be < 2^32");
   if (!(r.tau > 0.5) || !std::isfinite(r.tau)) return srv_fail(LBFD_EINVAL, "request: tau must be > 1/2");
-  if (!(r.rho_mean >= 0.0) || !std::isfinite(r.rho_mean)) return srv_fail(LBFD_EINVAL, "request: rho_mean must be >= 0");
+  if (!(r.rho_mean >= 0.0) || !std::isfinite(r.rho_mean))
+    return srv_fail(LBFD_EINVAL, "request: rho_mean must be >= 0");
   if (r.steps < 0) return srv_fail(LBFD_EINVAL, "request: steps must be >= 0");
   if (r.init != LBFD_INIT_UNIFORM && r.init != LBFD_INIT_SINE && r.init != LBFD_INIT_HOST)
     return srv_fail(LBFD_EINVAL, "request: init must be LBFD_INIT_UNIFORM, LBFD_INIT_SINE or LBFD_INIT_HOST");
   if (r.init == LBFD_INIT_HOST && !r.in_host) return srv_fail(LBFD_EINVAL, "request: LBFD_INIT_HOST needs in_host");
-  if (r.result < LBFD_RESULT_F || r.result > LBFD_RESULT_NONE) return srv_fail(LBFD_EINVAL, "request: unknown result kind");
+  if (r.result < LBFD_RESULT_F || r.result > LBFD_RESULT_NONE)
+    return srv_fail(LBFD_EINVAL, "request: unknown result kind");
   q.r = r;
   q.Q = q_of(r.lattice);
   q.N = int64_t(sites);
@@ -568,11 +570,13 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   if (o.noise_dist != LBFD_GAUSSIAN && o.noise_dist != LBFD_UNIFORM)
     return srv_fail(LBFD_EINVAL, "server: unknown noise distribution");
   if (o.hbm_budget < kAlign) return srv_fail(LBFD_EINVAL, "server: hbm_budget too small");
-  if (o.max_active < 1 || o.max_active > kMaxSlots) return srv_fail(LBFD_EINVAL, "server: max_active must be in [1, 65536]");
+  if (o.max_active < 1 || o.max_active > kMaxSlots)
+    return srv_fail(LBFD_EINVAL, "server: max_active must be in [1, 65536]");
   if (o.max_ahead < 1 || o.max_ahead > 1024) return srv_fail(LBFD_EINVAL, "server: max_ahead must be in [1, 1024]");
   if (o.passes != 1 && o.passes != 2 && o.passes != 4 && o.passes != 8)
     return srv_fail(LBFD_EINVAL, "server: passes must be 1, 2, 4 or 8");
-  if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST) return srv_fail(LBFD_EINVAL, "server: unknown policy");
+  if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST)
+    return srv_fail(LBFD_EINVAL, "server: unknown policy");
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.vx_max != 1 && o.vx_max != 2) return srv_fail(LBFD_EINVAL, "server: vx_max must be 1 or 2");
   if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS && o.walk != LBFD_WALK_PER_TILE)
@@ -716,7 +720,8 @@ int lbfd_server_run_trace(lbfd_server_t s, const lbfd_request *reqs, const doubl
   if (!s || n < 0 || (n > 0 && (!reqs || !arrival_s || !latency_s)) || sink_bytes < 0 || (sink_bytes > 0 && !sink_host))
     return srv_fail(LBFD_EINVAL, "lbfd_server_run_trace: bad argument");
   for (int32_t k = 1; k < n; ++k)
-    if (!(arrival_s[k] >= arrival_s[k - 1])) return srv_fail(LBFD_EINVAL, "lbfd_server_run_trace: arrivals must not decrease");
+    if (!(arrival_s[k] >= arrival_s[k - 1]))
+      return srv_fail(LBFD_EINVAL, "lbfd_server_run_trace: arrivals must not decrease");
   if (s->sink_pool) return srv_fail(LBFD_EBUSY, "lbfd_server_run_trace: a trace is already running");
   DevScope scope(s->device);
   s->sink = static_cast<char *>(sink_host);

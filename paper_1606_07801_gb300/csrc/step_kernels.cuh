@@ -119,7 +119,9 @@ __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *_
 // blocks take the SM slots that this step's last blocks free; each block then
 // waits for the previous grid's completion (and memory) before its first
 // load.  Without the launch attribute both instructions do nothing.
-__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Scalar kernel: one site per thread, any lattice shape.
@@ -224,7 +226,9 @@ __global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
 }
 
 // True when every value offset i N + site of a lattice fits 32 bits.
-inline bool offsets_fit_32(int Q, int64_t N) { return static_cast<uint64_t>(Q) * static_cast<uint64_t>(N) <= 0xffffffffull; }
+inline bool offsets_fit_32(int Q, int64_t N) {
+  return static_cast<uint64_t>(Q) * static_cast<uint64_t>(N) <= 0xffffffffull;
+}
 
 inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block, int vx = 1) {
   const int cols = Lx / vx;
