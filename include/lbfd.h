@@ -77,6 +77,18 @@ extern "C" {
 #define LBFD_MAX_Q 19
 #define LBFD_MAX_MODES 16
 
+/* ---- step kernels (lbfd_options.step_kernel, lbfd_step_kernel) ---------------
+ * Every kernel computes the same site update with the same arithmetic, so the
+ * choice changes speed only, never a result bit. */
+#define LBFD_KERNEL_AUTO 0    /* the library's choice (option value only) */
+#define LBFD_KERNEL_VEC 1     /* k_step_vec: two sites of a row per thread, pulled straight from global memory
+                                 (Lx even) */
+#define LBFD_KERNEL_SCALAR 2  /* k_step: one site per thread (any Lx) */
+#define LBFD_KERNEL_SMALL 3   /* k_step_small: many steps per launch in one block's shared memory (small
+                                 lattices, n >= 2; chosen automatically) */
+#define LBFD_KERNEL_CLUSTER 4 /* k_step_cluster: the same over a thread-block cluster (chosen automatically) */
+#define LBFD_KERNEL_MRT 5     /* k_step_mrt: moment-space collision (D2Q5, multiple relaxation times) */
+
 /* Options of lbfd_create_ex.  Fill with lbfd_options_init, then override. */
 typedef struct lbfd_options {
     int32_t lattice;    /* LBFD_D1Q3 / LBFD_D2Q9 / LBFD_D3Q19 */
@@ -97,7 +109,10 @@ typedef struct lbfd_options {
                            storage format; both or neither.  Never freed by the library. */
     int32_t n_modes;    /* structure-factor wave vectors sampled by lbfd_sample */
     int32_t modes[LBFD_MAX_MODES][3];
-    int32_t reserved[8];
+    int32_t step_kernel; /* LBFD_KERNEL_AUTO, or LBFD_KERNEL_VEC / LBFD_KERNEL_SCALAR to ask for that
+                            kernel for the one-launch-per-step path (LBFD_KERNEL_VEC needs Lx even).
+                            Small lattices still take the many-steps-per-launch path. */
+    int32_t reserved[7];
     double theta;       /* D2Q5: sum_i w_i v_ix^2, in (0, 1/2); 0 = 1/3.  Other lattices: 0 or 1/3 */
     double tau_moments[LBFD_MAX_Q]; /* multiple relaxation times (Sec. III): tau^a of moment a of
                            the basis, a = 1..Q-1 (entry 0, the conserved density, is ignored);
@@ -141,6 +156,10 @@ int lbfd_destroy(lbfd_t h);
 /* Advances the state by n >= 0 steps of eq. LB (collide, add noise,
  * stream).  Asynchronous on the handle's stream; t advances by n. */
 int lbfd_step(lbfd_t h, int64_t n);
+
+/* The kernel lbfd_step(h, n) would run for this n (one of LBFD_KERNEL_VEC ..
+ * LBFD_KERNEL_MRT), into *kernel.  No device work. */
+int lbfd_step_kernel(lbfd_t h, int64_t n, int32_t *kernel);
 
 /* Waits for all work queued on the handle's stream. */
 int lbfd_sync(lbfd_t h);
@@ -232,7 +251,11 @@ int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t
  * loading the library holds until exit, so n_sites is limited to 16,777,216
  * (LBFD_EINVAL beyond).  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call overwrites the partials it reads, so no state
+ * stream capture.  A failed lookup is not remembered: the next call tries
+ * again.  A CUDA error still pending on the calling thread from earlier work
+ * is reported as LBFD_ECUDA before anything is launched (and cleared), so a
+ * launch failure reported here is always this call's own.  Every call
+ * overwrites the partials it reads, so no state
  * carries over, but all calls share the array: calls whose kernels overlap
  * on the GPU race and may return wrong sums; order them on one stream. */
 int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void *f_dev, int64_t n_sites, double *mass_dev,

@@ -47,8 +47,10 @@ class Simulation:
     def __init__(self, lattice: int, dims, tau: float, rho_mean: float, seed: int = 1, *, precision: int = F32,
                  noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN, init: int = INIT_UNIFORM,
                  sine_amp: float = 0.0, sine_k=(1, 0, 0), lattice_id: int = 0, modes=(), stream=None,
-                 torch_buffers: bool = False, device: int = -1, theta: float = 0.0, tau_moments=None):
+                 torch_buffers: bool = False, device: int = -1, theta: float = 0.0, tau_moments=None,
+                 step_kernel: int = 0):
         o = abi.lbfd_options_init()
+        o.step_kernel = int(step_kernel)
         o.lattice, o.precision, o.noise_mode, o.noise_dist, o.init = lattice, precision, noise_mode, noise_dist, init
         d = [int(x) for x in dims] + [1] * (3 - len(dims))
         for a in range(3):
@@ -112,6 +114,10 @@ class Simulation:
 
     def sync(self) -> None:
         abi.lbfd_sync(self.h)
+
+    def kernel(self, n: int = 1) -> str:
+        """Name of the kernel that step(n) runs."""
+        return abi.KERNEL_NAMES[abi.lbfd_step_kernel(self.h, n)]
 
     @property
     def t(self) -> int:

@@ -183,7 +183,28 @@ static int validate(const lbfd_options *o) {
   if (mrt && double(lattice_q(o->lattice)) * n > 4294967295.0)
     return fail(LBFD_ENOTSUP, "D2Q5 and multiple relaxation times need Q * sites < 2^32");
   if (o->f_dev[0] && o->f_dev[0] == o->f_dev[1]) return fail(LBFD_EINVAL, "the two f_dev buffers must differ");
+  if (o->step_kernel != LBFD_KERNEL_AUTO && o->step_kernel != LBFD_KERNEL_VEC && o->step_kernel != LBFD_KERNEL_SCALAR)
+    return fail(LBFD_EINVAL, "step_kernel must be LBFD_KERNEL_AUTO, LBFD_KERNEL_VEC or LBFD_KERNEL_SCALAR");
+  if (o->step_kernel == LBFD_KERNEL_VEC && o->dims[0] % 2 != 0)
+    return fail(LBFD_EINVAL, "LBFD_KERNEL_VEC needs an even Lx");
+  for (int k = 0; k < 7; ++k)
+    if (o->reserved[k] != 0) return fail(LBFD_EINVAL, "reserved option fields must be 0");
   return LBFD_OK;
+}
+
+// The kernel lbfd_step(h, n) runs.  The small-lattice paths hold many steps
+// per launch, so they need n >= 2; otherwise one launch per step.
+static int step_path(const lbfd_sim *h, int64_t n) {
+  const lbfd_options &o = h->opt;
+  if (h->mrt) return LBFD_KERNEL_MRT;
+  if (n >= 2) {
+    const int ctas = small_path_ctas(o.lattice, o.precision, h->N);
+    if (ctas == 1) return LBFD_KERNEL_SMALL;
+    if (ctas > 1) return LBFD_KERNEL_CLUSTER;
+  }
+  if (o.step_kernel == LBFD_KERNEL_SCALAR) return LBFD_KERNEL_SCALAR;
+  if (o.step_kernel == LBFD_KERNEL_VEC) return LBFD_KERNEL_VEC;
+  return step_vec_width(int32_t(o.dims[0])) == 2 ? LBFD_KERNEL_VEC : LBFD_KERNEL_SCALAR;
 }
 
 static void free_sim(lbfd_sim *h) {
@@ -316,7 +337,8 @@ int lbfd_step(lbfd_t h, int64_t n) {
   fill_step_params(a, o.tau, o.rho_mean);
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
-  if (!h->mrt && n >= 2 && small_path_fits(o.lattice, o.precision, h->N)) {
+  const int path = step_path(h, n);
+  if (path == LBFD_KERNEL_SMALL || path == LBFD_KERNEL_CLUSTER) {
     // a small lattice: many steps per launch in shared memory (bit-identical)
     constexpr int64_t kChunk = 4096;
     int64_t launches = 0, done = 0;
@@ -343,16 +365,23 @@ int lbfd_step(lbfd_t h, int64_t n) {
     if (placed) return LBFD_OK;
     n -= done;
   }
+  const int vec_width = step_path(h, 1) == LBFD_KERNEL_VEC ? 2 : 1;
   for (int64_t k = 0; k < n; ++k) {
     a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
     cudaError_t e = h->mrt ? launch_step_mrt(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->m, h->w,
                                              h->tau_m, h->stream)
-                           : launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream);
+                           : launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream, vec_width);
     if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
     h->cur ^= 1;
     h->t += 1;
   }
   g_launches.fetch_add(n, std::memory_order_relaxed);
+  return LBFD_OK;
+}
+
+int lbfd_step_kernel(lbfd_t h, int64_t n, int32_t *kernel) {
+  if (!h || !kernel || n < 0) return fail(LBFD_EINVAL, "lbfd_step_kernel: bad argument");
+  *kernel = step_path(h, n);
   return LBFD_OK;
 }
 

@@ -354,9 +354,28 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
   const int pass_cand[4] = {1, 2, 4, 8};
   float best_ms = -1.0f;
   int best_vx = e->vx_max, best_passes = e->passes, best_occ = e->occ, best_walk = e->walk;
-  cudaEvent_t a = nullptr, b = nullptr;
-  ENS_CU(cudaEventCreate(&a));
-  ENS_CU(cudaEventCreate(&b));
+  // On every early exit: destroy the timing events and put the plan the
+  // ensemble had before tuning back (the error of the failed call stays the
+  // thread's lbfd_last_error()).
+  struct TuneGuard {
+    lbfd_ens *e;
+    int vx, passes, occ, walk;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool finished = false;
+    ~TuneGuard() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (!finished) {
+        const std::string err = lbfd_last_error();
+        (void)ens_plan(e, vx, passes, occ, walk);
+        (void)cudaGetLastError();
+        set_last_error(LBFD_ECUDA, err);
+      }
+    }
+  } guard{e, e->vx_max, e->passes, e->occ, e->walk};
+  ENS_CU(cudaEventCreate(&guard.a));
+  ENS_CU(cudaEventCreate(&guard.b));
+  cudaEvent_t a = guard.a, b = guard.b;
   // timing launches read the state and write the spare block only (t is not advanced)
   int64_t launched = 0;
   for (int walk = 0; walk < 4; ++walk) {
@@ -385,11 +404,10 @@ int lbfd_ensemble_tune(lbfd_ens_t e, int32_t steps, int32_t *vx_chosen, int32_t 
       }
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   count_launches(launched);
   int rc = ens_plan(e, best_vx, best_passes, best_occ, best_walk);
   if (rc) return rc;
+  guard.finished = true;
   if (vx_chosen) *vx_chosen = best_vx;
   if (passes_chosen) *passes_chosen = best_passes;
   if (blocks_per_sm) *blocks_per_sm = e->bps;

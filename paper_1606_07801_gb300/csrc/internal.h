@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
 #include <string>
 
 #include <nvtx3/nvToolsExt.h>
@@ -95,14 +96,37 @@ __host__ __device__ __forceinline__ double step_param<double>(double d, float) {
 template <>
 __host__ __device__ __forceinline__ float step_param<float>(double, float f) { return f; }
 
-// Per-lattice step launchers (one translation unit each).
-cudaError_t launch_step_d1q3(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream);
-cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream);
-cudaError_t launch_step_d3q19(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream);
+// Sites per thread of the register-pull step kernel: 2 where Lx is even (the
+// vector kernel k_step_vec), else 1 (k_step).  A tuning knob only; results
+// do not depend on it.  LBFD_STEP_VX = 1 forces one site per thread.
+inline int step_vec_width(int32_t Lx) {
+  static int forced = [] {
+    const char *e = getenv("LBFD_STEP_VX");
+    const int r = e ? atoi(e) : 0;
+    return (r == 1 || r == 2) ? r : 0;
+  }();
+  const int vx = forced ? forced : 2;
+  return Lx % vx == 0 ? vx : 1;
+}
 
-// One step of eq. LB from src to dst (pull streaming, two buffers).
+// CTAs of the many-steps-per-launch path for a small lattice: 1 = one block
+// (k_step_small), 2..8 = a thread-block cluster (k_step_cluster), 0 = the
+// lattice does not fit it (or its lattice type has no such path).
+int small_path_ctas(int lattice, int precision, int64_t N);
+
+// Per-lattice step launchers (one translation unit each).  vec_width: 2
+// runs k_step_vec (Lx even), 1 runs k_step.
+cudaError_t launch_step_d1q3(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream,
+                             int vec_width);
+cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream,
+                             int vec_width);
+cudaError_t launch_step_d3q19(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream,
+                              int vec_width);
+
+// One step of eq. LB from src to dst (pull streaming, two buffers); by
+// default with the library's choice of sites per thread.
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
-                        cudaStream_t stream);
+                        cudaStream_t stream, int vec_width = 0);
 
 // Streaming shift between the stored post-collision state g and the
 // paper's f: dir = +1 gives f_i(x) = g_i(x - v_i), dir = -1 the inverse.

@@ -9,7 +9,8 @@
 // takes the caller's population array and a caller-owned output slot, and
 // keeps its per-block partial sums in a file-scope device array instead of
 // allocating scratch.  The first call on each device looks up that array's
-// device address; make that first call before any stream capture.
+// device address; make that first call before any stream capture.  A lookup
+// that fails is not remembered: the next call on that device tries again.
 //
 // The scratch array is kNoAllocMaxBlocks doubles (128 KiB).  Every GPU that
 // loads this library holds it until the process exits.  One block reduces
@@ -82,33 +83,48 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_mass_tile_total(const doubl
   if (threadIdx.x == 0) *out = lane_tot[0];
 }
 
+// Launches both stages.  The caller has cleared the thread's last runtime
+// error, so the check after each launch sees only that launch's own error.
 template <int LAT, typename R>
 static cudaError_t mass_tiles(const void *f, int64_t N, double *scratch, double *out, cudaStream_t stream) {
   const int nblocks = static_cast<int>((N + kSitesPerBlock - 1) / kSitesPerBlock);
   k_mass_tile_partials<LAT, R><<<nblocks, kNoAllocThreads, 0, stream>>>(static_cast<const R *>(f), N, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_mass_tile_total<<<1, kNoAllocThreads, 0, stream>>>(scratch, nblocks, out);
   return cudaGetLastError();
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current.
+// Device address of the scratch array, looked up with the device current
+// and cached per device once the lookup has succeeded.  A failed lookup (for
+// example one made during a stream capture) is not cached, so a later call
+// tries again.
 static double *g_scratch_addr[kNoAllocMaxDevices] = {};
-static std::once_flag g_scratch_once[kNoAllocMaxDevices];
-static cudaError_t g_scratch_err[kNoAllocMaxDevices] = {};
+static std::mutex g_scratch_mutex;
 
 static cudaError_t scratch_for_current_device(double **ptr) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
-  std::call_once(g_scratch_once[dev], [dev]() {
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
     void *p = nullptr;
-    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = static_cast<double *>(p);
-  });
-  if (g_scratch_err[dev] != cudaSuccess) return g_scratch_err[dev];
+  }
   *ptr = g_scratch_addr[dev];
   return cudaSuccess;
+}
+
+// Records a failed CUDA call as the thread's lbfd_last_error() and clears the
+// runtime's per-thread last error, so that the next launch check elsewhere
+// does not report it again.
+static int noalloc_cuda_fail(const char *what, cudaError_t e) {
+  (void)cudaGetLastError();
+  return set_last_error(LBFD_ECUDA, std::string("lbfd_mass_noalloc: ") + what + ": " + cudaGetErrorName(e) + " (" +
+                                        cudaGetErrorString(e) + ")");
 }
 
 }  // namespace lbfd
@@ -125,8 +141,11 @@ extern "C" int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void 
                           "lbfd_mass_noalloc: n_sites must be between 1 and 16777216, the capacity of its fixed scratch");
   double *scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
-  if (e != cudaSuccess)
-    return set_last_error(LBFD_ECUDA, std::string("lbfd_mass_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return noalloc_cuda_fail("cudaGetSymbolAddress", e);
+  // an error left on this thread by earlier, unrelated work is not this
+  // call's: report it as such before launching anything
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_cuda_fail("earlier CUDA error pending on this thread", e);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool f64 = precision == LBFD_F64;
   switch (lattice) {
@@ -143,7 +162,6 @@ extern "C" int lbfd_mass_noalloc(int32_t lattice, int32_t precision, const void 
               : mass_tiles<kD3Q19, float>(f_dev, n_sites, scratch, mass_dev, s);
       break;
   }
-  if (e != cudaSuccess)
-    return set_last_error(LBFD_ECUDA, std::string("lbfd_mass_noalloc: launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return noalloc_cuda_fail("launch", e);
   return LBFD_OK;
 }

@@ -24,11 +24,13 @@
 namespace lbfd {
 
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int vec_width) {
+  if (vec_width == 0) vec_width = step_vec_width(a.Lx);
+  if (vec_width != 1 && (vec_width != 2 || a.Lx % 2 != 0)) return cudaErrorInvalidValue;
   switch (lattice) {
-    case kD1Q3: return launch_step_d1q3(precision, src, dst, a, stream);
-    case kD2Q9: return launch_step_d2q9(precision, src, dst, a, stream);
-    case kD3Q19: return launch_step_d3q19(precision, src, dst, a, stream);
+    case kD1Q3: return launch_step_d1q3(precision, src, dst, a, stream, vec_width);
+    case kD2Q9: return launch_step_d2q9(precision, src, dst, a, stream, vec_width);
+    case kD3Q19: return launch_step_d3q19(precision, src, dst, a, stream, vec_width);
   }
   return cudaErrorInvalidValue;
 }

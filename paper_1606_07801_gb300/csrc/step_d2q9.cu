@@ -4,10 +4,11 @@
 
 namespace lbfd {
 
-cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
+cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream,
+                             int vec_width) {
   return dispatch_storage(precision, [&](auto tag) {
     using S = typename decltype(tag)::type;
-    return step_t<kD2Q9, S>(src, dst, a, stream);
+    return step_t<kD2Q9, S>(src, dst, a, stream, vec_width);
   });
 }
 

@@ -240,18 +240,6 @@ inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &blo
   grid = dim3((cols + bx - 1) / bx, (Ly + by - 1) / by, Lz);
 }
 
-// Sites per thread of the step kernel (a tuning knob; results do not depend
-// on it).  LBFD_STEP_VX = 1 or 2 overrides the default of 2 when Lx allows
-// (else 1).
-inline int step_vx_override() {
-  static int v = [] {
-    const char *e = getenv("LBFD_STEP_VX");
-    const int r = e ? atoi(e) : 0;
-    return (r == 1 || r == 2) ? r : 0;
-  }();
-  return v;
-}
-
 // Programmatic dependent launch of the step kernels (a tuning knob; results
 // do not depend on it).  LBFD_STEP_PDL = 0 launches them plainly.
 inline bool step_pdl() {
@@ -281,10 +269,7 @@ cudaError_t step_noise_idx(const S *s, S *d, const StepArgs &a, int vx, cudaStre
 }
 
 template <int LAT, typename S, int NOISE>
-cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
-  int vx = step_vx_override();
-  if (vx == 0) vx = 2;
-  if (a.Lx % vx != 0) vx = 1;
+cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream_t stream, int vx) {
   const S *s = static_cast<const S *>(src);
   S *d = static_cast<S *>(dst);
   if (offsets_fit_32(Lattice<LAT>::Q, a.N)) return step_noise_idx<LAT, S, NOISE, uint32_t>(s, d, a, vx, stream);
@@ -294,10 +279,10 @@ cudaError_t step_noise(const void *src, void *dst, const StepArgs &a, cudaStream
 // Kernel selection by noise configuration: each variant is branch-free in
 // its per-site code, so the compiler can interleave the sites of a thread.
 template <int LAT, typename S>
-cudaError_t step_t(const void *src, void *dst, const StepArgs &a, cudaStream_t stream) {
-  if (a.noise_mode == kNoiseOff) return step_noise<LAT, S, kStepNoiseOff>(src, dst, a, stream);
-  if (a.noise_dist == kGaussian) return step_noise<LAT, S, kStepNoiseGauss>(src, dst, a, stream);
-  return step_noise<LAT, S, kStepNoiseFlat>(src, dst, a, stream);
+cudaError_t step_t(const void *src, void *dst, const StepArgs &a, cudaStream_t stream, int vx) {
+  if (a.noise_mode == kNoiseOff) return step_noise<LAT, S, kStepNoiseOff>(src, dst, a, stream, vx);
+  if (a.noise_dist == kGaussian) return step_noise<LAT, S, kStepNoiseGauss>(src, dst, a, stream, vx);
+  return step_noise<LAT, S, kStepNoiseFlat>(src, dst, a, stream, vx);
 }
 
 }  // namespace lbfd

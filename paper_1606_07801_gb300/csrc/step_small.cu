@@ -30,10 +30,12 @@ namespace {
 
 constexpr int kSmallThreads = 512;
 
+// src and dst may be the same buffer (lbfd_step runs an even number of steps
+// in place), so neither is __restrict__: every read of src happens before the
+// first barrier and every write of dst after the last one.
 template <int LAT, typename S, int NOISE>
 __global__ void __launch_bounds__(kSmallThreads)
-    k_step_small(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a, uint32_t lattice_id, uint64_t t0,
-                 int nsteps) {
+    k_step_small(const S *src, S *dst, const StepArgs a, uint32_t lattice_id, uint64_t t0, int nsteps) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Q = Lattice<LAT>::Q;
   const int64_t n = static_cast<int64_t>(Q) * a.N;
@@ -77,11 +79,12 @@ cudaError_t small_t(const void *src, void *dst, const StepArgs &a, uint64_t seed
 constexpr int kClusterMax = 8;       // portable cluster size
 constexpr int kClusterThreads = 256;
 
-// Sites of CTA `rank`: [rank * chunk, min(N, (rank + 1) * chunk)).
+// Sites of CTA `rank`: [rank * chunk, min(N, (rank + 1) * chunk)).  As in
+// k_step_small, src and dst may be the same buffer: all reads of src come
+// before the first cluster barrier and all writes of dst after the last.
 template <int LAT, typename S, int NOISE>
 __global__ void __launch_bounds__(kClusterThreads)
-    k_step_cluster(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a, uint32_t lattice_id, uint64_t t0,
-                   int nsteps, int chunk) {
+    k_step_cluster(const S *src, S *dst, const StepArgs a, uint32_t lattice_id, uint64_t t0, int nsteps, int chunk) {
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   constexpr int Q = L::Q;
@@ -204,11 +207,14 @@ cudaError_t small_or_cluster(const void *src, void *dst, const StepArgs &a, uint
 
 }  // namespace
 
-bool small_path_fits(int lattice, int precision, int64_t N) {
-  if (lattice != kD1Q3 && lattice != kD2Q9 && lattice != kD3Q19) return false;
+int small_path_ctas(int lattice, int precision, int64_t N) {
+  if (lattice != kD1Q3 && lattice != kD2Q9 && lattice != kD3Q19) return 0;
+  if (N < 1) return 0;
   const int Q = lattice == kD1Q3 ? 3 : (lattice == kD2Q9 ? 9 : 19);
-  return N >= 1 && small_ctas(Q, N, storage_bytes(precision), precision == kStoreF64) > 0;
+  return small_ctas(Q, N, storage_bytes(precision), precision == kStoreF64);
 }
+
+bool small_path_fits(int lattice, int precision, int64_t N) { return small_path_ctas(lattice, precision, N) > 0; }
 
 template <int LAT>
 cudaError_t small_lat(int precision, const void *src, void *dst, const StepArgs &a, uint64_t seed,

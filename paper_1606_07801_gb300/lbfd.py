@@ -29,6 +29,9 @@ POLICY_FIFO, POLICY_SHORTEST = 0, 1
 WALK_STRIDED, WALK_CONTIGUOUS, WALK_PER_TILE, WALK_PARAM = 0, 1, 2, 3
 REQ_UNKNOWN, REQ_QUEUED, REQ_RUNNING, REQ_DONE = -1, 0, 1, 2
 MAX_Q, MAX_MODES = 19, 16
+KERNEL_AUTO, KERNEL_VEC, KERNEL_SCALAR, KERNEL_SMALL, KERNEL_CLUSTER, KERNEL_MRT = 0, 1, 2, 3, 4, 5
+KERNEL_NAMES = {KERNEL_VEC: "k_step_vec", KERNEL_SCALAR: "k_step", KERNEL_SMALL: "k_step_small",
+                KERNEL_CLUSTER: "k_step_cluster", KERNEL_MRT: "k_step_mrt"}
 
 Q_OF = {D1Q3: 3, D2Q9: 9, D3Q19: 19, D2Q5: 5}
 D_OF = {D1Q3: 1, D2Q9: 2, D3Q19: 3, D2Q5: 2}
@@ -41,7 +44,8 @@ class Options(ctypes.Structure):
         ("init", c_int32), ("device", c_int32), ("dims", c_int64 * 3), ("tau", c_double),
         ("rho_mean", c_double), ("sine_amp", c_double), ("sine_k", c_int32 * 3), ("lattice_id", c_uint32),
         ("seed", c_uint64), ("stream", c_void_p), ("f_dev", c_void_p * 2), ("n_modes", c_int32),
-        ("modes", (c_int32 * 3) * MAX_MODES), ("reserved", c_int32 * 8), ("theta", c_double),
+        ("modes", (c_int32 * 3) * MAX_MODES), ("step_kernel", c_int32), ("reserved", c_int32 * 7),
+        ("theta", c_double),
         ("tau_moments", c_double * MAX_Q),
     ]
 
@@ -108,6 +112,7 @@ SIGNATURES = {
     "lbfd_create_ex": (c_int32, [P(c_void_p), P(Options)]),
     "lbfd_destroy": (c_int32, [c_void_p]),
     "lbfd_step": (c_int32, [c_void_p, c_int64]),
+    "lbfd_step_kernel": (c_int32, [c_void_p, c_int64, P(c_int32)]),
     "lbfd_sync": (c_int32, [c_void_p]),
     "lbfd_get_t": (c_int32, [c_void_p, P(c_int64)]),
     "lbfd_set_t": (c_int32, [c_void_p, c_int64]),
@@ -227,6 +232,12 @@ def lbfd_destroy(h: int) -> None:
 
 def lbfd_step(h: int, n: int) -> None:
     _check(load().lbfd_step(h, n), "lbfd_step")
+
+
+def lbfd_step_kernel(h: int, n: int) -> int:
+    k = c_int32()
+    _check(load().lbfd_step_kernel(h, n, ctypes.byref(k)), "lbfd_step_kernel")
+    return k.value
 
 
 def lbfd_sync(h: int) -> None:

@@ -104,12 +104,30 @@ def test_low_density_local_noise(orc):
     lat, dims, rho = lb.D2Q9, (128, 96), 0.5
     Q, N = 9, 128 * 96
     f0 = synth.random_populations(Q, N, rho, 0.3, seed=99)
-    o = _oracle_run(orc, lat, dims, f0, 200, 0.8, rho_mean=rho, seed=21)
+    # The oracle one step at a time, to see how close the pre-collision
+    # density came to zero.  The local noise amplitude is sqrt(c max(rho, 0))
+    # (eq. xilocal with the clamp of Sec. IV), whose slope 1/(2 sqrt(rho))
+    # scales a rounding difference in rho; at rho = rho_mean that slope is
+    # what the 1e-12 rho_mean bar allows for, so the bar is scaled by
+    # sqrt(rho_mean / |rho|) at the closest approach.  |rho| is floored at the
+    # rounding of the Q-term FP64 density sum, Q 2^-53 sum_i |f_i|, below
+    # which the two sides may see opposite signs of rho.
+    f, amp, t = f0.copy(), 1.0, 0
+    while t < 200:
+        r = f.sum(0)
+        floor = Q * 2.0 ** -53 * np.abs(f).sum(0)
+        amp = max(amp, float(np.max(np.sqrt(rho / np.maximum(np.abs(r), floor)))))
+        f = _oracle_run(orc, lat, dims, f, 1, 0.8, rho_mean=rho, seed=21, t0=t)
+        t += 1
+    o = f
     assert (o.sum(0) < 0).mean() > 0.01  # the clamp is exercised
     g64 = _gpu_run(lat, dims, f0, 200, 0.8, lb.F64, rho_mean=rho, seed=21)
-    # sites that pass close to rho = 0 amplify FP64 rounding through
-    # sqrt(rho) (slope 1/(2 sqrt(rho))), so this run gets a 1e-11 bound
-    assert np.max(np.abs(g64 - o)) <= 1e-11
+    err64 = np.abs(g64 - o)
+    bound = 1e-12 * rho * amp
+    print(f"FP64 at rho = 0.5: max error {err64.max():.2e} against the run's bound {bound:.2e} "
+          f"(slope factor {amp:.3g}); {100 * np.any(err64 > 1e-12 * rho, axis=0).mean():.2f}% of sites beyond "
+          f"1e-12 rho")
+    assert err64.max() <= bound
     g32 = _gpu_run(lat, dims, f0, 200, 0.8, lb.F32, rho_mean=rho, seed=21)
     bad = np.any(np.abs(g32 - o) > 2e-5 * rho, axis=0).mean()
     print(f"FP32 at rho = 0.5: {100 * bad:.1f}% of sites beyond 2e-5 rho after 200 steps")

@@ -22,6 +22,8 @@ REL = 1e-12  # the FP64 tolerance of the parity tests
     (lb.D3Q19, (24, 20, 18), lb.F64),
     (lb.D1Q3, (5000,), lb.F32),
     (lb.D2Q9, (2048, 2048), lb.F32),
+    # exactly the capacity of the fixed scratch: every one of its slots is written and read
+    (lb.D1Q3, (16777216,), lb.F32),
 ])
 def test_noalloc_mass_matches_lbfd_mass_on_two_calls(lat, dims, precision):
     Q, N = lb.Q_OF[lat], int(np.prod(dims))
