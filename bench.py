@@ -616,21 +616,39 @@ def main():
     # --sample-every steps (the fluctuation statistics of a long run)
     obs = None
     if args.sample_every > 0:
+        # lbfd_step with a sample every k steps (inside the step kernel where
+        # the format allows), timed over the same number of steps as the
+        # main region, and the separate sampling pass for comparison
+        k = args.sample_every
+        lb.abi.lbfd_set_sample_every(sim.h, k)
+        sim.step(2 * k)
+        torch.cuda.synchronize()
+        s_steps = max(k, (args.steps // k) * k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(s_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sampled = e0.elapsed_time(e1)
+        lb.abi.lbfd_set_sample_every(sim.h, 0)
         n_samp = 5
         sim.sample()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(n_samp):
             sim.sample()
         e1.record(stream)
         torch.cuda.synchronize()
         ms_sample = e0.elapsed_time(e1) / n_samp
-        k = args.sample_every
-        obs = {"ms_per_sample": ms_sample, "sample_every": k, "modes": len(modes),
-               "value_with_sampling": job_glups(world, N, k, (k * ms_per_step + ms_sample) * 1e-3),
-               "algorithmic_bytes_per_sample": Q * elem * N,
-               "achieved_gbs": Q * elem * N / (ms_sample * 1e-3) / 1e9}
+        fused = bool(kname in ("k_step_vec", "k_step", "k_step_staged") and prec != 1)
+        obs = {"sample_every": k, "modes": len(modes), "steps": s_steps,
+               "value_with_sampling": job_glups(world, N, s_steps, ms_sampled * 1e-3),
+               "fused": fused,
+               "ms_per_sampled_step_extra": (ms_sampled / s_steps - ms_per_step) * k,
+               "separate_pass": {"ms_per_sample": ms_sample,
+                                 "value_with_sampling": job_glups(world, N, k, (k * ms_per_step + ms_sample) * 1e-3),
+                                 "algorithmic_bytes_per_sample": Q * elem * N,
+                                 "achieved_gbs": Q * elem * N / (ms_sample * 1e-3) / 1e9}}
 
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device (pinned), one step runs, the density comes back

@@ -88,6 +88,11 @@ extern "C" {
                                  lattices, n >= 2; chosen automatically) */
 #define LBFD_KERNEL_CLUSTER 4 /* k_step_cluster: the same over a thread-block cluster (chosen automatically) */
 #define LBFD_KERNEL_MRT 5     /* k_step_mrt: moment-space collision (D2Q5, multiple relaxation times) */
+#define LBFD_KERNEL_STAGED 6  /* k_step_staged: persistent; each tile's source rows are copied into shared
+                                 memory by the TMA unit (bulk asynchronous copies on an mbarrier), the sites
+                                 pull from there, and the results go back by bulk stores.  Needs
+                                 Lx * (bytes per stored value) to be a multiple of 16 and 16-byte aligned
+                                 buffers; D1Q3, D2Q9, D3Q19 */
 
 /* Options of lbfd_create_ex.  Fill with lbfd_options_init, then override. */
 typedef struct lbfd_options {
@@ -109,10 +114,33 @@ typedef struct lbfd_options {
                            storage format; both or neither.  Never freed by the library. */
     int32_t n_modes;    /* structure-factor wave vectors sampled by lbfd_sample */
     int32_t modes[LBFD_MAX_MODES][3];
-    int32_t step_kernel; /* LBFD_KERNEL_AUTO, or LBFD_KERNEL_VEC / LBFD_KERNEL_SCALAR to ask for that
-                            kernel for the one-launch-per-step path (LBFD_KERNEL_VEC needs Lx even).
-                            Small lattices still take the many-steps-per-launch path. */
-    int32_t reserved[7];
+    int32_t step_kernel; /* LBFD_KERNEL_AUTO, or LBFD_KERNEL_VEC / LBFD_KERNEL_SCALAR /
+                            LBFD_KERNEL_STAGED to ask for that kernel for the one-launch-per-step path
+                            (LBFD_EINVAL where the lattice does not meet its requirements).  Small
+                            lattices still take the many-steps-per-launch path. */
+    int32_t wait_test_bytes; /* tests of the staged kernel's bounded waits only (0 in normal use): every
+                            CTA's first tile waits for this many bytes more than its copies deliver, so
+                            the wait runs out after about a second, the kernel stops, and the next
+                            synchronous call reports LBFD_ETIMEOUT.  Needs the staged kernel; < 2^20 */
+    int32_t slab_global; /* slab decomposition of one lattice over several processes (see
+                            lbfd_slab_bounds); 0 = the handle holds the whole lattice.  > 0: the lattice
+                            has slab_global planes along its slowest axis (y for D2Q9, z for D3Q19) and
+                            this handle owns planes slab_first .. slab_first + n - 1, n = that axis'
+                            entry of dims (the other dims are the whole lattice's).  The handle stores
+                            n + 2 planes, a halo plane on each side, and keys the noise of a site by its
+                            global index.  Between steps the caller fills the halo planes of the current
+                            state (lbfd_state_device) with its neighbours' crossing populations
+                            (lbfd_slab_halo).  Slab handles take one step per lbfd_step call, run the
+                            staged kernel (LBFD_ENOTSUP where it cannot run), and offer no mass or
+                            sampling; lbfd_set_f(_raw) take the owned planes plus both halo planes
+                            (n + 2 planes), the other readers return the owned planes. */
+    int32_t slab_first;
+    int32_t sample_every; /* s > 0: lbfd_step also adds the observables of f(x, t) to the accumulators
+                            (as lbfd_sample would) at every step t with t mod s == 0, before that
+                            step's collision.  For the FP32-arithmetic formats with at most 4
+                            modes this runs inside the step kernel (one pass over the state);
+                            otherwise lbfd_step runs the separate pass first.  0 = off */
+    int32_t reserved[3];
     double theta;       /* D2Q5: sum_i w_i v_ix^2, in (0, 1/2); 0 = 1/3.  Other lattices: 0 or 1/3 */
     double tau_moments[LBFD_MAX_Q]; /* multiple relaxation times (Sec. III): tau^a of moment a of
                            the basis, a = 1..Q-1 (entry 0, the conserved density, is ignored);
@@ -157,11 +185,47 @@ int lbfd_destroy(lbfd_t h);
  * stream).  Asynchronous on the handle's stream; t advances by n. */
 int lbfd_step(lbfd_t h, int64_t n);
 
+/* Sets lbfd_options.sample_every of a handle (0 turns the sampling in
+ * lbfd_step off).  LBFD_EINVAL for a slab handle or every < 0. */
+int lbfd_set_sample_every(lbfd_t h, int32_t every);
+
 /* The kernel lbfd_step(h, n) would run for this n (one of LBFD_KERNEL_VEC ..
  * LBFD_KERNEL_MRT), into *kernel.  No device work. */
 int lbfd_step_kernel(lbfd_t h, int64_t n, int32_t *kernel);
 
-/* Waits for all work queued on the handle's stream. */
+/* ---- slab decomposition (one lattice over several processes) -------------
+ * The step of eq. LB reads nearest neighbours only, so a lattice cut into
+ * slabs along its slowest axis evolves exactly as a whole if each slab holds,
+ * before every step, one plane beyond each face with the populations that
+ * cross it (3 for D2Q9, 5 for D3Q19).  The noise is keyed by the global site
+ * index, so the split run is bit-identical to the unsplit one.  These calls
+ * are host arithmetic only. */
+
+/* Planes [*first, *first + *count) of global_planes for rank of nranks
+ * (balanced; the first global_planes mod nranks ranks hold one more). */
+int lbfd_slab_bounds(int64_t global_planes, int32_t nranks, int32_t rank, int64_t *first, int64_t *count);
+
+/* Populations with velocity component dir (+1 or -1) along the slowest axis
+ * (the ones that cross a face in that direction), in velocity order, into
+ * pops (may be NULL) and their number into *n_pops.  D2Q9 and D3Q19. */
+int lbfd_slab_cross(int32_t lattice, int32_t dir, int32_t *pops, int32_t *n_pops);
+
+/* Exchange plan of one face of a slab whose dims are as in lbfd_options
+ * (dims of the slowest axis = owned planes n): value offsets, within the
+ * slab's state buffer (lbfd_state_device, n + 2 stored planes), of the
+ * *n_pops planes of *plane_values values that this slab sends through the
+ * face (send_off) and of the halo planes it receives into (recv_off), in
+ * matching order.  face 0 is the low face (to and from the rank below),
+ * face 1 the high face.  What one slab sends through its high face, the slab
+ * above receives through its low face, in the same order.  Either offset
+ * array may be NULL. */
+int lbfd_slab_halo(int32_t lattice, const int64_t *dims, int32_t face, int64_t *send_off, int64_t *recv_off,
+                   int32_t *n_pops, int64_t *plane_values);
+
+/* Waits for all work queued on the handle's stream.  LBFD_ETIMEOUT if a
+ * bounded device wait of a step kernel gave up since the last check (the
+ * state is then not valid); lbfd_get_f, lbfd_get_f_raw, lbfd_moments,
+ * lbfd_mass and lbfd_observables report it the same way. */
 int lbfd_sync(lbfd_t h);
 
 /* Step counter t; lbfd_set_t sets it (resume from a checkpoint: the noise

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build_mod
 from .lbfd import (D1Q3, D2Q5, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
-                   F64, GAUSSIAN, INIT_HOST, INIT_NONE, INIT_SINE, INIT_UNIFORM, MAX_MODES, MAX_Q, NOISE_GLOBAL,
+                   F64, GAUSSIAN, INIT_HOST, INIT_NONE, INIT_SINE, INIT_UNIFORM, KERNEL_AUTO, KERNEL_CLUSTER,
+                   KERNEL_MRT, KERNEL_SCALAR, KERNEL_SMALL, KERNEL_STAGED, KERNEL_VEC, MAX_MODES, MAX_Q, NOISE_GLOBAL,
                    NOISE_LOCAL, NOISE_OFF, OK, POLICY_FIFO, POLICY_SHORTEST, Q_OF, REQ_DONE, REQ_QUEUED, REQ_RUNNING,
                    REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, WALK_CONTIGUOUS, WALK_PARAM, WALK_PER_TILE,
                    WALK_STRIDED, LbfdError, Options, load)
@@ -25,7 +26,8 @@ __all__ = ["Simulation", "Ensemble", "Server", "STORAGE_DTYPE", "abi", "build", 
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
            "INIT_NONE", "INIT_HOST", "RESULT_F", "RESULT_RHO", "RESULT_NONE", "POLICY_FIFO", "POLICY_SHORTEST",
            "WALK_STRIDED", "WALK_CONTIGUOUS", "WALK_PER_TILE", "WALK_PARAM", "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE",
-           "REQ_UNKNOWN", "Q_OF", "D_OF"]
+           "REQ_UNKNOWN", "Q_OF", "D_OF", "KERNEL_AUTO", "KERNEL_VEC", "KERNEL_SCALAR", "KERNEL_SMALL",
+           "KERNEL_CLUSTER", "KERNEL_MRT", "KERNEL_STAGED"]
 
 # numpy type of one stored value per precision (bfloat16 as its raw 16 bits)
 STORAGE_DTYPE = {F32: np.float32, F64: np.float64, F32_F16: np.float16, F32_BF16: np.uint16}
@@ -48,9 +50,13 @@ class Simulation:
                  noise_mode: int = NOISE_LOCAL, noise_dist: int = GAUSSIAN, init: int = INIT_UNIFORM,
                  sine_amp: float = 0.0, sine_k=(1, 0, 0), lattice_id: int = 0, modes=(), stream=None,
                  torch_buffers: bool = False, device: int = -1, theta: float = 0.0, tau_moments=None,
-                 step_kernel: int = 0):
+                 step_kernel: int = 0, wait_test_bytes: int = 0, slab_global: int = 0, slab_first: int = 0,
+                 sample_every: int = 0):
         o = abi.lbfd_options_init()
+        o.sample_every = int(sample_every)
         o.step_kernel = int(step_kernel)
+        o.wait_test_bytes = int(wait_test_bytes)
+        o.slab_global, o.slab_first = int(slab_global), int(slab_first)
         o.lattice, o.precision, o.noise_mode, o.noise_dist, o.init = lattice, precision, noise_mode, noise_dist, init
         d = [int(x) for x in dims] + [1] * (3 - len(dims))
         for a in range(3):
@@ -77,17 +83,25 @@ class Simulation:
         if stream is not None:
             o.stream = int(getattr(stream, "cuda_stream", stream))
             self._keep.append(stream)
+        self.buffers = None
         if torch_buffers:
             import torch
 
             q, n = Q_OF[lattice], int(np.prod(d))
+            if slab_global:  # a slab stores a halo plane on each side of its slowest axis
+                ax = {D2Q9: 1, D3Q19: 2}.get(lattice, 0)
+                n = n // d[ax] * (d[ax] + 2)
             dt = {F64: torch.float64, F32: torch.float32, F32_F16: torch.float16, F32_BF16: torch.bfloat16}[precision]
             dev = torch.device("cuda", device if device >= 0 else torch.cuda.current_device())
             bufs = [torch.empty(q * n, dtype=dt, device=dev) for _ in range(2)]
             o.f_dev[0], o.f_dev[1] = bufs[0].data_ptr(), bufs[1].data_ptr()
             self._keep.extend(bufs)
+            self.buffers = bufs
         self.lattice, self.dims, self.precision = lattice, tuple(d), precision
         self.Q, self.D, self.N = Q_OF[lattice], D_OF[lattice], int(np.prod(d))
+        # sites set_f takes: a slab also takes its two halo planes
+        ax = {D2Q9: 1, D3Q19: 2}.get(lattice, 0)
+        self.stored_sites = self.N // d[ax] * (d[ax] + 2) if slab_global else self.N
         self.h = abi.lbfd_create_ex(o)
 
     # -- lifecycle -------------------------------------------------------------
@@ -132,7 +146,8 @@ class Simulation:
         return abi.lbfd_get_f(self.h)
 
     def set_f(self, f) -> None:
-        abi.lbfd_set_f(self.h, np.asarray(f, dtype=np.float64))
+        """f(x, t), [Q, N] (a slab: [Q, owned plus both halo planes])."""
+        abi.lbfd_set_f(self.h, np.asarray(f, dtype=np.float64), self.stored_sites)
 
     def moments(self, with_flux: bool = False):
         return abi.lbfd_moments(self.h, with_flux)

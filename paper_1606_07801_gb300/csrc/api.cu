@@ -78,6 +78,7 @@ struct lbfd_sim {
   double *acc = nullptr;       // observable accumulators
   int acc_n = 0;
   double *d_mass = nullptr;
+  double *fin = nullptr;  // stage-2 scratch of the FP32 observables (totals and a ticket word)
   double *mom = nullptr;  // rho and j for lbfd_moments, allocated on first use
   int64_t n_samples = 0;
   int32_t modes_host[LBFD_MAX_MODES][3] = {};
@@ -86,7 +87,32 @@ struct lbfd_sim {
   // any tau^a differs from tau; tables of the lattice at its theta
   bool mrt = false;
   double w[LBFD_MAX_Q] = {}, m[LBFD_MAX_Q * LBFD_MAX_Q] = {}, tau_m[LBFD_MAX_Q] = {};
+  // status word of the staged kernel's bounded waits: pinned host memory
+  // mapped into the device, so the host reads it after a sync without a copy
+  int *status_host = nullptr;
+  int *status_dev = nullptr;
+  bool staged_ok = false;  // the lattice and buffers meet the staged kernel's requirements
+  // the stored lattice: dims itself, or for a slab its n owned planes plus
+  // a halo plane on each side along the slowest axis
+  int32_t sd[3] = {1, 1, 1};
+  int64_t NS = 0;     // stored sites (N for a whole lattice)
+  bool slab = false;
+  int64_t plane = 0;  // sites of one plane along the slowest axis (slabs)
 };
+
+static int slow_axis_of(int lattice) { return lattice == LBFD_D3Q19 ? 2 : (lattice == LBFD_D2Q9 ? 1 : 0); }
+
+// LBFD_ETIMEOUT if a staged step kernel recorded a wait that gave up (call
+// after a stream synchronisation); clears the word.
+static int check_status(lbfd_sim *h) {
+  if (!h->status_host) return LBFD_OK;
+  volatile int *st = h->status_host;
+  const int v = *st;
+  if (v == 0) return LBFD_OK;
+  *st = 0;
+  return fail(LBFD_ETIMEOUT, "a bounded wait of the staged step kernel gave up (status " + std::to_string(v) +
+                                 "); the state is not valid");
+}
 
 // The handle stores the post-collision populations g of the last step (the
 // pull kernel's natural state).  The paper's f(x, t) is g streamed once.
@@ -94,14 +120,14 @@ struct lbfd_sim {
 // overwrites anyway.
 static cudaError_t materialize_f(lbfd_sim *h) {
   const lbfd_options &o = h->opt;
-  return launch_shift(o.lattice, h->elem, h->f[h->cur], h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                      int32_t(o.dims[2]), +1, h->stream);
+  return launch_shift(o.lattice, h->elem, h->f[h->cur], h->f[h->cur ^ 1], h->sd[0], h->sd[1], h->sd[2], +1,
+                      h->stream);
 }
 
 static cudaError_t store_f_from_spare(lbfd_sim *h) {
   const lbfd_options &o = h->opt;
-  return launch_shift(o.lattice, h->elem, h->f[h->cur ^ 1], h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                      int32_t(o.dims[2]), -1, h->stream);
+  return launch_shift(o.lattice, h->elem, h->f[h->cur ^ 1], h->f[h->cur], h->sd[0], h->sd[1], h->sd[2], -1,
+                      h->stream);
 }
 
 // Host conversion between FP64 populations and the storage format (16-bit
@@ -183,13 +209,48 @@ static int validate(const lbfd_options *o) {
   if (mrt && double(lattice_q(o->lattice)) * n > 4294967295.0)
     return fail(LBFD_ENOTSUP, "D2Q5 and multiple relaxation times need Q * sites < 2^32");
   if (o->f_dev[0] && o->f_dev[0] == o->f_dev[1]) return fail(LBFD_EINVAL, "the two f_dev buffers must differ");
-  if (o->step_kernel != LBFD_KERNEL_AUTO && o->step_kernel != LBFD_KERNEL_VEC && o->step_kernel != LBFD_KERNEL_SCALAR)
-    return fail(LBFD_EINVAL, "step_kernel must be LBFD_KERNEL_AUTO, LBFD_KERNEL_VEC or LBFD_KERNEL_SCALAR");
-  if (o->step_kernel == LBFD_KERNEL_VEC && o->dims[0] % 2 != 0)
-    return fail(LBFD_EINVAL, "LBFD_KERNEL_VEC needs an even Lx");
-  for (int k = 0; k < 7; ++k)
+  if (o->step_kernel != LBFD_KERNEL_AUTO && o->step_kernel != LBFD_KERNEL_VEC &&
+      o->step_kernel != LBFD_KERNEL_SCALAR && o->step_kernel != LBFD_KERNEL_STAGED)
+    return fail(LBFD_EINVAL,
+                "step_kernel must be LBFD_KERNEL_AUTO, LBFD_KERNEL_VEC, LBFD_KERNEL_SCALAR or LBFD_KERNEL_STAGED");
+  if (o->step_kernel != LBFD_KERNEL_AUTO && mrt)
+    return fail(LBFD_EINVAL, "D2Q5 and multiple relaxation times run the moment-space kernel only");
+  if (o->wait_test_bytes < 0 || o->wait_test_bytes >= (1 << 20))
+    return fail(LBFD_EINVAL, "wait_test_bytes must be in [0, 2^20)");
+  if (o->wait_test_bytes != 0 && o->step_kernel != LBFD_KERNEL_STAGED)
+    return fail(LBFD_EINVAL, "wait_test_bytes needs step_kernel = LBFD_KERNEL_STAGED");
+  if (o->slab_global != 0) {
+    if (o->lattice != LBFD_D2Q9 && o->lattice != LBFD_D3Q19)
+      return fail(LBFD_EINVAL, "slabs are cut along y (D2Q9) or z (D3Q19)");
+    const int ax = slow_axis_of(o->lattice);
+    if (o->slab_global < 1 || o->slab_first < 0 || o->slab_first + o->dims[ax] > o->slab_global)
+      return fail(LBFD_EINVAL, "slab planes must lie within [0, slab_global)");
+    if (o->dims[ax] + 2 > 65535) return fail(LBFD_EINVAL, "a slab stores its planes plus two: at most 65535");
+    if (mrt) return fail(LBFD_EINVAL, "slabs run single relaxation on D2Q9 / D3Q19");
+    if (o->step_kernel != LBFD_KERNEL_AUTO && o->step_kernel != LBFD_KERNEL_STAGED)
+      return fail(LBFD_EINVAL, "slabs run the staged kernel");
+  } else if (o->slab_first != 0) {
+    return fail(LBFD_EINVAL, "slab_first needs slab_global > 0");
+  }
+  if (o->sample_every < 0) return fail(LBFD_EINVAL, "sample_every must be >= 0");
+  if (o->sample_every > 0 && o->slab_global > 0) return fail(LBFD_EINVAL, "slab handles do not sample");
+  for (int k = 0; k < 3; ++k)
     if (o->reserved[k] != 0) return fail(LBFD_EINVAL, "reserved option fields must be 0");
   return LBFD_OK;
+}
+
+// Whether the library's own choice takes the staged kernel where it can run.
+// On GB300 the register-pull kernel is faster for every lattice (both run
+// about the same instructions per site, and the staged kernel's producer
+// warp and copies cost a few per cent), so the default is off;
+// LBFD_STEP_STAGED = 1 turns it on (a tuning knob; results do not depend on
+// the kernel).
+static bool staged_default() {
+  static const bool v = [] {
+    const char *e = getenv("LBFD_STEP_STAGED");
+    return e && atoi(e) == 1;
+  }();
+  return v;
 }
 
 // The kernel lbfd_step(h, n) runs.  The small-lattice paths hold many steps
@@ -197,14 +258,15 @@ static int validate(const lbfd_options *o) {
 static int step_path(const lbfd_sim *h, int64_t n) {
   const lbfd_options &o = h->opt;
   if (h->mrt) return LBFD_KERNEL_MRT;
+  if (h->slab) return LBFD_KERNEL_STAGED;
   if (n >= 2) {
     const int ctas = small_path_ctas(o.lattice, o.precision, h->N);
     if (ctas == 1) return LBFD_KERNEL_SMALL;
     if (ctas > 1) return LBFD_KERNEL_CLUSTER;
   }
-  if (o.step_kernel == LBFD_KERNEL_SCALAR) return LBFD_KERNEL_SCALAR;
-  if (o.step_kernel == LBFD_KERNEL_VEC) return LBFD_KERNEL_VEC;
-  return step_vec_width(int32_t(o.dims[0])) == 2 ? LBFD_KERNEL_VEC : LBFD_KERNEL_SCALAR;
+  if (o.step_kernel != LBFD_KERNEL_AUTO) return o.step_kernel;
+  if (h->staged_ok && staged_default()) return LBFD_KERNEL_STAGED;
+  return step_vec_width(o.lattice, o.precision, int32_t(o.dims[0])) >= 2 ? LBFD_KERNEL_VEC : LBFD_KERNEL_SCALAR;
 }
 
 static void free_sim(lbfd_sim *h) {
@@ -217,7 +279,9 @@ static void free_sim(lbfd_sim *h) {
   cudaFree(h->phase);
   cudaFree(h->acc);
   cudaFree(h->d_mass);
+  cudaFree(h->fin);
   cudaFree(h->mom);
+  if (h->status_host) cudaFreeHost(h->status_host);
   delete h;
 }
 
@@ -237,6 +301,14 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   h->Q = lattice_q(opt->lattice);
   h->D = lattice_dims(opt->lattice);
   h->N = opt->dims[0] * opt->dims[1] * opt->dims[2];
+  for (int a = 0; a < 3; ++a) h->sd[a] = int32_t(opt->dims[a]);
+  h->slab = opt->slab_global > 0;
+  if (h->slab) {
+    const int ax = slow_axis_of(opt->lattice);
+    h->sd[ax] += 2;
+    h->plane = ax == 1 ? opt->dims[0] : opt->dims[0] * opt->dims[1];
+  }
+  h->NS = int64_t(h->sd[0]) * h->sd[1] * h->sd[2];
   h->elem = storage_bytes(opt->precision);
   h->stream = static_cast<cudaStream_t>(opt->stream);
   for (int m = 0; m < opt->n_modes; ++m)
@@ -255,7 +327,7 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
     h->tau_m[a] = (a == 0 || ta == 0.0) ? opt->tau : ta;
     if (a > 0 && h->tau_m[a] != opt->tau) h->mrt = true;
   }
-  const size_t fbytes = size_t(h->Q) * size_t(h->N) * size_t(h->elem);
+  const size_t fbytes = size_t(h->Q) * size_t(h->NS) * size_t(h->elem);
   cudaError_t e = cudaSuccess;
   if (opt->f_dev[0]) {
     h->f[0] = opt->f_dev[0];
@@ -266,12 +338,37 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
     e = cudaMalloc(&h->f[0], fbytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->f[1], fbytes);
   }
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&h->status_host), sizeof(int), cudaHostAllocMapped);
+  if (e == cudaSuccess) {
+    *h->status_host = 0;
+    e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->status_dev), h->status_host, 0);
+  }
+  if (e == cudaSuccess) {
+    h->staged_ok = !h->mrt && staged_fits(opt->lattice, opt->precision, opt->dims[0], h->NS, h->f[0], h->f[1]);
+    if (h->slab && !h->staged_ok) {
+      free_sim(h);
+      return fail(LBFD_ENOTSUP, "slab handles run the staged kernel: Lx * (bytes per value) must be a multiple "
+                                "of 16 and the buffers 16-byte aligned");
+    }
+    if (opt->step_kernel == LBFD_KERNEL_STAGED && !h->staged_ok) {
+      free_sim(h);
+      return fail(LBFD_EINVAL, "LBFD_KERNEL_STAGED needs Lx * (bytes per value) to be a multiple of 16 and "
+                               "16-byte aligned buffers");
+    }
+    if (opt->step_kernel == LBFD_KERNEL_VEC && opt->dims[0] % 2 != 0) {
+      free_sim(h);
+      return fail(LBFD_EINVAL, "LBFD_KERNEL_VEC needs an even Lx");
+    }
+  }
   h->acc_n = 2 + h->Q + h->Q * h->Q + LBFD_MAX_MODES;
   if (e == cudaSuccess)
     e = cudaMalloc(&h->partials, sizeof(double) * size_t(std::max(kReduceBlocks, kObsBlocks)) *
                                      obs_quantities(h->Q, LBFD_MAX_MODES));
   if (e == cudaSuccess) e = cudaMalloc(&h->acc, sizeof(double) * h->acc_n);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_mass, sizeof(double));
+  const size_t fin_n = size_t(obs_quantities(h->Q, LBFD_MAX_MODES)) + 1;
+  if (e == cudaSuccess) e = cudaMalloc(&h->fin, sizeof(double) * fin_n);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->fin, 0, sizeof(double) * fin_n, h->stream);
   // the structure-factor phases of FP32 sampling as per-axis tables (when small)
   const size_t nphase = obs_phase_values(opt->n_modes, int32_t(opt->dims[0]), int32_t(opt->dims[1]),
                                          int32_t(opt->dims[2]));
@@ -286,8 +383,17 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   if (e == cudaSuccess && opt->init != LBFD_INIT_NONE) {
     // f(x, 0) into the spare buffer, then stored as g = f shifted back
     const double amp = opt->init == LBFD_INIT_SINE ? opt->sine_amp : 0.0;
-    e = launch_init(opt->lattice, opt->precision, h->f[1], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
-                    int32_t(opt->dims[2]), opt->rho_mean, amp, opt->sine_k, h->stream, h->w);
+    // a slab's stored plane c is global plane slab_first - 1 + c (the halo
+    // planes take their neighbours' values, so the owned planes un-stream
+    // correctly)
+    int32_t off[3] = {0, 0, 0}, len[3] = {int32_t(opt->dims[0]), int32_t(opt->dims[1]), int32_t(opt->dims[2])};
+    if (h->slab) {
+      const int ax = slow_axis_of(opt->lattice);
+      off[ax] = opt->slab_first - 1;
+      len[ax] = opt->slab_global;
+    }
+    e = launch_init(opt->lattice, opt->precision, h->f[1], h->sd[0], h->sd[1], h->sd[2], opt->rho_mean, amp,
+                    opt->sine_k, h->stream, h->w, off, len);
     if (e == cudaSuccess) e = store_f_from_spare(h);
   }
   if (e != cudaSuccess) {
@@ -322,29 +428,76 @@ int lbfd_destroy(lbfd_t h) {
   return LBFD_OK;
 }
 
+// The observables of the current state into the accumulators (the body of
+// lbfd_sample; a separate pass over the state).
+static int sample_now(lbfd_sim *h) {
+  const lbfd_options &o = h->opt;
+  if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
+    // FP32 arithmetic: pulled straight from the stored state
+    LBFD_CU(launch_observables_pull(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                                    int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->phase,
+                                    h->partials, h->fin, h->acc, h->stream));
+    g_launches.fetch_add(2, std::memory_order_relaxed);
+  } else {
+    // FP64 storage: FP64 throughout, on the streamed copy of the state
+    LBFD_CU(materialize_f(h));
+    LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
+                               int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials, h->acc,
+                               h->stream));
+    g_launches.fetch_add(3, std::memory_order_relaxed);
+  }
+  h->n_samples += 1;
+  return LBFD_OK;
+}
+
+// Steps until the next sampled step counter (t itself if it is sampled).
+static int64_t steps_to_sample(const lbfd_sim *h, int64_t t) {
+  const int64_t s = h->opt.sample_every;
+  return s > 0 ? (s - t % s) % s : INT64_MAX;
+}
+
 int lbfd_step(lbfd_t h, int64_t n) {
   NvtxRange nvtx_("lbfd_step");
   if (!h) return fail(LBFD_EINVAL, "lbfd_step: null handle");
   if (n < 0) return fail(LBFD_EINVAL, "lbfd_step: n must be >= 0");
   if (n == 0) return LBFD_OK;
+  if (h->slab && n > 1)
+    return fail(LBFD_EINVAL, "lbfd_step: a slab takes one step per call (its halo planes are filled between steps)");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
   StepArgs a{};
-  a.Lx = int32_t(o.dims[0]);
-  a.Ly = int32_t(o.dims[1]);
-  a.Lz = int32_t(o.dims[2]);
-  a.N = h->N;
+  a.Lx = h->sd[0];
+  a.Ly = h->sd[1];
+  a.Lz = h->sd[2];
+  a.N = h->NS;
+  // rows updated and their keys: a slab skips its halo planes and keys its
+  // rows by their global position
+  StagedRows rows{0, uint32_t(h->sd[1]) * uint32_t(h->sd[2]), 0};
+  if (h->slab) {
+    const uint32_t rpp = uint32_t(h->plane / h->sd[0]);  // rows per plane
+    const int ax = slow_axis_of(o.lattice);
+    rows.row_begin = rpp;
+    rows.nrows = rpp * uint32_t(o.dims[ax]);
+    rows.row_key = rpp * uint32_t(o.slab_first) - rpp;
+  }
   fill_step_params(a, o.tau, o.rho_mean);
   a.noise_mode = o.noise_mode;
   a.noise_dist = o.noise_dist;
   const int path = step_path(h, n);
   if (path == LBFD_KERNEL_SMALL || path == LBFD_KERNEL_CLUSTER) {
-    // a small lattice: many steps per launch in shared memory (bit-identical)
+    // a small lattice: many steps per launch in shared memory (bit-identical);
+    // chunks end at the sampled steps, which sample by the separate pass
     constexpr int64_t kChunk = 4096;
     int64_t launches = 0, done = 0;
     bool placed = true;
     while (done < n) {
-      const int chunk = int(std::min<int64_t>(kChunk, n - done));
+      if (steps_to_sample(h, h->t) == 0) {
+        int rc = sample_now(h);
+        if (rc) return rc;
+      }
+      int64_t until = steps_to_sample(h, h->t);
+      if (until == 0) until = h->opt.sample_every;
+      const int chunk = int(std::min<int64_t>(std::min<int64_t>(kChunk, n - done), until));
       const int to = h->cur ^ (chunk & 1);
       a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
       cudaError_t e = launch_step_small(o.lattice, o.precision, h->f[h->cur], h->f[to], a, o.seed, o.lattice_id,
@@ -365,17 +518,55 @@ int lbfd_step(lbfd_t h, int64_t n) {
     if (placed) return LBFD_OK;
     n -= done;
   }
-  const int vec_width = step_path(h, 1) == LBFD_KERNEL_VEC ? 2 : 1;
+  const int kernel = step_path(h, 1);
+  int vec_width = 1;
+  if (kernel == LBFD_KERNEL_VEC) {
+    vec_width = step_vec_width(o.lattice, o.precision, a.Lx);
+    if (vec_width == 1) vec_width = 2;  // asked for by step_kernel: Lx is even
+  }
+  const bool fusable = o.sample_every > 0 && !h->mrt &&
+                       sample_fusable(o.lattice, o.precision, a.Lx, a.Ly, a.Lz, o.n_modes, h->phase);
+  int64_t extra = 0;  // launches besides one step kernel per step
   for (int64_t k = 0; k < n; ++k) {
     a.ph = make_philox_step(o.seed, o.lattice_id, uint64_t(h->t));
-    cudaError_t e = h->mrt ? launch_step_mrt(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->m, h->w,
-                                             h->tau_m, h->stream)
-                           : launch_step(o.lattice, o.precision, h->f[h->cur], h->f[h->cur ^ 1], a, h->stream, vec_width);
+    const void *src = h->f[h->cur];
+    void *dst = h->f[h->cur ^ 1];
+    if (steps_to_sample(h, h->t) == 0) {
+      if (fusable) {
+        // the step and the observables of the state it reads, in one pass
+        int nblocks = 0;
+        cudaError_t e = launch_step_sample(o.lattice, o.precision, src, dst, a, o.n_modes, h->phase, h->partials,
+                                           &nblocks, h->staged_ok, h->status_dev, h->stream);
+        if (e == cudaSuccess)
+          e = launch_obs_pull_finalize(o.lattice, h->partials, nblocks, o.n_modes, h->N, o.rho_mean, h->fin, h->acc,
+                                       h->stream);
+        if (e != cudaSuccess) return cuda_fail("lbfd_step: sampled step", e);
+        h->n_samples += 1;
+        h->cur ^= 1;
+        h->t += 1;
+        extra += 1;
+        continue;
+      }
+      int rc = sample_now(h);
+      if (rc) return rc;
+    }
+    cudaError_t e =
+        kernel == LBFD_KERNEL_MRT ? launch_step_mrt(o.lattice, o.precision, src, dst, a, h->m, h->w, h->tau_m, h->stream)
+        : kernel == LBFD_KERNEL_STAGED ? launch_step_staged(o.lattice, o.precision, src, dst, a, rows, h->status_dev,
+                                                            uint32_t(o.wait_test_bytes), h->stream)
+                                       : launch_step(o.lattice, o.precision, src, dst, a, h->stream, vec_width);
     if (e != cudaSuccess) return cuda_fail("lbfd_step: launch", e);
     h->cur ^= 1;
     h->t += 1;
   }
-  g_launches.fetch_add(n, std::memory_order_relaxed);
+  g_launches.fetch_add(n + extra, std::memory_order_relaxed);
+  return LBFD_OK;
+}
+
+int lbfd_set_sample_every(lbfd_t h, int32_t every) {
+  if (!h || every < 0) return fail(LBFD_EINVAL, "lbfd_set_sample_every: null handle or every < 0");
+  if (h->slab && every > 0) return fail(LBFD_EINVAL, "lbfd_set_sample_every: slab handles do not sample");
+  h->opt.sample_every = every;
   return LBFD_OK;
 }
 
@@ -389,7 +580,7 @@ int lbfd_sync(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_sync: null handle");
   DeviceGuard g(h->device);
   LBFD_CU(cudaStreamSynchronize(h->stream));
-  return LBFD_OK;
+  return check_status(h);
 }
 
 int lbfd_get_t(lbfd_t h, int64_t *t) {
@@ -408,15 +599,24 @@ int lbfd_get_f_raw(lbfd_t h, void *f_host) {
   if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_get_f_raw: null argument");
   DeviceGuard g(h->device);
   LBFD_CU(materialize_f(h));
-  LBFD_CU(cudaMemcpyAsync(f_host, h->f[h->cur ^ 1], size_t(h->Q) * h->N * h->elem, cudaMemcpyDeviceToHost, h->stream));
+  if (h->slab) {
+    // the owned planes of each population (the stored rows between the halo planes)
+    const size_t row = size_t(h->N) * h->elem, pitch = size_t(h->NS) * h->elem;
+    const char *from = static_cast<const char *>(h->f[h->cur ^ 1]) + size_t(h->plane) * h->elem;
+    LBFD_CU(cudaMemcpy2DAsync(f_host, row, from, pitch, row, size_t(h->Q), cudaMemcpyDeviceToHost, h->stream));
+  } else {
+    LBFD_CU(cudaMemcpyAsync(f_host, h->f[h->cur ^ 1], size_t(h->Q) * h->N * h->elem, cudaMemcpyDeviceToHost,
+                            h->stream));
+  }
   LBFD_CU(cudaStreamSynchronize(h->stream));
-  return LBFD_OK;
+  return check_status(h);
 }
 
 int lbfd_set_f_raw(lbfd_t h, const void *f_host) {
   if (!h || !f_host) return fail(LBFD_EINVAL, "lbfd_set_f_raw: null argument");
   DeviceGuard g(h->device);
-  LBFD_CU(cudaMemcpyAsync(h->f[h->cur ^ 1], f_host, size_t(h->Q) * h->N * h->elem, cudaMemcpyHostToDevice, h->stream));
+  // a slab takes its stored planes: the owned ones and both halo planes
+  LBFD_CU(cudaMemcpyAsync(h->f[h->cur ^ 1], f_host, size_t(h->Q) * h->NS * h->elem, cudaMemcpyHostToDevice, h->stream));
   LBFD_CU(store_f_from_spare(h));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   return LBFD_OK;
@@ -447,23 +647,45 @@ int lbfd_set_f(lbfd_t h, const double *f_host) {
   if (h->opt.precision == LBFD_F64) return lbfd_set_f_raw(h, f_host);
   std::vector<uint8_t> tmp;
   try {
-    tmp.resize(size_t(h->Q) * h->N * h->elem);
+    tmp.resize(size_t(h->Q) * h->NS * h->elem);
   } catch (...) {
     return fail(LBFD_ENOMEM, "lbfd_set_f: host staging allocation failed");
   }
   const lbfd_options &o = h->opt;
   dispatch_storage(o.precision, [&](auto tag) {
     using S = typename decltype(tag)::type;
-    encode_host<S>(f_host, reinterpret_cast<S *>(tmp.data()), o.lattice, h->N, o.rho_mean);
+    encode_host<S>(f_host, reinterpret_cast<S *>(tmp.data()), o.lattice, h->NS, o.rho_mean);
     return cudaSuccess;
   });
   return lbfd_set_f_raw(h, tmp.data());
+}
+
+// A slab's density and flux: computed over its stored planes into h->mom,
+// then the owned planes copied to rho_dev / j_dev (D2D or D2H by kind).
+static int slab_moments(lbfd_sim *h, double *rho_out, double *j_out, cudaMemcpyKind kind) {
+  const lbfd_options &o = h->opt;
+  if (!h->mom) LBFD_CU(cudaMalloc(&h->mom, sizeof(double) * size_t(h->NS) * (1 + h->D)));
+  if (!j_out) {
+    LBFD_CU(launch_density_of_state(o.lattice, o.precision, h->f[h->cur], h->sd[0], h->sd[1], h->sd[2], o.rho_mean,
+                                    h->mom, h->stream));
+  } else {
+    LBFD_CU(materialize_f(h));
+    LBFD_CU(launch_moments(o.lattice, o.precision, h->f[h->cur ^ 1], h->sd[0], h->sd[1], h->sd[2], o.rho_mean, h->mom,
+                           h->mom + h->NS, h->stream));
+  }
+  LBFD_CU(cudaMemcpyAsync(rho_out, h->mom + h->plane, sizeof(double) * h->N, kind, h->stream));
+  if (j_out)
+    for (int a = 0; a < h->D; ++a)
+      LBFD_CU(cudaMemcpyAsync(j_out + a * h->N, h->mom + (1 + a) * h->NS + h->plane, sizeof(double) * h->N, kind,
+                              h->stream));
+  return LBFD_OK;
 }
 
 int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev) {
   if (!h || !rho_dev) return fail(LBFD_EINVAL, "lbfd_moments_device: null argument");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
+  if (h->slab) return slab_moments(h, rho_dev, j_dev, cudaMemcpyDeviceToDevice);
   if (!j_dev) {
     // density only: pulled from the stored state, no streamed copy
     LBFD_CU(launch_density_of_state(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
@@ -479,6 +701,12 @@ int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev) {
 int lbfd_moments(lbfd_t h, double *rho_host, double *j_host) {
   if (!h || !rho_host) return fail(LBFD_EINVAL, "lbfd_moments: null argument");
   DeviceGuard g(h->device);
+  if (h->slab) {
+    int rc = slab_moments(h, rho_host, j_host, cudaMemcpyDeviceToHost);
+    if (rc) return rc;
+    LBFD_CU(cudaStreamSynchronize(h->stream));
+    return check_status(h);
+  }
   if (!h->mom) LBFD_CU(cudaMalloc(&h->mom, sizeof(double) * size_t(h->N) * (1 + h->D)));
   int rc = lbfd_moments_device(h, h->mom, j_host ? h->mom + h->N : nullptr);
   if (rc) return rc;
@@ -486,41 +714,30 @@ int lbfd_moments(lbfd_t h, double *rho_host, double *j_host) {
   if (j_host)
     LBFD_CU(cudaMemcpyAsync(j_host, h->mom + h->N, sizeof(double) * h->N * h->D, cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
-  return LBFD_OK;
+  return check_status(h);
 }
 
 int lbfd_mass(lbfd_t h, double *mass) {
   if (!h || !mass) return fail(LBFD_EINVAL, "lbfd_mass: null argument");
+  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_mass: not offered for slab handles");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
   LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, o.rho_mean, h->partials, h->d_mass, h->stream));
   LBFD_CU(cudaMemcpyAsync(mass, h->d_mass, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
-  return LBFD_OK;
+  return check_status(h);
 }
 
 int lbfd_sample(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_sample: null handle");
+  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_sample: not offered for slab handles");
   DeviceGuard g(h->device);
-  const lbfd_options &o = h->opt;
-  if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
-    // FP32 arithmetic: pulled straight from the stored state
-    LBFD_CU(launch_observables_pull(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                                    int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->phase,
-                                    h->partials, h->acc, h->stream));
-  } else {
-    // FP64 storage: FP64 throughout, on the streamed copy of the state
-    LBFD_CU(materialize_f(h));
-    LBFD_CU(launch_observables(o.lattice, o.precision, h->f[h->cur ^ 1], int32_t(o.dims[0]), int32_t(o.dims[1]),
-                               int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->partials, h->acc,
-                               h->stream));
-  }
-  h->n_samples += 1;
-  return LBFD_OK;
+  return sample_now(h);
 }
 
 int lbfd_reset_obs(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_reset_obs: null handle");
+  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_reset_obs: not offered for slab handles");
   DeviceGuard g(h->device);
   LBFD_CU(cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream));
   h->n_samples = 0;
@@ -529,10 +746,12 @@ int lbfd_reset_obs(lbfd_t h) {
 
 int lbfd_observables(lbfd_t h, lbfd_obs *obs) {
   if (!h || !obs) return fail(LBFD_EINVAL, "lbfd_observables: null argument");
+  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_observables: not offered for slab handles");
   DeviceGuard g(h->device);
   std::vector<double> acc(h->acc_n);
   LBFD_CU(cudaMemcpyAsync(acc.data(), h->acc, sizeof(double) * h->acc_n, cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
+  if (int rc = check_status(h)) return rc;
   std::memset(obs, 0, sizeof(*obs));
   obs->t = h->t;
   obs->n_samples = h->n_samples;

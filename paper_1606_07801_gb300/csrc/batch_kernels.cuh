@@ -140,7 +140,7 @@ __device__ __forceinline__ void batch_tile_items(S *__restrict__ base, const Bat
       const int z = static_cast<int>(fastdiv(static_cast<uint32_t>(row), b.div_Ly));
       const int y = row - z * b.a.Ly;
       // a member's value offsets fit 32 bits (checked when it is listed)
-      using C = SrtCollide<LAT, typename Store<S>::R, NOISE>;
+      using C = SrtCollideFor<LAT, S, NOISE>;
       if (VXMAX == 2 && b.vx == 2)
         step_vec_body<LAT, S, 2, NOISE, C, uint32_t>(src, dst, b.a, col * 2, y, z);
       else

@@ -24,9 +24,11 @@ enum NoiseDist : int { kGaussian = 0, kUniform = 1 };
 
 // ---------------------------------------------------------------------------
 // Storage formats of the populations.  FP32 and FP64 store f_i itself.  The
-// 16-bit formats store the deviation f_i - w_i rho_mean (rounded to nearest
-// even), and all arithmetic on them is FP32: get() decodes, put() encodes,
-// wr = w_i rho_mean.
+// 16-bit formats store the deviation d_i = f_i - w_i rho_mean (rounded to
+// nearest even), and all arithmetic on them is FP32.  load() / store()
+// convert the stored value alone (the step kernels collide on the
+// deviations themselves); get() / put() (and the FP64 getd() / putd())
+// decode to and encode from f_i with wr = w_i rho_mean.
 // ---------------------------------------------------------------------------
 enum StorageId : int { kStoreF32 = 0, kStoreF64 = 1, kStoreF16 = 2, kStoreBF16 = 3 };
 
@@ -77,6 +79,8 @@ template <>
 struct Store<float> {
   using R = float;
   static constexpr bool kDeviation = false;
+  __host__ __device__ static __forceinline__ float load(float v) { return v; }
+  __host__ __device__ static __forceinline__ float store(float f) { return f; }
   __host__ __device__ static __forceinline__ float get(float v, float) { return v; }
   __host__ __device__ static __forceinline__ float put(float f, float) { return f; }
   __host__ __device__ static __forceinline__ double getd(float v, double) { return v; }
@@ -86,6 +90,8 @@ template <>
 struct Store<double> {
   using R = double;
   static constexpr bool kDeviation = false;
+  __host__ __device__ static __forceinline__ double load(double v) { return v; }
+  __host__ __device__ static __forceinline__ double store(double f) { return f; }
   __host__ __device__ static __forceinline__ double get(double v, double) { return v; }
   __host__ __device__ static __forceinline__ double put(double f, double) { return f; }
   __host__ __device__ static __forceinline__ double getd(double v, double) { return v; }
@@ -95,6 +101,8 @@ template <>
 struct Store<__half> {
   using R = float;
   static constexpr bool kDeviation = true;
+  __host__ __device__ static __forceinline__ float load(__half v) { return __half2float(v); }
+  __host__ __device__ static __forceinline__ __half store(float d) { return __float2half_rn(d); }
   __host__ __device__ static __forceinline__ float get(__half v, float wr) { return add_rn(__half2float(v), wr); }
   __host__ __device__ static __forceinline__ __half put(float f, float wr) { return __float2half_rn(sub_rn(f, wr)); }
   __host__ __device__ static __forceinline__ double getd(__half v, double wr) {
@@ -108,6 +116,8 @@ template <>
 struct Store<__nv_bfloat16> {
   using R = float;
   static constexpr bool kDeviation = true;
+  __host__ __device__ static __forceinline__ float load(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __host__ __device__ static __forceinline__ __nv_bfloat16 store(float d) { return __float2bfloat16_rn(d); }
   __host__ __device__ static __forceinline__ float get(__nv_bfloat16 v, float wr) {
     return add_rn(__bfloat162float(v), wr);
   }

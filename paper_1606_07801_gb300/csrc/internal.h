@@ -96,17 +96,41 @@ __host__ __device__ __forceinline__ double step_param<double>(double d, float) {
 template <>
 __host__ __device__ __forceinline__ float step_param<float>(double, float f) { return f; }
 
-// Sites per thread of the register-pull step kernel: 2 where Lx is even (the
-// vector kernel k_step_vec), else 1 (k_step).  A tuning knob only; results
-// do not depend on it.  LBFD_STEP_VX = 1 forces one site per thread.
-inline int step_vec_width(int32_t Lx) {
+// Sites per thread of the register-pull step kernel (k_step_vec; 1 is
+// k_step): 4 (16-byte loads and stores of FP32) where that measured faster on
+// GB300 and Lx allows, else 2 where Lx is even, else 1.  Four sites won for
+// D2Q9 in every FP32-arithmetic format (84.5 against 83.9 GLUPS at 2048^2)
+// and for D3Q19 with 16-bit storage (37.9 against 37.6 at 256^3); D3Q19 in
+// FP32 needs too many registers for four (31.7 against 38.9), and FP64 keeps
+// two.  A tuning knob only; results do not depend on it.  LBFD_STEP_VX = 1,
+// 2 or 4 overrides the choice where Lx allows.
+inline int step_vec_width(int lattice, int precision, int32_t Lx) {
   static int forced = [] {
     const char *e = getenv("LBFD_STEP_VX");
     const int r = e ? atoi(e) : 0;
-    return (r == 1 || r == 2) ? r : 0;
+    return (r == 1 || r == 2 || r == 4) ? r : 0;
   }();
-  const int vx = forced ? forced : 2;
-  return Lx % vx == 0 ? vx : 1;
+  int vx = forced;
+  if (vx == 0) {
+    const bool four = precision != kStoreF64 && (lattice == kD2Q9 || (lattice == kD3Q19 && precision != kStoreF32));
+    vx = four ? 4 : 2;
+  }
+  if (vx == 4 && precision == kStoreF64) vx = 2;
+  if (Lx % vx == 0) return vx;
+  return Lx % 2 == 0 ? 2 : 1;
+}
+
+// Block and grid of the one-launch-per-step kernels for vx sites per thread:
+// 256-thread blocks, x fastest (at least one warp along x), one grid plane
+// per z.
+inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block, int vx = 1) {
+  const int cols = Lx / vx;
+  int bx = 256;
+  while (bx > 32 && bx / 2 >= cols) bx /= 2;
+  int by = 256 / bx;
+  while (by > 1 && by / 2 >= Ly) by /= 2;
+  block = dim3(bx, by, 1);
+  grid = dim3((cols + bx - 1) / bx, (Ly + by - 1) / by, Lz);
 }
 
 // CTAs of the many-steps-per-launch path for a small lattice: 1 = one block
@@ -123,6 +147,41 @@ cudaError_t launch_step_d2q9(int precision, const void *src, void *dst, const St
 cudaError_t launch_step_d3q19(int precision, const void *src, void *dst, const StepArgs &a, cudaStream_t stream,
                               int vec_width);
 
+// Rows a staged launch updates, and the key offset of their sites (see
+// staged_kernels.cuh).
+struct StagedRows {
+  uint32_t row_begin, nrows, row_key;
+};
+
+// The same step by the shared-memory staged kernel (staged_kernels.cuh).
+// Needs Lx * (bytes per stored value) to be a multiple of 16, both buffers
+// 16-byte aligned and fewer than 2^31 sites (staged_fits); a bounded wait
+// that gives up sets *status (device-visible memory) to a non-zero code.
+cudaError_t launch_step_staged_d1q3(int precision, const void *src, void *dst, const StepArgs &a, 
+                                   const StagedRows &rows, int *status, uint32_t wait_test_bytes, cudaStream_t stream);
+cudaError_t launch_step_staged_d2q9(int precision, const void *src, void *dst, const StepArgs &a, 
+                                   const StagedRows &rows, int *status, uint32_t wait_test_bytes, cudaStream_t stream);
+cudaError_t launch_step_staged_d3q19(int precision, const void *src, void *dst, const StepArgs &a, 
+                                    const StagedRows &rows, int *status, uint32_t wait_test_bytes, cudaStream_t stream);
+inline bool staged_fits(int lattice, int precision, int64_t Lx, int64_t N, const void *f0, const void *f1) {
+  if (lattice != kD1Q3 && lattice != kD2Q9 && lattice != kD3Q19) return false;
+  const int64_t elem = storage_bytes(precision);
+  return (Lx * elem) % 16 == 0 && N < (int64_t(1) << 31) && reinterpret_cast<uintptr_t>(f0) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(f1) % 16 == 0;
+}
+// wait_test_bytes > 0 only in tests of the bounded wait: the first tile of
+// every CTA waits for that many bytes more than its copies deliver.
+inline cudaError_t launch_step_staged(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
+                                      const StagedRows &rows, int *status, uint32_t wait_test_bytes,
+                                      cudaStream_t stream) {
+  switch (lattice) {
+    case kD1Q3: return launch_step_staged_d1q3(precision, src, dst, a, rows, status, wait_test_bytes, stream);
+    case kD2Q9: return launch_step_staged_d2q9(precision, src, dst, a, rows, status, wait_test_bytes, stream);
+    case kD3Q19: return launch_step_staged_d3q19(precision, src, dst, a, rows, status, wait_test_bytes, stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
 // One step of eq. LB from src to dst (pull streaming, two buffers); by
 // default with the library's choice of sites per thread.
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
@@ -134,9 +193,12 @@ cudaError_t launch_shift(int lattice, int value_bytes, const void *src, void *ds
                          int dir, cudaStream_t stream);
 
 // f_i = w_i rho(x), rho = rho_mean (+ amp sin(2 pi k.x / L)); w (Q values)
-// overrides the lattice's compiled weights (D2Q5 with theta != 1/3).
+// overrides the lattice's compiled weights (D2Q5 with theta != 1/3).  The
+// sine's coordinates are (c + phase_off) mod phase_len per axis (default:
+// the stored lattice itself), so a slab takes its part of the global mode.
 cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
-                        double amp, const int32_t *k, cudaStream_t stream, const double *w = nullptr);
+                        double amp, const int32_t *k, cudaStream_t stream, const double *w = nullptr,
+                        const int32_t *phase_off = nullptr, const int32_t *phase_len = nullptr);
 
 // Multiple-relaxation-time step (mrt_kernels.cuh), FP32 or FP64 storage:
 // m (Q*Q, [a][i]) and w (Q) the basis and weights (run-time for D2Q5), tau
@@ -198,11 +260,75 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
 // phase (optional): the per-axis factors of the structure-factor modes,
 // obs_phase_values() float pairs filled by obs_phase_fill(); without it the
 // kernel evaluates each phase with sincospif.
+// fin: stage-2 scratch of obs_quantities(Q, LBFD_MAX_MODES_DEV) + 1 doubles,
+// its last word zero before the first call (the kernels leave it zero).
 cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
                                     double rho_mean, int n_modes, const int32_t *modes, const void *phase,
-                                    double *partials, double *acc, cudaStream_t stream);
+                                    double *partials, double *fin, double *acc, cudaStream_t stream);
 size_t obs_phase_values(int n_modes, int32_t Lx, int32_t Ly, int32_t Lz);
 void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out);
+
+// c_i = w_i rho_mean in FP32, the constants the FP32-arithmetic observables
+// take their deviations e_i = f_i - c_i from (rounded so that every kernel
+// forms the same value).
+template <int LAT>
+__host__ __device__ __forceinline__ float obs_offset(int i, float rho_f) {
+  return mul_rn(static_cast<float>(Lattice<LAT>::w(i)), rho_f);
+}
+
+// Stage 2 for partials in the layout of the FP32-arithmetic observable pass
+// (nblocks <= kObsBlocks): sums them in block order, restores the sums of rho,
+// f and f f from the deviation sums, and adds them into acc.
+cudaError_t launch_obs_pull_finalize(int lattice, const double *partials, int nblocks, int n_modes, int64_t N,
+                                     double rho_mean, double *fin, double *acc, cudaStream_t stream);
+
+// A step fused with the sampled observables of the state it reads (the
+// FP32-arithmetic formats; sample_kernels.cuh): the observables of f(x, t)
+// go into per-block partials (nblocks written to *nblocks, <= kObsBlocks) in
+// the layout launch_obs_pull_finalize takes, and f(x, t) is advanced one
+// step from src to dst exactly as launch_step does.  phase: the per-axis
+// structure-factor tables (obs_phase_fill); n_modes <= kFusedModes.
+constexpr int kFusedModes = 4;
+// Whether a lattice can take the fused step-and-sample kernel: FP32
+// arithmetic, fewer than 2^31 sites, at most kFusedModes modes with their
+// phase tables, and a work block of 256 threads with whole warps along x
+// (the one-launch-per-step kernel's shape).
+inline bool sample_fusable(int lattice, int precision, int32_t Lx, int32_t Ly, int32_t Lz, int n_modes,
+                           const void *phase) {
+  if (lattice != kD1Q3 && lattice != kD2Q9 && lattice != kD3Q19) return false;
+  if (precision == kStoreF64 || n_modes > kFusedModes || (n_modes > 0 && !phase)) return false;
+  if (int64_t(Lx) * Ly * Lz >= (int64_t(1) << 31)) return false;
+  dim3 grid, block;
+  step_shape(Lx, Ly, Lz, grid, block, step_vec_width(lattice, precision, Lx) >= 2 ? 2 : 1);
+  return block.x * block.y == 256 && block.x % 32 == 0;
+}
+cudaError_t launch_step_sample_d1q3(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
+                                    const void *phase, double *partials, int *nblocks, bool staged_ok, int *status,
+                                    cudaStream_t stream);
+cudaError_t launch_step_sample_d2q9(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
+                                    const void *phase, double *partials, int *nblocks, bool staged_ok, int *status,
+                                    cudaStream_t stream);
+cudaError_t launch_step_sample_d3q19(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
+                                     const void *phase, double *partials, int *nblocks, bool staged_ok, int *status,
+                                     cudaStream_t stream);
+// staged_ok: the lattice and buffers meet the staged kernel's requirements
+// (staged_fits); status: its bounded waits' status word.
+inline cudaError_t launch_step_sample(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
+                                      int n_modes, const void *phase, double *partials, int *nblocks, bool staged_ok,
+                                      int *status, cudaStream_t stream) {
+  switch (lattice) {
+    case kD1Q3:
+      return launch_step_sample_d1q3(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
+                                     stream);
+    case kD2Q9:
+      return launch_step_sample_d2q9(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
+                                     stream);
+    case kD3Q19:
+      return launch_step_sample_d3q19(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
+                                      stream);
+  }
+  return cudaErrorInvalidValue;
+}
 
 // Records msg as the calling thread's lbfd_last_error() and returns code.
 int set_last_error(int code, const std::string &msg);

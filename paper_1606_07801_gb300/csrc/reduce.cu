@@ -281,10 +281,6 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
 // ---------------------------------------------------------------------------
 constexpr int kObsThreads = 256;
 
-template <int LAT>
-__device__ __forceinline__ float obs_offset(int i, float rho_f) {
-  return mul_rn(static_cast<float>(Lattice<LAT>::w(i)), rho_f);
-}
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -504,42 +500,84 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
   }
 }
 
-// Stage 2 of the FP32 pass: sums the block partials in block order (FP64),
-// restores the sums of rho, f and f f from the deviation sums with
-// c_i = w_i rho_mean (the kernel's own FP32 constants) and adds them to acc:
+// Stage 2 of the FP32 pass, spread over the GPU (its FP64 units are few, so
+// one block summing every quantity would take ~0.1 ms): warp w sums
+// quantity w over the block partials (lane l adds blocks l, l + 32, ... in
+// order, then a fixed butterfly), and the last block to finish (a ticket in
+// fin[nq_max]) restores the sums of rho, f and f f from the deviation sums
+// with c_i = w_i rho_mean (the kernels' own FP32 constants) and adds them to
+// acc:
 //   sum rho   = S_delta + N C,            C = sum_i c_i
 //   sum rho^2 = S_delta2 + 2 C S_delta + N C^2
 //   sum f_i   = E_i + N c_i
 //   sum f_i f_j = P_ij + c_j E_i + c_i E_j + N c_i c_j
+// Every sum has a fixed order, so the result does not depend on timing.
+constexpr int kFinWarps = 8;
 template <int LAT>
-__global__ void k_obs_pull_finalize(const double *__restrict__ partials, int nblocks, int K, double Nd, float rho_f,
-                                    double *__restrict__ acc) {
+__global__ void __launch_bounds__(kFinWarps * 32)
+    k_obs_pull_finalize(const double *__restrict__ partials, int nblocks, int K, double Nd, float rho_f,
+                        double *__restrict__ tot, unsigned int *__restrict__ ticket, double *__restrict__ acc) {
   constexpr int Q = Lattice<LAT>::Q;
-  extern __shared__ double tot[];
   const int nq1 = 2 + Q + 2 * K, npair = Q * (Q + 1) / 2, nq = nq1 + npair;
-  sum_partials_ordered(partials, nblocks, nq, tot);
-  if (threadIdx.x == 0) {
-    double c[Q], C = 0.0;
-    for (int i = 0; i < Q; ++i) {
-      c[i] = static_cast<double>(obs_offset<LAT>(i, rho_f));
-      C += c[i];
-    }
-    const double Sd = tot[0], Sd2 = tot[1];
-    acc[0] += Sd + Nd * C;
-    acc[1] += Sd2 + 2.0 * C * Sd + Nd * C * C;
-    for (int i = 0; i < Q; ++i) acc[2 + i] += tot[2 + i] + Nd * c[i];
-    int p = 0;
-    for (int i = 0; i < Q; ++i)
-      for (int j = i; j < Q; ++j, ++p) {
-        const double v = tot[nq1 + p] + c[j] * tot[2 + i] + c[i] * tot[2 + j] + Nd * c[i] * c[j];
-        acc[2 + Q + i * Q + j] += v;
-        if (j != i) acc[2 + Q + j * Q + i] += v;
-      }
-    for (int m = 0; m < K; ++m) {
-      const double re = tot[2 + Q + 2 * m], im = tot[3 + Q + 2 * m];
-      acc[2 + Q + Q * Q + m] += re * re + im * im;
-    }
+  const int lane = threadIdx.x & 31, q = blockIdx.x * kFinWarps + (threadIdx.x >> 5);
+  if (q < nq) {
+    double t = 0.0;
+    for (int b = lane; b < nblocks; b += 32) t += partials[static_cast<size_t>(b) * nq + q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) tot[q] = t;
   }
+  __threadfence();
+  __syncthreads();
+  __shared__ bool last;
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  *ticket = 0u;  // for the next launch (stream-ordered after this one)
+  const volatile double *vt = tot;  // the other blocks' totals, from L2
+  double c[Q], C = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    c[i] = static_cast<double>(obs_offset<LAT>(i, rho_f));
+    C += c[i];
+  }
+  const double Sd = vt[0], Sd2 = vt[1];
+  acc[0] += Sd + Nd * C;
+  acc[1] += Sd2 + 2.0 * C * Sd + Nd * C * C;
+  for (int i = 0; i < Q; ++i) acc[2 + i] += vt[2 + i] + Nd * c[i];
+  int p = 0;
+  for (int i = 0; i < Q; ++i)
+    for (int j = i; j < Q; ++j, ++p) {
+      const double v = vt[nq1 + p] + c[j] * vt[2 + i] + c[i] * vt[2 + j] + Nd * c[i] * c[j];
+      acc[2 + Q + i * Q + j] += v;
+      if (j != i) acc[2 + Q + j * Q + i] += v;
+    }
+  for (int m = 0; m < K; ++m) {
+    const double re = vt[2 + Q + 2 * m], im = vt[3 + Q + 2 * m];
+    acc[2 + Q + Q * Q + m] += re * re + im * im;
+  }
+}
+
+template <int LAT>
+static cudaError_t pull_finalize_t(const double *partials, int nblocks, int n_modes, int64_t N, float rho_f,
+                                   double *fin, double *acc, cudaStream_t stream) {
+  constexpr int Q = Lattice<LAT>::Q;
+  const int nq = obs_quantities(Q, n_modes);
+  unsigned int *ticket = reinterpret_cast<unsigned int *>(fin + obs_quantities(Q, LBFD_MAX_MODES_DEV));
+  k_obs_pull_finalize<LAT><<<(nq + kFinWarps - 1) / kFinWarps, kFinWarps * 32, 0, stream>>>(
+      partials, nblocks, n_modes, double(N), rho_f, fin, ticket, acc);
+  return cudaGetLastError();
+}
+
+// Stage 2 of the FP32-arithmetic observables for partials written by a
+// fused sampling step (sample_kernels.cuh), in the layout of k_obs_pull.
+cudaError_t launch_obs_pull_finalize(int lattice, const double *partials, int nblocks, int n_modes, int64_t N,
+                                     double rho_mean, double *fin, double *acc, cudaStream_t stream) {
+  const float rho_f = static_cast<float>(rho_mean);
+  return dispatch_lattice(lattice, [&](auto lat) -> cudaError_t {
+    constexpr int LAT = decltype(lat)::value;
+    return pull_finalize_t<LAT>(partials, nblocks, n_modes, N, rho_f, fin, acc, stream);
+  });
 }
 
 int obs_pull_blocks(int64_t N) {
@@ -548,7 +586,7 @@ int obs_pull_blocks(int64_t N) {
 
 cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
                                     double rho_mean, int n_modes, const int32_t *modes, const void *phase,
-                                    double *partials, double *acc, cudaStream_t stream) {
+                                    double *partials, double *fin, double *acc, cudaStream_t stream) {
   if (n_modes < 0 || n_modes > LBFD_MAX_MODES_DEV || precision == kStoreF64) return cudaErrorInvalidValue;
   const int64_t N = int64_t(Lx) * Ly * Lz;
   if (N >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
@@ -584,10 +622,9 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
       const float d_off = static_cast<float>(C - rho_mean);
       k_obs_pull<LAT, S><<<nblocks, kObsThreads, 0, stream>>>(static_cast<const S *>(g), dm, rho_f, d_off, ma,
                                                               static_cast<const float2 *>(phase), partials);
-      const int nq = obs_quantities(Q, n_modes);
-      k_obs_pull_finalize<LAT><<<1, kFinalThreads, final_smem(nq), stream>>>(partials, nblocks, n_modes, double(N),
-                                                                                 rho_f, acc);
-      return cudaGetLastError();
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      return pull_finalize_t<LAT>(partials, nblocks, n_modes, N, rho_f, fin, acc, stream);
     }
   });
 }

@@ -25,8 +25,9 @@ namespace lbfd {
 
 cudaError_t launch_step(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
                         cudaStream_t stream, int vec_width) {
-  if (vec_width == 0) vec_width = step_vec_width(a.Lx);
-  if (vec_width != 1 && (vec_width != 2 || a.Lx % 2 != 0)) return cudaErrorInvalidValue;
+  if (vec_width == 0) vec_width = step_vec_width(lattice, precision, a.Lx);
+  if (vec_width != 1 && ((vec_width != 2 && vec_width != 4) || a.Lx % vec_width != 0)) return cudaErrorInvalidValue;
+  if (vec_width == 4 && precision == kStoreF64) return cudaErrorInvalidValue;
   switch (lattice) {
     case kD1Q3: return launch_step_d1q3(precision, src, dst, a, stream, vec_width);
     case kD2Q9: return launch_step_d2q9(precision, src, dst, a, stream, vec_width);
@@ -94,9 +95,16 @@ struct WeightArg {
   double w[LBFD_MAX_Q_DEV];
 };
 
+// Where a stored lattice sits in the lattice whose sine mode is set up: the
+// stored coordinate c of axis a is c + off[a] (mod len[a]) there (a slab
+// with a halo plane sits at its first plane minus one).
+struct PhaseFrame {
+  int32_t off[3], len[3];
+};
+
 template <int LAT, typename S>
 __global__ void k_init(S *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean, double amp, int32_t kx,
-                       int32_t ky, int32_t kz, const WeightArg wt) {
+                       int32_t ky, int32_t kz, const WeightArg wt, const PhaseFrame fr) {
   using L = Lattice<LAT>;
   const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
   for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < N;
@@ -105,10 +113,13 @@ __global__ void k_init(S *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, do
     double rho = rho_mean;
     if (amp != 0.0) {
       // phase / (2 pi) reduced exactly with integers before the sine
-      const int64_t px = ((static_cast<int64_t>(kx) * x) % Lx + Lx) % Lx;
-      const int64_t py = ((static_cast<int64_t>(ky) * y) % Ly + Ly) % Ly;
-      const int64_t pz = ((static_cast<int64_t>(kz) * z) % Lz + Lz) % Lz;
-      const double frac = double(px) / Lx + double(py) / Ly + double(pz) / Lz;
+      const int64_t Px = fr.len[0], Py = fr.len[1], Pz = fr.len[2];
+      const int64_t gx = ((x + fr.off[0]) % Px + Px) % Px, gy = ((y + fr.off[1]) % Py + Py) % Py;
+      const int64_t gz = ((z + fr.off[2]) % Pz + Pz) % Pz;
+      const int64_t px = ((static_cast<int64_t>(kx) * gx) % Px + Px) % Px;
+      const int64_t py = ((static_cast<int64_t>(ky) * gy) % Py + Py) % Py;
+      const int64_t pz = ((static_cast<int64_t>(kz) * gz) % Pz + Pz) % Pz;
+      const double frac = double(px) / Px + double(py) / Py + double(pz) / Pz;
       rho += amp * sinpi(2.0 * frac);
     }
     static_for<L::Q>([&](auto I) {
@@ -119,16 +130,23 @@ __global__ void k_init(S *__restrict__ f, int32_t Lx, int32_t Ly, int32_t Lz, do
 }
 
 cudaError_t launch_init(int lattice, int precision, void *f, int32_t Lx, int32_t Ly, int32_t Lz, double rho_mean,
-                        double amp, const int32_t *k, cudaStream_t stream, const double *w) {
+                        double amp, const int32_t *k, cudaStream_t stream, const double *w, const int32_t *phase_off,
+                        const int32_t *phase_len) {
   return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
     constexpr int LAT = decltype(lat)::value;
     using S = typename decltype(tag)::type;
     WeightArg wt{};
     for (int i = 0; i < Lattice<LAT>::Q; ++i) wt.w[i] = w ? w[i] : Lattice<LAT>::w(i);
+    PhaseFrame fr{{0, 0, 0}, {Lx, Ly, Lz}};
+    for (int a = 0; a < 3; ++a) {
+      if (phase_off) fr.off[a] = phase_off[a];
+      if (phase_len) fr.len[a] = phase_len[a];
+    }
     const int64_t N = static_cast<int64_t>(Lx) * Ly * Lz;
     const int64_t blocks = (N + 255) / 256;
     const int grid = static_cast<int>(blocks < 152 * 64 ? blocks : 152 * 64);
-    k_init<LAT, S><<<grid, 256, 0, stream>>>(static_cast<S *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2], wt);
+    k_init<LAT, S><<<grid, 256, 0, stream>>>(static_cast<S *>(f), Lx, Ly, Lz, rho_mean, amp, k[0], k[1], k[2], wt,
+                                             fr);
     return cudaGetLastError();
   });
 }

@@ -16,11 +16,18 @@ enum StepNoise : int { kStepNoiseOff = 0, kStepNoiseGauss = 1, kStepNoiseFlat = 
 // Collision of one site in registers: f holds the pulled populations
 // f_i(x, t) on entry and the post-collision f*_i(x) on exit; s is the site
 // index that keys the noise.
-template <int LAT, typename R, int NOISE>
+//
+// DEV: f holds the deviations d_i = f_i - w_i rho_mean instead (the 16-bit
+// storage formats).  With rho = rho_mean + drho, drho = sum_i d_i, and
+// 1 - 1/tau = omega, the update f*_i = omega f_i + w_i rho/tau + w_i sigma T_i
+// is d*_i = omega d_i + w_i drho/tau + w_i sigma T_i in exact arithmetic (the
+// w_i rho_mean terms cancel), so the same code runs on the deviations with
+// drho in place of rho; only the noise amplitude needs rho itself.
+template <int LAT, typename R, int NOISE, bool DEV = false>
 __device__ __forceinline__ void collide_site(R (&f)[Lattice<LAT>::Q], uint32_t s, const StepArgs &a) {
   using L = Lattice<LAT>;
   constexpr int Q = L::Q;
-  R rho = f[0];
+  R rho = f[0];  // drho for DEV
   static_for<Q - 1>([&](auto I) { rho += f[decltype(I)::value + 1]; });
 
   R sigma = R(0);
@@ -28,7 +35,8 @@ __device__ __forceinline__ void collide_site(R (&f)[Lattice<LAT>::Q], uint32_t s
   static_for<Q>([&](auto I) { T[decltype(I)::value] = R(0); });
   if constexpr (NOISE != kStepNoiseOff) {
     // local noise: max(rho, 0); global noise: rho^eq (a select, not a branch)
-    const R rho_loc = rho > R(0) ? rho : R(0);
+    const R rho_abs = DEV ? step_param<R>(a.rho_eq, a.rho_eq_f) + rho : rho;
+    const R rho_loc = rho_abs > R(0) ? rho_abs : R(0);
     const R rho_n = a.noise_mode == kNoiseLocal ? rho_loc : step_param<R>(a.rho_eq, a.rho_eq_f);
     sigma = noise_amplitude<R>(rho_n * step_param<R>(a.noise_var, a.noise_var_f));
     R zz[Q - 1];
@@ -58,24 +66,16 @@ __device__ __forceinline__ void collide_site(R (&f)[Lattice<LAT>::Q], uint32_t s
 }
 
 // The single-relaxation-time collision as a function object, the default
-// collision of the site-update bodies below.
-template <int LAT, typename R, int NOISE>
+// collision of the site-update bodies below (DEV for the deviation formats).
+template <int LAT, typename R, int NOISE, bool DEV = false>
 struct SrtCollide {
   __device__ __forceinline__ void operator()(R (&f)[Lattice<LAT>::Q], uint32_t s, const StepArgs &a) const {
-    collide_site<LAT, R, NOISE>(f, s, a);
+    collide_site<LAT, R, NOISE, DEV>(f, s, a);
   }
 };
-
-// w_i rho_mean in the compute type: the offset that the 16-bit formats store
-// the deviation from (zero for FP32/FP64 storage).
-template <int LAT, typename S>
-__device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepArgs &a) {
-  using R = typename Store<S>::R;
-  if constexpr (Store<S>::kDeviation)
-    return mul_rn(static_cast<R>(Lattice<LAT>::w(i)), step_param<R>(a.rho_eq, a.rho_eq_f));
-  else
-    return R(0);
-}
+// The default collision for storage S.
+template <int LAT, typename S, int NOISE>
+using SrtCollideFor = SrtCollide<LAT, typename Store<S>::R, NOISE, Store<S>::kDeviation>;
 
 // Scalar kernel: one site per thread, any lattice shape.  S is the storage
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
@@ -83,7 +83,7 @@ __device__ __forceinline__ typename Store<S>::R store_offset(int i, const StepAr
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
 // Idx is the type of the value offsets i N + site: uint32_t when Q N < 2^32
 // (fewer address instructions), size_t otherwise.
-template <int LAT, typename S, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>, typename Idx = size_t>
+template <int LAT, typename S, int NOISE, class C = SrtCollideFor<LAT, S, NOISE>, typename Idx = size_t>
 __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a,
                                                  int x, int y, int z, const C &collide = C()) {
   using L = Lattice<LAT>;
@@ -105,12 +105,12 @@ __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *_
     const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
     const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
     const uint32_t so = static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
-    f[i] = Store<S>::get(src[static_cast<Idx>(i) * static_cast<Idx>(a.N) + so], store_offset<LAT, S>(i, a));
+    f[i] = Store<S>::load(src[static_cast<Idx>(i) * static_cast<Idx>(a.N) + so]);
   });
   collide(f, s, a);
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    dst[static_cast<Idx>(i) * static_cast<Idx>(a.N) + s] = Store<S>::put(f[i], store_offset<LAT, S>(i, a));
+    dst[static_cast<Idx>(i) * static_cast<Idx>(a.N) + s] = Store<S>::store(f[i]);
   });
 }
 
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__re
   const int z = blockIdx.z;
   pdl_wait();
   if (x >= a.Lx || y >= a.Ly) return;
-  step_scalar_body<LAT, S, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, Idx>(src, dst, a, x, y, z);
+  step_scalar_body<LAT, S, NOISE, SrtCollideFor<LAT, S, NOISE>, Idx>(src, dst, a, x, y, z);
 }
 
 // Vector kernel: VX consecutive sites of a row per thread (needs Lx % VX == 0).
@@ -146,23 +146,70 @@ struct alignas(sizeof(S) * VX) Pack {
   S v[VX];
 };
 
+// Conversions of a VX-wide pack of stored values to and from the compute
+// type (format only, see Store<S>::load/store).  Two 16-bit values go
+// through one paired conversion each way (cvt.rn.f16x2.f32 /
+// cvt.rn.bf16x2.f32 for the encode); every element rounds as the scalar
+// conversion would, so packed and single-value kernels agree bit for bit.
+template <typename S, int VX>
+struct PackCvt {
+  using R = typename Store<S>::R;
+  __device__ static __forceinline__ void load(const Pack<S, VX> &p, R (&v)[VX]) {
+#pragma unroll
+    for (int k = 0; k < VX; ++k) v[k] = Store<S>::load(p.v[k]);
+  }
+  __device__ static __forceinline__ Pack<S, VX> store(const R (&v)[VX]) {
+    Pack<S, VX> p;
+#pragma unroll
+    for (int k = 0; k < VX; ++k) p.v[k] = Store<S>::store(v[k]);
+    return p;
+  }
+};
+template <>
+struct PackCvt<__half, 2> {
+  __device__ static __forceinline__ void load(const Pack<__half, 2> &p, float (&v)[2]) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&p));
+    v[0] = f.x;
+    v[1] = f.y;
+  }
+  __device__ static __forceinline__ Pack<__half, 2> store(const float (&v)[2]) {
+    const __half2 h = __floats2half2_rn(v[0], v[1]);  // .x (low half, v[0]) first in memory
+    return *reinterpret_cast<const Pack<__half, 2> *>(&h);
+  }
+};
+template <>
+struct PackCvt<__nv_bfloat16, 2> {
+  __device__ static __forceinline__ void load(const Pack<__nv_bfloat16, 2> &p, float (&v)[2]) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&p));
+    v[0] = f.x;
+    v[1] = f.y;
+  }
+  __device__ static __forceinline__ Pack<__nv_bfloat16, 2> store(const float (&v)[2]) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
+    return *reinterpret_cast<const Pack<__nv_bfloat16, 2> *>(&h);
+  }
+};
+
 // Minimum resident 256-thread blocks per SM asked of the register allocator
 // for the vector kernel.  Measured on GB300 (FP32, local Gaussian noise,
 // two sites per thread): D2Q9 2048^2 is fastest at 4 blocks (<= 64
 // registers), D3Q19 256^3 at 3 (<= 85 registers); the unconstrained
 // allocation leaves D3Q19 one block per SM, and tighter caps spill.  FP64
 // kernels need more registers: 2.
-template <int LAT, typename S>
+template <int LAT, typename S, int VX = 2>
 constexpr int step_min_blocks() {
+  if (VX == 4) return (sizeof(typename Store<S>::R) != 4 || LAT == kD3Q19) ? 2 : 3;
   if (sizeof(typename Store<S>::R) != 4) return 2;
   return LAT == kD3Q19 ? 3 : 4;
 }
 
 // Update of sites (x0 .. x0 + VX - 1, y, z) of one lattice (Lx % VX == 0).
-template <int LAT, typename S, int VX, int NOISE, class C = SrtCollide<LAT, typename Store<S>::R, NOISE>,
-          typename Idx = size_t>
-__device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a, int x0,
-                                              int y, int z, const C &collide = C()) {
+// Pull of sites (x0 .. x0 + VX - 1, y, z) into f[k][i] = f_i(x0 + k, t):
+// the first half of step_vec_body (Lx % VX == 0).  Returns the row offset
+// Lx (y + Ly z) of the sites.
+template <int LAT, typename S, int VX, typename Idx>
+__device__ __forceinline__ uint32_t vec_pull(const S *__restrict__ src, const StepArgs &a, int x0, int y, int z,
+                                             typename Store<S>::R (&f)[VX][Lattice<LAT>::Q]) {
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   using P = Pack<S, VX>;
@@ -172,9 +219,6 @@ __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__re
   const int ym = (y == 0 ? a.Ly : y) - 1, yp = (y + 1 == a.Ly) ? 0 : y + 1;
   const int zm = (z == 0 ? a.Lz : z) - 1, zp = (z + 1 == a.Lz) ? 0 : z + 1;
   const uint32_t Lx = static_cast<uint32_t>(a.Lx), Lxy = Lx * static_cast<uint32_t>(a.Ly);
-  const uint32_t row = Lx * static_cast<uint32_t>(y) + Lxy * static_cast<uint32_t>(z);
-
-  R f[VX][Q];
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int vx = L::v(i, 0), vy = L::v(i, 1), vz = L::v(i, 2);
@@ -182,39 +226,54 @@ __device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__re
     const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
     const uint32_t srow = Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
     const S *pop = src + (static_cast<Idx>(i) * static_cast<Idx>(a.N) + static_cast<Idx>(srow));
-    const R wr = store_offset<LAT, S>(i, a);
     const P pk = *reinterpret_cast<const P *>(pop + x0);
     R v[VX];
-#pragma unroll
-    for (int k = 0; k < VX; ++k) v[k] = Store<S>::get(pk.v[k], wr);
+    PackCvt<S, VX>::load(pk, v);
     if constexpr (vx == 0) {
 #pragma unroll
       for (int k = 0; k < VX; ++k) f[k][i] = v[k];
     } else if constexpr (vx > 0) {  // site x0 + k pulls from x0 + k - 1
-      f[0][i] = Store<S>::get(pop[xl], wr);
+      f[0][i] = Store<S>::load(pop[xl]);
 #pragma unroll
       for (int k = 1; k < VX; ++k) f[k][i] = v[k - 1];
     } else {  // site x0 + k pulls from x0 + k + 1
 #pragma unroll
       for (int k = 0; k < VX - 1; ++k) f[k][i] = v[k + 1];
-      f[VX - 1][i] = Store<S>::get(pop[xr], wr);
+      f[VX - 1][i] = Store<S>::load(pop[xr]);
     }
   });
-#pragma unroll
-  for (int k = 0; k < VX; ++k) collide(f[k], row + static_cast<uint32_t>(x0 + k), a);
-  static_for<Q>([&](auto I) {
+  return Lx * static_cast<uint32_t>(y) + Lxy * static_cast<uint32_t>(z);
+}
+
+// Store of f*_i of sites (x0 .. x0 + VX - 1) of the row at offset `row`:
+// the second half of step_vec_body (VX-wide stores).
+template <int LAT, typename S, int VX, typename Idx>
+__device__ __forceinline__ void vec_store(S *__restrict__ dst, const StepArgs &a, uint32_t row, int x0,
+                                          const typename Store<S>::R (&f)[VX][Lattice<LAT>::Q]) {
+  using R = typename Store<S>::R;
+  using P = Pack<S, VX>;
+  static_for<Lattice<LAT>::Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    const R wr = store_offset<LAT, S>(i, a);
-    P pk;
+    R v[VX];
 #pragma unroll
-    for (int k = 0; k < VX; ++k) pk.v[k] = Store<S>::put(f[k][i], wr);
+    for (int k = 0; k < VX; ++k) v[k] = f[k][i];
     *reinterpret_cast<P *>(dst + (static_cast<Idx>(i) * static_cast<Idx>(a.N) + static_cast<Idx>(row) + static_cast<Idx>(x0))) =
-        pk;
+        PackCvt<S, VX>::store(v);
   });
 }
 
+template <int LAT, typename S, int VX, int NOISE, class C = SrtCollideFor<LAT, S, NOISE>, typename Idx = size_t>
+__device__ __forceinline__ void step_vec_body(const S *__restrict__ src, S *__restrict__ dst, const StepArgs &a, int x0,
+                                              int y, int z, const C &collide = C()) {
+  typename Store<S>::R f[VX][Lattice<LAT>::Q];
+  const uint32_t row = vec_pull<LAT, S, VX, Idx>(src, a, x0, y, z, f);
+#pragma unroll
+  for (int k = 0; k < VX; ++k) collide(f[k], row + static_cast<uint32_t>(x0 + k), a);
+  vec_store<LAT, S, VX, Idx>(dst, a, row, x0, f);
+}
+
 template <int LAT, typename S, int VX, int NOISE, typename Idx>
-__global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
+__global__ void __launch_bounds__(256, step_min_blocks<LAT, S, VX>())
     k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   pdl_launch_dependents();
   const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
@@ -222,7 +281,7 @@ __global__ void __launch_bounds__(256, step_min_blocks<LAT, S>())
   const int z = blockIdx.z;
   pdl_wait();
   if (x0 >= a.Lx || y >= a.Ly) return;
-  step_vec_body<LAT, S, VX, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, Idx>(src, dst, a, x0, y, z);
+  step_vec_body<LAT, S, VX, NOISE, SrtCollideFor<LAT, S, NOISE>, Idx>(src, dst, a, x0, y, z);
 }
 
 // True when every value offset i N + site of a lattice fits 32 bits.
@@ -230,15 +289,6 @@ inline bool offsets_fit_32(int Q, int64_t N) {
   return static_cast<uint64_t>(Q) * static_cast<uint64_t>(N) <= 0xffffffffull;
 }
 
-inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block, int vx = 1) {
-  const int cols = Lx / vx;
-  int bx = 256;
-  while (bx > 32 && bx / 2 >= cols) bx /= 2;
-  int by = 256 / bx;
-  while (by > 1 && by / 2 >= Ly) by /= 2;
-  block = dim3(bx, by, 1);
-  grid = dim3((cols + bx - 1) / bx, (Ly + by - 1) / by, Lz);
-}
 
 // Programmatic dependent launch of the step kernels (a tuning knob; results
 // do not depend on it).  LBFD_STEP_PDL = 0 launches them plainly.
@@ -265,6 +315,8 @@ cudaError_t step_noise_idx(const S *s, S *d, const StepArgs &a, int vx, cudaStre
   cfg.attrs = attr;
   cfg.numAttrs = step_pdl() ? 1 : 0;
   if (vx == 2) return cudaLaunchKernelEx(&cfg, k_step_vec<LAT, S, 2, NOISE, Idx>, s, d, a);
+  if constexpr (sizeof(typename Store<S>::R) == 4)
+    if (vx == 4) return cudaLaunchKernelEx(&cfg, k_step_vec<LAT, S, 4, NOISE, Idx>, s, d, a);
   return cudaLaunchKernelEx(&cfg, k_step<LAT, S, NOISE, Idx>, s, d, a);
 }
 

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kSmallThreads)
     for (int s = threadIdx.x; s < a.N; s += blockDim.x) {
       const int x = s % a.Lx, r = s / a.Lx;
       const int y = r % a.Ly, z = r / a.Ly;
-      step_scalar_body<LAT, S, NOISE, SrtCollide<LAT, typename Store<S>::R, NOISE>, uint32_t>(from, to, sa, x, y, z);
+      step_scalar_body<LAT, S, NOISE, SrtCollideFor<LAT, S, NOISE>, uint32_t>(from, to, sa, x, y, z);
     }
     __syncthreads();
   }
@@ -137,12 +137,12 @@ __global__ void __launch_bounds__(kClusterThreads)
         const int so = static_cast<int>(static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) +
                                         Lxy * static_cast<uint32_t>(zs));
         const int owner = so / chunk;
-        f[i] = Store<S>::get(remote[from][owner][i * chunk + (so - owner * chunk)], store_offset<LAT, S>(i, args));
+        f[i] = Store<S>::load(remote[from][owner][i * chunk + (so - owner * chunk)]);
       });
-      collide_site<LAT, R, NOISE>(f, static_cast<uint32_t>(s), args);
+      collide_site<LAT, R, NOISE, Store<S>::kDeviation>(f, static_cast<uint32_t>(s), args);
       static_for<Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        own[from ^ 1][i * chunk + l] = Store<S>::put(f[i], store_offset<LAT, S>(i, args));
+        own[from ^ 1][i * chunk + l] = Store<S>::store(f[i]);
       });
     }
     cl.sync();  // the step's writes are visible cluster-wide before the next reads

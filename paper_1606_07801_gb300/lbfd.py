@@ -29,9 +29,9 @@ POLICY_FIFO, POLICY_SHORTEST = 0, 1
 WALK_STRIDED, WALK_CONTIGUOUS, WALK_PER_TILE, WALK_PARAM = 0, 1, 2, 3
 REQ_UNKNOWN, REQ_QUEUED, REQ_RUNNING, REQ_DONE = -1, 0, 1, 2
 MAX_Q, MAX_MODES = 19, 16
-KERNEL_AUTO, KERNEL_VEC, KERNEL_SCALAR, KERNEL_SMALL, KERNEL_CLUSTER, KERNEL_MRT = 0, 1, 2, 3, 4, 5
+KERNEL_AUTO, KERNEL_VEC, KERNEL_SCALAR, KERNEL_SMALL, KERNEL_CLUSTER, KERNEL_MRT, KERNEL_STAGED = 0, 1, 2, 3, 4, 5, 6
 KERNEL_NAMES = {KERNEL_VEC: "k_step_vec", KERNEL_SCALAR: "k_step", KERNEL_SMALL: "k_step_small",
-                KERNEL_CLUSTER: "k_step_cluster", KERNEL_MRT: "k_step_mrt"}
+                KERNEL_CLUSTER: "k_step_cluster", KERNEL_MRT: "k_step_mrt", KERNEL_STAGED: "k_step_staged"}
 
 Q_OF = {D1Q3: 3, D2Q9: 9, D3Q19: 19, D2Q5: 5}
 D_OF = {D1Q3: 1, D2Q9: 2, D3Q19: 3, D2Q5: 2}
@@ -44,7 +44,9 @@ class Options(ctypes.Structure):
         ("init", c_int32), ("device", c_int32), ("dims", c_int64 * 3), ("tau", c_double),
         ("rho_mean", c_double), ("sine_amp", c_double), ("sine_k", c_int32 * 3), ("lattice_id", c_uint32),
         ("seed", c_uint64), ("stream", c_void_p), ("f_dev", c_void_p * 2), ("n_modes", c_int32),
-        ("modes", (c_int32 * 3) * MAX_MODES), ("step_kernel", c_int32), ("reserved", c_int32 * 7),
+        ("modes", (c_int32 * 3) * MAX_MODES), ("step_kernel", c_int32), ("wait_test_bytes", c_int32),
+        ("slab_global", c_int32), ("slab_first", c_int32), ("sample_every", c_int32),
+        ("reserved", c_int32 * 3),
         ("theta", c_double),
         ("tau_moments", c_double * MAX_Q),
     ]
@@ -113,7 +115,11 @@ SIGNATURES = {
     "lbfd_destroy": (c_int32, [c_void_p]),
     "lbfd_step": (c_int32, [c_void_p, c_int64]),
     "lbfd_step_kernel": (c_int32, [c_void_p, c_int64, P(c_int32)]),
+    "lbfd_set_sample_every": (c_int32, [c_void_p, c_int32]),
     "lbfd_sync": (c_int32, [c_void_p]),
+    "lbfd_slab_bounds": (c_int32, [c_int64, c_int32, c_int32, P(c_int64), P(c_int64)]),
+    "lbfd_slab_cross": (c_int32, [c_int32, c_int32, c_void_p, P(c_int32)]),
+    "lbfd_slab_halo": (c_int32, [c_int32, P(c_int64), c_int32, c_void_p, c_void_p, P(c_int32), P(c_int64)]),
     "lbfd_get_t": (c_int32, [c_void_p, P(c_int64)]),
     "lbfd_set_t": (c_int32, [c_void_p, c_int64]),
     "lbfd_get_f": (c_int32, [c_void_p, c_void_p]),
@@ -234,10 +240,42 @@ def lbfd_step(h: int, n: int) -> None:
     _check(load().lbfd_step(h, n), "lbfd_step")
 
 
+def lbfd_set_sample_every(h: int, every: int) -> None:
+    _check(load().lbfd_set_sample_every(h, every), "lbfd_set_sample_every")
+
+
 def lbfd_step_kernel(h: int, n: int) -> int:
     k = c_int32()
     _check(load().lbfd_step_kernel(h, n, ctypes.byref(k)), "lbfd_step_kernel")
     return k.value
+
+
+def lbfd_slab_bounds(global_planes: int, nranks: int, rank: int):
+    """(first plane, plane count) of rank's slab."""
+    first, count = c_int64(), c_int64()
+    _check(load().lbfd_slab_bounds(global_planes, nranks, rank, ctypes.byref(first), ctypes.byref(count)),
+           "lbfd_slab_bounds")
+    return first.value, count.value
+
+
+def lbfd_slab_cross(lattice: int, direction: int) -> list:
+    """Populations with velocity component `direction` along the slowest axis."""
+    pops = np.zeros(MAX_Q, dtype=np.int32)
+    n = c_int32()
+    _check(load().lbfd_slab_cross(lattice, direction, _ptr(pops), ctypes.byref(n)), "lbfd_slab_cross")
+    return [int(x) for x in pops[: n.value]]
+
+
+def lbfd_slab_halo(lattice: int, dims, face: int):
+    """(send offsets, receive offsets, values per plane) of one face of a slab
+    with owned dims `dims`; offsets are values into its stored state."""
+    d = (c_int64 * 3)(*[int(x) for x in dims] + [1] * (3 - len(dims)))
+    send = np.zeros(MAX_Q, dtype=np.int64)
+    recv = np.zeros(MAX_Q, dtype=np.int64)
+    n, plane = c_int32(), c_int64()
+    _check(load().lbfd_slab_halo(lattice, d, face, _ptr(send), _ptr(recv), ctypes.byref(n), ctypes.byref(plane)),
+           "lbfd_slab_halo")
+    return send[: n.value].copy(), recv[: n.value].copy(), plane.value
 
 
 def lbfd_sync(h: int) -> None:
@@ -269,11 +307,14 @@ def lbfd_get_f(h: int, out: np.ndarray | None = None) -> np.ndarray:
     return out
 
 
-def lbfd_set_f(h: int, f: np.ndarray) -> None:
+def lbfd_set_f(h: int, f: np.ndarray, stored_sites: int | None = None) -> None:
+    """stored_sites: for a slab handle, its owned planes plus both halo
+    planes (what lbfd_set_f takes); default the handle's N."""
     Q, D, N, _ = lbfd_query(h)
+    n = N if stored_sites is None else int(stored_sites)
     f = np.ascontiguousarray(f, dtype=np.float64)
-    if f.size != Q * N:
-        raise ValueError(f"f must hold Q*N = {Q * N} values")
+    if f.size != Q * n:
+        raise ValueError(f"f must hold Q*N = {Q * n} values")
     _check(load().lbfd_set_f(h, _ptr(f)), "lbfd_set_f")
 
 

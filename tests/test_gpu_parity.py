@@ -18,6 +18,8 @@ import pytest
 import paper_1606_07801_gb300 as lb
 from paper_1606_07801_gb300 import abi, synth
 
+from .slope_bound import oracle_run_with_slope
+
 pytestmark = pytest.mark.gpu
 
 TOL = {lb.F64: 1e-12, lb.F32: 2e-5}
@@ -104,22 +106,9 @@ def test_low_density_local_noise(orc):
     lat, dims, rho = lb.D2Q9, (128, 96), 0.5
     Q, N = 9, 128 * 96
     f0 = synth.random_populations(Q, N, rho, 0.3, seed=99)
-    # The oracle one step at a time, to see how close the pre-collision
-    # density came to zero.  The local noise amplitude is sqrt(c max(rho, 0))
-    # (eq. xilocal with the clamp of Sec. IV), whose slope 1/(2 sqrt(rho))
-    # scales a rounding difference in rho; at rho = rho_mean that slope is
-    # what the 1e-12 rho_mean bar allows for, so the bar is scaled by
-    # sqrt(rho_mean / |rho|) at the closest approach.  |rho| is floored at the
-    # rounding of the Q-term FP64 density sum, Q 2^-53 sum_i |f_i|, below
-    # which the two sides may see opposite signs of rho.
-    f, amp, t = f0.copy(), 1.0, 0
-    while t < 200:
-        r = f.sum(0)
-        floor = Q * 2.0 ** -53 * np.abs(f).sum(0)
-        amp = max(amp, float(np.max(np.sqrt(rho / np.maximum(np.abs(r), floor)))))
-        f = _oracle_run(orc, lat, dims, f, 1, 0.8, rho_mean=rho, seed=21, t0=t)
-        t += 1
-    o = f
+    # FP64 bar scaled by the slope of the clamped noise amplitude at the
+    # run's closest approach to zero density (tests/slope_bound.py)
+    o, amp = oracle_run_with_slope(orc, lat, dims, f0, 200, 0.8, rho, 21)
     assert (o.sum(0) < 0).mean() > 0.01  # the clamp is exercised
     g64 = _gpu_run(lat, dims, f0, 200, 0.8, lb.F64, rho_mean=rho, seed=21)
     err64 = np.abs(g64 - o)
