@@ -53,8 +53,10 @@ WORKLOADS = {
 ELEM_BYTES = {0: 4, 1: 8, 2: 2, 3: 2}
 DTYPE_NAME = {0: "f32", 1: "f64", 2: "f32 (f16 storage)", 3: "f32 (bf16 storage)"}
 Q_OF = {0: 3, 1: 9, 2: 19}
+# sources of the step kernel k_step_vec and of the choice of its sites per thread
 KERNEL_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_07801_gb300/csrc/device.cuh",
-                  "paper_1606_07801_gb300/csrc/step_d2q9.cu", "paper_1606_07801_gb300/csrc/step_d3q19.cu"]
+                  "paper_1606_07801_gb300/csrc/step_shape.h", "paper_1606_07801_gb300/csrc/step_d2q9.cu",
+                  "paper_1606_07801_gb300/csrc/step_d3q19.cu"]
 # sources of the batched kernel (k_batch_tile / k_batch_step)
 BATCH_SOURCES = ["paper_1606_07801_gb300/csrc/step_kernels.cuh", "paper_1606_07801_gb300/csrc/device.cuh",
                  "paper_1606_07801_gb300/csrc/batch_kernels.cuh", "paper_1606_07801_gb300/csrc/fastdiv.cuh",

@@ -533,13 +533,10 @@ int lbfd_step(lbfd_t h, int64_t n) {
     void *dst = h->f[h->cur ^ 1];
     if (steps_to_sample(h, h->t) == 0) {
       if (fusable) {
-        // the step and the observables of the state it reads, in one pass
-        int nblocks = 0;
+        // the step and the observables of the state it reads in one pass,
+        // then stage 2 of the observables
         cudaError_t e = launch_step_sample(o.lattice, o.precision, src, dst, a, o.n_modes, h->phase, h->partials,
-                                           &nblocks, h->staged_ok, h->status_dev, h->stream);
-        if (e == cudaSuccess)
-          e = launch_obs_pull_finalize(o.lattice, h->partials, nblocks, o.n_modes, h->N, o.rho_mean, h->fin, h->acc,
-                                       h->stream);
+                                           h->fin, h->acc, h->staged_ok, h->status_dev, h->stream);
         if (e != cudaSuccess) return cuda_fail("lbfd_step: sampled step", e);
         h->n_samples += 1;
         h->cur ^= 1;

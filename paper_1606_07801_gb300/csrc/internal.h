@@ -10,6 +10,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "device.cuh"
+#include "step_shape.h"
 
 #define LBFD_MAX_MODES_DEV 16
 #define LBFD_MAX_Q_DEV 19
@@ -95,43 +96,6 @@ template <>
 __host__ __device__ __forceinline__ double step_param<double>(double d, float) { return d; }
 template <>
 __host__ __device__ __forceinline__ float step_param<float>(double, float f) { return f; }
-
-// Sites per thread of the register-pull step kernel (k_step_vec; 1 is
-// k_step): 4 (16-byte loads and stores of FP32) where that measured faster on
-// GB300 and Lx allows, else 2 where Lx is even, else 1.  Four sites won for
-// D2Q9 in every FP32-arithmetic format (84.5 against 83.9 GLUPS at 2048^2)
-// and for D3Q19 with 16-bit storage (37.9 against 37.6 at 256^3); D3Q19 in
-// FP32 needs too many registers for four (31.7 against 38.9), and FP64 keeps
-// two.  A tuning knob only; results do not depend on it.  LBFD_STEP_VX = 1,
-// 2 or 4 overrides the choice where Lx allows.
-inline int step_vec_width(int lattice, int precision, int32_t Lx) {
-  static int forced = [] {
-    const char *e = getenv("LBFD_STEP_VX");
-    const int r = e ? atoi(e) : 0;
-    return (r == 1 || r == 2 || r == 4) ? r : 0;
-  }();
-  int vx = forced;
-  if (vx == 0) {
-    const bool four = precision != kStoreF64 && (lattice == kD2Q9 || (lattice == kD3Q19 && precision != kStoreF32));
-    vx = four ? 4 : 2;
-  }
-  if (vx == 4 && precision == kStoreF64) vx = 2;
-  if (Lx % vx == 0) return vx;
-  return Lx % 2 == 0 ? 2 : 1;
-}
-
-// Block and grid of the one-launch-per-step kernels for vx sites per thread:
-// 256-thread blocks, x fastest (at least one warp along x), one grid plane
-// per z.
-inline void step_shape(int32_t Lx, int32_t Ly, int32_t Lz, dim3 &grid, dim3 &block, int vx = 1) {
-  const int cols = Lx / vx;
-  int bx = 256;
-  while (bx > 32 && bx / 2 >= cols) bx /= 2;
-  int by = 256 / bx;
-  while (by > 1 && by / 2 >= Ly) by /= 2;
-  block = dim3(bx, by, 1);
-  grid = dim3((cols + bx - 1) / bx, (Ly + by - 1) / by, Lz);
-}
 
 // CTAs of the many-steps-per-launch path for a small lattice: 1 = one block
 // (k_step_small), 2..8 = a thread-block cluster (k_step_cluster), 0 = the
@@ -276,6 +240,29 @@ __host__ __device__ __forceinline__ float obs_offset(int i, float rho_f) {
   return mul_rn(static_cast<float>(Lattice<LAT>::w(i)), rho_f);
 }
 
+// Entry k of the observable accumulators ([sum rho, sum rho^2, sum f_i (Q),
+// sum f_i f_j (Q x Q), |rho(k_m)|^2 (K)]) from the totals tt of a sample's
+// deviation sums in the layout of the FP32 observable pass ([sum delta,
+// sum delta^2, sum e_i (Q), (re, im) of the K modes, pairs i <= j
+// row-major]), with cs[i] = c_i, C = sum_i c_i and Nd sites: rho = C +
+// delta and f_i = c_i + e_i expanded, in FP64.
+template <int Q>
+__device__ __forceinline__ double obs_restore(int k, const double *tt, const double *cs, double C, double Nd, int K) {
+  const int nq1 = 2 + Q + 2 * K;
+  if (k == 0) return tt[0] + Nd * C;
+  if (k == 1) return tt[1] + 2.0 * C * tt[0] + Nd * C * C;
+  if (k < 2 + Q) return tt[k] + Nd * cs[k - 2];
+  if (k < 2 + Q + Q * Q) {
+    const int r = k - 2 - Q, a = r / Q, b = r - a * Q;
+    const int i = a < b ? a : b, j = a < b ? b : a;
+    const int p = i * Q - i * (i - 1) / 2 + (j - i);
+    return tt[nq1 + p] + cs[j] * tt[2 + i] + cs[i] * tt[2 + j] + Nd * cs[i] * cs[j];
+  }
+  const int m = k - 2 - Q - Q * Q;
+  const double re = tt[2 + Q + 2 * m], im = tt[3 + Q + 2 * m];
+  return re * re + im * im;
+}
+
 // Stage 2 for partials in the layout of the FP32-arithmetic observable pass
 // (nblocks <= kObsBlocks): sums them in block order, restores the sums of rho,
 // f and f f from the deviation sums, and adds them into acc.
@@ -283,11 +270,12 @@ cudaError_t launch_obs_pull_finalize(int lattice, const double *partials, int nb
                                      double rho_mean, double *fin, double *acc, cudaStream_t stream);
 
 // A step fused with the sampled observables of the state it reads (the
-// FP32-arithmetic formats; sample_kernels.cuh): the observables of f(x, t)
-// go into per-block partials (nblocks written to *nblocks, <= kObsBlocks) in
-// the layout launch_obs_pull_finalize takes, and f(x, t) is advanced one
-// step from src to dst exactly as launch_step does.  phase: the per-axis
-// structure-factor tables (obs_phase_fill); n_modes <= kFusedModes.
+// FP32-arithmetic formats; sample_kernels.cuh): f(x, t) is advanced one step
+// from src to dst exactly as launch_step does, its observables go into
+// per-block partials (at most kObsBlocks sets, in the layout of the FP32
+// observable pass), and launch_obs_pull_finalize (fin, acc) adds them into
+// the accumulators: two launches.  phase: the per-axis structure-factor
+// tables (obs_phase_fill); n_modes <= kFusedModes.
 constexpr int kFusedModes = 4;
 // Whether a lattice can take the fused step-and-sample kernel: FP32
 // arithmetic, fewer than 2^31 sites, at most kFusedModes modes with their
@@ -303,28 +291,28 @@ inline bool sample_fusable(int lattice, int precision, int32_t Lx, int32_t Ly, i
   return block.x * block.y == 256 && block.x % 32 == 0;
 }
 cudaError_t launch_step_sample_d1q3(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                    const void *phase, double *partials, int *nblocks, bool staged_ok, int *status,
-                                    cudaStream_t stream);
+                                    const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                    int *status, cudaStream_t stream);
 cudaError_t launch_step_sample_d2q9(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                    const void *phase, double *partials, int *nblocks, bool staged_ok, int *status,
-                                    cudaStream_t stream);
+                                    const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                    int *status, cudaStream_t stream);
 cudaError_t launch_step_sample_d3q19(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                     const void *phase, double *partials, int *nblocks, bool staged_ok, int *status,
-                                     cudaStream_t stream);
+                                     const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                     int *status, cudaStream_t stream);
 // staged_ok: the lattice and buffers meet the staged kernel's requirements
 // (staged_fits); status: its bounded waits' status word.
 inline cudaError_t launch_step_sample(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
-                                      int n_modes, const void *phase, double *partials, int *nblocks, bool staged_ok,
-                                      int *status, cudaStream_t stream) {
+                                      int n_modes, const void *phase, double *partials, double *fin, double *acc,
+                                      bool staged_ok, int *status, cudaStream_t stream) {
   switch (lattice) {
     case kD1Q3:
-      return launch_step_sample_d1q3(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
+      return launch_step_sample_d1q3(precision, src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status,
                                      stream);
     case kD2Q9:
-      return launch_step_sample_d2q9(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
+      return launch_step_sample_d2q9(precision, src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status,
                                      stream);
     case kD3Q19:
-      return launch_step_sample_d3q19(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
+      return launch_step_sample_d3q19(precision, src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status,
                                       stream);
   }
   return cudaErrorInvalidValue;

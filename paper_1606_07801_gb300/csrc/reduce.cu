@@ -17,6 +17,7 @@
 #include "device.cuh"
 #include "fastdiv.cuh"
 #include "internal.h"
+#include "step_kernels.cuh"
 
 namespace lbfd {
 
@@ -518,8 +519,12 @@ __global__ void __launch_bounds__(kFinWarps * 32)
     k_obs_pull_finalize(const double *__restrict__ partials, int nblocks, int K, double Nd, float rho_f,
                         double *__restrict__ tot, unsigned int *__restrict__ ticket, double *__restrict__ acc) {
   constexpr int Q = Lattice<LAT>::Q;
-  const int nq1 = 2 + Q + 2 * K, npair = Q * (Q + 1) / 2, nq = nq1 + npair;
+  const int nq = 2 + Q + 2 * K + Q * (Q + 1) / 2;
   const int lane = threadIdx.x & 31, q = blockIdx.x * kFinWarps + (threadIdx.x >> 5);
+  // launched as a dependent of the kernel that wrote the partials: start
+  // the next launch early, and read only after that kernel has completed
+  pdl_launch_dependents();
+  pdl_wait();
   if (q < nq) {
     double t = 0.0;
     for (int b = lane; b < nblocks; b += 32) t += partials[static_cast<size_t>(b) * nq + q];
@@ -532,30 +537,26 @@ __global__ void __launch_bounds__(kFinWarps * 32)
   __shared__ bool last;
   if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
+  // the last block: the totals into shared memory (from L2: the other blocks
+  // wrote them), then one accumulator entry per thread
   __threadfence();
-  *ticket = 0u;  // for the next launch (stream-ordered after this one)
-  const volatile double *vt = tot;  // the other blocks' totals, from L2
-  double c[Q], C = 0.0;
-  for (int i = 0; i < Q; ++i) {
-    c[i] = static_cast<double>(obs_offset<LAT>(i, rho_f));
-    C += c[i];
+  __shared__ double tt[2 + LBFD_MAX_Q_DEV + 2 * LBFD_MAX_MODES_DEV + LBFD_MAX_Q_DEV * (LBFD_MAX_Q_DEV + 1) / 2];
+  __shared__ double cs[LBFD_MAX_Q_DEV + 1];
+  const volatile double *vt = tot;
+  for (int k = threadIdx.x; k < nq; k += blockDim.x) tt[k] = vt[k];
+  if (threadIdx.x < Q) cs[threadIdx.x] = static_cast<double>(obs_offset<LAT>(static_cast<int>(threadIdx.x), rho_f));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double C = 0.0;
+    for (int i = 0; i < Q; ++i) C += cs[i];
+    cs[Q] = C;
+    *ticket = 0u;  // for the next launch (stream-ordered after this one)
   }
-  const double Sd = vt[0], Sd2 = vt[1];
-  acc[0] += Sd + Nd * C;
-  acc[1] += Sd2 + 2.0 * C * Sd + Nd * C * C;
-  for (int i = 0; i < Q; ++i) acc[2 + i] += vt[2 + i] + Nd * c[i];
-  int p = 0;
-  for (int i = 0; i < Q; ++i)
-    for (int j = i; j < Q; ++j, ++p) {
-      const double v = vt[nq1 + p] + c[j] * vt[2 + i] + c[i] * vt[2 + j] + Nd * c[i] * c[j];
-      acc[2 + Q + i * Q + j] += v;
-      if (j != i) acc[2 + Q + j * Q + i] += v;
-    }
-  for (int m = 0; m < K; ++m) {
-    const double re = vt[2 + Q + 2 * m], im = vt[3 + Q + 2 * m];
-    acc[2 + Q + Q * Q + m] += re * re + im * im;
-  }
+  __syncthreads();
+  const double C = cs[Q];
+  const int nacc = 2 + Q + Q * Q + K;
+  for (int k = threadIdx.x; k < nacc; k += blockDim.x) acc[k] += obs_restore<Q>(k, tt, cs, C, Nd, K);
 }
 
 template <int LAT>
@@ -564,9 +565,17 @@ static cudaError_t pull_finalize_t(const double *partials, int nblocks, int n_mo
   constexpr int Q = Lattice<LAT>::Q;
   const int nq = obs_quantities(Q, n_modes);
   unsigned int *ticket = reinterpret_cast<unsigned int *>(fin + obs_quantities(Q, LBFD_MAX_MODES_DEV));
-  k_obs_pull_finalize<LAT><<<(nq + kFinWarps - 1) / kFinWarps, kFinWarps * 32, 0, stream>>>(
-      partials, nblocks, n_modes, double(N), rho_f, fin, ticket, acc);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((nq + kFinWarps - 1) / kFinWarps, 1, 1);
+  cfg.blockDim = dim3(kFinWarps * 32, 1, 1);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = step_pdl() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_obs_pull_finalize<LAT>, partials, nblocks, n_modes, double(N), rho_f, fin, ticket,
+                            acc);
 }
 
 // Stage 2 of the FP32-arithmetic observables for partials written by a

@@ -3,11 +3,17 @@
 With sample_every = s, lbfd_step adds the observables of f(x, t) at every
 step t with t mod s == 0 (paper Sec. IV: sums of rho, rho^2, f_i, f_i f_j and
 |rho(k)|^2, eqs. rhoth, dijexp, fkfk).  For the FP32-arithmetic formats this
-runs in one pass with the step.  The state must evolve bit for bit as
-without sampling; the accumulated sums must match FP64 sums over the same
-stored states to what FP32 partial sums of at most 256 terms allow (the
-bounds of the separate sampling pass's test); the launch count shows that
-the fused path ran."""
+runs in one pass with the step, plus the stage-2 kernel of the sample.  The
+state must evolve bit for bit as without sampling; the accumulated sums
+must match FP64 sums over the same stored states to what the fused path's
+FP32 sums allow, well inside the bounds below (those of the separate
+sampling pass's test):
+  - D1Q3, D2Q9: each lane adds FP32 products over at most 128 sites, then an
+    FP32 butterfly over the warp (5 more additions), then FP64;
+  - D3Q19: products of TF32 parts (hi hi + hi lo + lo hi, FP32-accurate)
+    added by the tensor cores in FP32 over at most 256 sites, folded in FP32
+    over at most 2048, then FP64: about 100 roundings of 2^-24 in all.
+The launch count shows that the fused path ran."""
 import numpy as np
 import pytest
 
