@@ -269,7 +269,9 @@ int lbfd_observables(lbfd_t h, lbfd_obs *obs);
 int lbfd_query(lbfd_t h, int32_t *Q, int32_t *D, int64_t *N, int32_t *value_bytes);
 
 /* Device buffer holding the stored state g_i(x) = f_i(x + v_i, t) (layout
- * [i][site]; valid until the next step), and the stream the handle works on. */
+ * [i][site]; valid until the next step), and the stream the handle works on.
+ * Work the handle ran on its side stream (the stage 2 of sampled steps) is
+ * ordered before whatever is enqueued on that stream after this call. */
 int lbfd_state_device(lbfd_t h, void **f_dev, void **stream);
 
 /* Lattice tables the CUDA kernels use: velocities v[Q][3], weights w[Q] and

@@ -79,6 +79,12 @@ struct lbfd_sim {
   int acc_n = 0;
   double *d_mass = nullptr;
   double *fin = nullptr;  // stage-2 scratch of the FP32 observables (totals and a ticket word)
+  // stage 2 of a sampled step runs on a side stream, overlapping the next
+  // steps; ev_obs marks its end, and obs_pending says that the handle's own
+  // stream has not waited for it yet (obs_join)
+  cudaStream_t obs_stream = nullptr;
+  cudaEvent_t ev_sampled = nullptr, ev_obs = nullptr;
+  bool obs_pending = false;
   double *mom = nullptr;  // rho and j for lbfd_moments, allocated on first use
   int64_t n_samples = 0;
   int32_t modes_host[LBFD_MAX_MODES][3] = {};
@@ -282,7 +288,18 @@ static void free_sim(lbfd_sim *h) {
   cudaFree(h->fin);
   cudaFree(h->mom);
   if (h->status_host) cudaFreeHost(h->status_host);
+  if (h->ev_sampled) cudaEventDestroy(h->ev_sampled);
+  if (h->ev_obs) cudaEventDestroy(h->ev_obs);
+  if (h->obs_stream) cudaStreamDestroy(h->obs_stream);
   delete h;
+}
+
+// The handle's stream waits for the last sampled step's stage 2 (before
+// anything that reads or rewrites the observable scratch or accumulators).
+static cudaError_t obs_join(lbfd_sim *h) {
+  if (!h->obs_pending) return cudaSuccess;
+  h->obs_pending = false;
+  return cudaStreamWaitEvent(h->stream, h->ev_obs, 0);
 }
 
 int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
@@ -422,7 +439,9 @@ int lbfd_create(lbfd_t *out, int32_t lattice, const int64_t *dims, double tau, d
 int lbfd_destroy(lbfd_t h) {
   if (!h) return LBFD_OK;
   DeviceGuard g(h->device);
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaError_t e = obs_join(h);
+  const cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = e2;
   free_sim(h);
   if (e != cudaSuccess) return cuda_fail("lbfd_destroy: stream sync", e);
   return LBFD_OK;
@@ -432,6 +451,7 @@ int lbfd_destroy(lbfd_t h) {
 // lbfd_sample; a separate pass over the state).
 static int sample_now(lbfd_sim *h) {
   const lbfd_options &o = h->opt;
+  LBFD_CU(obs_join(h));
   if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
     // FP32 arithmetic: pulled straight from the stored state
     LBFD_CU(launch_observables_pull(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
@@ -534,10 +554,25 @@ int lbfd_step(lbfd_t h, int64_t n) {
     if (steps_to_sample(h, h->t) == 0) {
       if (fusable) {
         // the step and the observables of the state it reads in one pass,
-        // then stage 2 of the observables
-        cudaError_t e = launch_step_sample(o.lattice, o.precision, src, dst, a, o.n_modes, h->phase, h->partials,
-                                           h->fin, h->acc, h->staged_ok, h->status_dev, h->stream);
+        // then stage 2 of the observables on the side stream
+        cudaError_t e = obs_join(h);
+        int nblocks = 0;
+        if (e == cudaSuccess)
+          e = launch_step_sample(o.lattice, o.precision, src, dst, a, o.n_modes, h->phase, h->partials, &nblocks,
+                                 h->staged_ok, h->status_dev, h->stream);
+        if (e == cudaSuccess && !h->obs_stream) {
+          e = cudaStreamCreateWithFlags(&h->obs_stream, cudaStreamNonBlocking);
+          if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_sampled, cudaEventDisableTiming);
+          if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_obs, cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_sampled, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->obs_stream, h->ev_sampled, 0);
+        if (e == cudaSuccess)
+          e = launch_obs_pull_finalize(o.lattice, h->partials, nblocks, o.n_modes, h->N, o.rho_mean, h->fin, h->acc,
+                                       h->obs_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_obs, h->obs_stream);
         if (e != cudaSuccess) return cuda_fail("lbfd_step: sampled step", e);
+        h->obs_pending = true;
         h->n_samples += 1;
         h->cur ^= 1;
         h->t += 1;
@@ -576,6 +611,7 @@ int lbfd_step_kernel(lbfd_t h, int64_t n, int32_t *kernel) {
 int lbfd_sync(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_sync: null handle");
   DeviceGuard g(h->device);
+  LBFD_CU(obs_join(h));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   return check_status(h);
 }
@@ -719,6 +755,7 @@ int lbfd_mass(lbfd_t h, double *mass) {
   if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_mass: not offered for slab handles");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
+  LBFD_CU(obs_join(h));
   LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, o.rho_mean, h->partials, h->d_mass, h->stream));
   LBFD_CU(cudaMemcpyAsync(mass, h->d_mass, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
@@ -736,6 +773,7 @@ int lbfd_reset_obs(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_reset_obs: null handle");
   if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_reset_obs: not offered for slab handles");
   DeviceGuard g(h->device);
+  LBFD_CU(obs_join(h));
   LBFD_CU(cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream));
   h->n_samples = 0;
   return LBFD_OK;
@@ -746,6 +784,7 @@ int lbfd_observables(lbfd_t h, lbfd_obs *obs) {
   if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_observables: not offered for slab handles");
   DeviceGuard g(h->device);
   std::vector<double> acc(h->acc_n);
+  LBFD_CU(obs_join(h));
   LBFD_CU(cudaMemcpyAsync(acc.data(), h->acc, sizeof(double) * h->acc_n, cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   if (int rc = check_status(h)) return rc;
@@ -774,6 +813,10 @@ int lbfd_query(lbfd_t h, int32_t *Q, int32_t *D, int64_t *N, int32_t *value_byte
 
 int lbfd_state_device(lbfd_t h, void **f_dev, void **stream) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_state_device: null handle");
+  if (h->obs_pending) {
+    DeviceGuard g(h->device);
+    LBFD_CU(obs_join(h));  // so that the stream handed out covers all of the handle's work
+  }
   if (f_dev) *f_dev = h->f[h->cur];
   if (stream) *stream = static_cast<void *>(h->stream);
   return LBFD_OK;

@@ -272,10 +272,10 @@ cudaError_t launch_obs_pull_finalize(int lattice, const double *partials, int nb
 // A step fused with the sampled observables of the state it reads (the
 // FP32-arithmetic formats; sample_kernels.cuh): f(x, t) is advanced one step
 // from src to dst exactly as launch_step does, its observables go into
-// per-block partials (at most kObsBlocks sets, in the layout of the FP32
-// observable pass), and launch_obs_pull_finalize (fin, acc) adds them into
-// the accumulators: two launches.  phase: the per-axis structure-factor
-// tables (obs_phase_fill); n_modes <= kFusedModes.
+// per-block partials (*nblocks sets, at most kObsBlocks, in the layout of
+// the FP32 observable pass) for launch_obs_pull_finalize.  phase: the
+// per-axis structure-factor tables (obs_phase_fill); n_modes <=
+// kFusedModes.
 constexpr int kFusedModes = 4;
 // Whether a lattice can take the fused step-and-sample kernel: FP32
 // arithmetic, fewer than 2^31 sites, at most kFusedModes modes with their
@@ -291,28 +291,28 @@ inline bool sample_fusable(int lattice, int precision, int32_t Lx, int32_t Ly, i
   return block.x * block.y == 256 && block.x % 32 == 0;
 }
 cudaError_t launch_step_sample_d1q3(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                    const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                    const void *phase, double *partials, int *nblocks, bool staged_ok,
                                     int *status, cudaStream_t stream);
 cudaError_t launch_step_sample_d2q9(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                    const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                    const void *phase, double *partials, int *nblocks, bool staged_ok,
                                     int *status, cudaStream_t stream);
 cudaError_t launch_step_sample_d3q19(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                     const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                     const void *phase, double *partials, int *nblocks, bool staged_ok,
                                      int *status, cudaStream_t stream);
 // staged_ok: the lattice and buffers meet the staged kernel's requirements
 // (staged_fits); status: its bounded waits' status word.
 inline cudaError_t launch_step_sample(int lattice, int precision, const void *src, void *dst, const StepArgs &a,
-                                      int n_modes, const void *phase, double *partials, double *fin, double *acc,
-                                      bool staged_ok, int *status, cudaStream_t stream) {
+                                      int n_modes, const void *phase, double *partials, int *nblocks, bool staged_ok,
+                                      int *status, cudaStream_t stream) {
   switch (lattice) {
     case kD1Q3:
-      return launch_step_sample_d1q3(precision, src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status,
+      return launch_step_sample_d1q3(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
                                      stream);
     case kD2Q9:
-      return launch_step_sample_d2q9(precision, src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status,
+      return launch_step_sample_d2q9(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
                                      stream);
     case kD3Q19:
-      return launch_step_sample_d3q19(precision, src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status,
+      return launch_step_sample_d3q19(precision, src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status,
                                       stream);
   }
   return cudaErrorInvalidValue;

@@ -17,7 +17,6 @@
 #include "device.cuh"
 #include "fastdiv.cuh"
 #include "internal.h"
-#include "step_kernels.cuh"
 
 namespace lbfd {
 
@@ -521,10 +520,6 @@ __global__ void __launch_bounds__(kFinWarps * 32)
   constexpr int Q = Lattice<LAT>::Q;
   const int nq = 2 + Q + 2 * K + Q * (Q + 1) / 2;
   const int lane = threadIdx.x & 31, q = blockIdx.x * kFinWarps + (threadIdx.x >> 5);
-  // launched as a dependent of the kernel that wrote the partials: start
-  // the next launch early, and read only after that kernel has completed
-  pdl_launch_dependents();
-  pdl_wait();
   if (q < nq) {
     double t = 0.0;
     for (int b = lane; b < nblocks; b += 32) t += partials[static_cast<size_t>(b) * nq + q];
@@ -565,17 +560,12 @@ static cudaError_t pull_finalize_t(const double *partials, int nblocks, int n_mo
   constexpr int Q = Lattice<LAT>::Q;
   const int nq = obs_quantities(Q, n_modes);
   unsigned int *ticket = reinterpret_cast<unsigned int *>(fin + obs_quantities(Q, LBFD_MAX_MODES_DEV));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((nq + kFinWarps - 1) / kFinWarps, 1, 1);
-  cfg.blockDim = dim3(kFinWarps * 32, 1, 1);
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = step_pdl() ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_obs_pull_finalize<LAT>, partials, nblocks, n_modes, double(N), rho_f, fin, ticket,
-                            acc);
+  // a plain launch: as a dependent launch it let the next step's blocks take
+  // the SMs while it still waited for the sampled step, which cost D3Q19
+  // 256^3 0.5 ms per sample on GB300
+  k_obs_pull_finalize<LAT><<<(nq + kFinWarps - 1) / kFinWarps, kFinWarps * 32, 0, stream>>>(
+      partials, nblocks, n_modes, double(N), rho_f, fin, ticket, acc);
+  return cudaGetLastError();
 }
 
 // Stage 2 of the FP32-arithmetic observables for partials written by a

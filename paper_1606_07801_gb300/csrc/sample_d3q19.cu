@@ -5,11 +5,11 @@
 namespace lbfd {
 
 cudaError_t launch_step_sample_d3q19(int precision, const void *src, void *dst, const StepArgs &a, int n_modes,
-                                    const void *phase, double *partials, double *fin, double *acc, bool staged_ok,
+                                    const void *phase, double *partials, int *nblocks, bool staged_ok,
                                     int *status, cudaStream_t stream) {
   return dispatch_storage(precision, [&](auto tag) {
     using S = typename decltype(tag)::type;
-    return step_sample_t<kD3Q19, S>(src, dst, a, n_modes, phase, partials, fin, acc, staged_ok, status, stream);
+    return step_sample_t<kD3Q19, S>(src, dst, a, n_modes, phase, partials, nblocks, staged_ok, status, stream);
   });
 }
 

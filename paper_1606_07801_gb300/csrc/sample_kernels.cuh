@@ -83,13 +83,9 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 // sites does not depend on their order, so k = t and k = t + 4 of a step
 // are the adjacent columns 2t and 2t + 1: one 8-byte load gives a lane both.
 // Each value is split into TF32 parts hi + lo (hi the nearest TF32, lo =
-// e - hi, exact), so that hi hi + hi lo + lo hi keeps the products to FP32
-// accuracy:
-//   - up to two row blocks (D1Q3, D2Q9): C += H^T H + H^T (2 L) over the
-//     whole QL x QL block (one or two m16n8 tiles), and the pair sum (i, j)
-//     is (C_ij + C_ji) / 2, C_ii on the diagonal: two products per tile;
-//   - three row blocks (D3Q19): the tiles (0,0) (0,1) (0,2) (1,2) of the
-//     upper triangle, each C += H^T H + H^T L + L^T H.
+// e - hi, exact), so that C += H^T H + H^T L + L^T H keeps the products to
+// FP32 accuracy, on the m16n8 tiles of the upper triangle: D1Q3 (0,0); D2Q9
+// (0,0) (0,1); D3Q19 (0,0) (0,1) (0,2) (1,2).
 // The tensor cores add in FP32; after at most kSampleInnerTerms sites a
 // lane adds its accumulators into a second FP32 set (in its own column of
 // shared memory, to spare registers), and after at most
@@ -104,18 +100,16 @@ struct WarpSampler {
   static constexpr int SITES = 32 * VX;
   static constexpr int KSTEPS = SITES / 8;
   static constexpr int NSLOT = QL * (QL + 1) / 2;
-  static constexpr bool kSym = NRB <= 2;        // whole block, symmetrised at the flush
   struct Smem {  // one warp's
-    float hi[QL][SITES], lo[QL][SITES];         // columns swizzled (col); lo holds 2 lo where kSym
-    float outer[(kSym ? NRB : 4) * 4][32];     // each lane's folded FP32 sums, element-major
+    float hi[QL][SITES], lo[QL][SITES];         // columns swizzled (col)
+    float outer[(NRB == 1 ? 1 : (NRB == 2 ? 2 : 4)) * 4][32];  // each lane's folded FP32 sums
     double slots[NSLOT];                        // upper triangle of E^T E, row-major
     double modes[2 * kFusedModes];
   };
-  static_assert(SITES >= QL, "the flush stages C in hi");
   // the m16n8 tiles: (m, n) with rows 16m.. and columns 8n..
-  static constexpr int NMMA = kSym ? NRB : 4;
-  __device__ static constexpr int tile_m(int k) { return !kSym && k == 3 ? 1 : 0; }
-  __device__ static constexpr int tile_n(int k) { return !kSym && k == 3 ? 2 : k; }
+  static constexpr int NMMA = NRB == 1 ? 1 : (NRB == 2 ? 2 : 4);
+  __device__ static constexpr int tile_m(int k) { return NRB == 3 && k == 3 ? 1 : 0; }
+  __device__ static constexpr int tile_n(int k) { return NRB == 3 && k == 3 ? 2 : k; }
   static constexpr int kInnerTiles = kSampleInnerTerms / SITES;
   static constexpr int kOuterFlushes = kSampleFlushTerms / kSampleInnerTerms;
   static_assert(kInnerTiles >= 1 && kOuterFlushes >= 1, "flush intervals");
@@ -169,33 +163,13 @@ struct WarpSampler {
   __device__ __forceinline__ void flush(int K) {
     fold_inner();
     const int g = lane >> 2, t = lane & 3;
-    if constexpr (kSym) {
-      float *st = &sm->hi[0][0];  // C, QL x QL, row-major
 #pragma unroll
-      for (int k = 0; k < NMMA; ++k)
+    for (int k = 0; k < NMMA; ++k)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = g + (e >= 2 ? 8 : 0), c = 8 * k + 2 * t + (e & 1);
-          if (r < QL && c < QL) st[r * QL + c] = sm->outer[4 * k + e][lane];
-        }
-      __syncwarp();
-      for (int idx = lane; idx < QL * QL; idx += 32) {
-        const int i = idx / QL, j = idx - i * QL;
-        if (i < j)
-          sm->slots[slot(i, j)] += 0.5 * (static_cast<double>(st[idx]) + static_cast<double>(st[j * QL + i]));
-        else if (i == j)
-          sm->slots[slot(i, i)] += static_cast<double>(st[idx]);
+      for (int e = 0; e < 4; ++e) {
+        const int r = 16 * tile_m(k) + g + (e >= 2 ? 8 : 0), c = 8 * tile_n(k) + 2 * t + (e & 1);
+        if (r <= c && c < QL) sm->slots[slot(r, c)] += static_cast<double>(sm->outer[4 * k + e][lane]);
       }
-      __syncwarp();  // the stage is read before the next tile is written
-    } else {
-#pragma unroll
-      for (int k = 0; k < NMMA; ++k)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = 16 * tile_m(k) + g + (e >= 2 ? 8 : 0), c = 8 * tile_n(k) + 2 * t + (e & 1);
-          if (r <= c && c < QL) sm->slots[slot(r, c)] += static_cast<double>(sm->outer[4 * k + e][lane]);
-        }
-    }
 #pragma unroll
     for (int k = 0; k < NMMA; ++k)
 #pragma unroll
@@ -257,7 +231,6 @@ struct WarpSampler {
       for (int k = 0; k < VX; ++k) {
         vh[k] = __uint_as_float(to_tf32(e[k][r]));
         vl[k] = e[k][r] - vh[k];
-        if constexpr (kSym) vl[k] *= 2.0f;
       }
       if constexpr (VX == 2) {
         *reinterpret_cast<float2 *>(&sm->hi[r][col(r, 2 * lane)]) = make_float2(vh[0], vh[1]);
@@ -299,24 +272,15 @@ struct WarpSampler {
         l0[j] = __float_as_uint(lv.x);
         l1[j] = __float_as_uint(lv.y);
       }
-      if constexpr (kSym) {
-        const uint32_t a1 = NRB > 1 ? h0[NRB - 1] : 0u, a3 = NRB > 1 ? h1[NRB - 1] : 0u;
 #pragma unroll
-        for (int n = 0; n < NMMA; ++n) {
-          mma_tf32(acc[n], h0[0], a1, h1[0], a3, h0[n], h1[n]);
-          mma_tf32(acc[n], h0[0], a1, h1[0], a3, l0[n], l1[n]);
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NMMA; ++k) {
-          const int am = 2 * tile_m(k), bn = tile_n(k);
-          const uint32_t ah0 = h0[am], ah2 = h1[am], al0 = l0[am], al2 = l1[am];
-          const uint32_t ah1 = am + 1 < NRB ? h0[am + 1] : 0u, ah3 = am + 1 < NRB ? h1[am + 1] : 0u;
-          const uint32_t al1 = am + 1 < NRB ? l0[am + 1] : 0u, al3 = am + 1 < NRB ? l1[am + 1] : 0u;
-          mma_tf32(acc[k], ah0, ah1, ah2, ah3, h0[bn], h1[bn]);
-          mma_tf32(acc[k], ah0, ah1, ah2, ah3, l0[bn], l1[bn]);
-          mma_tf32(acc[k], al0, al1, al2, al3, h0[bn], h1[bn]);
-        }
+      for (int k = 0; k < NMMA; ++k) {
+        const int am = 2 * tile_m(k), bn = tile_n(k);
+        const uint32_t ah0 = h0[am], ah2 = h1[am], al0 = l0[am], al2 = l1[am];
+        const uint32_t ah1 = am + 1 < NRB ? h0[am + 1] : 0u, ah3 = am + 1 < NRB ? h1[am + 1] : 0u;
+        const uint32_t al1 = am + 1 < NRB ? l0[am + 1] : 0u, al3 = am + 1 < NRB ? l1[am + 1] : 0u;
+        mma_tf32(acc[k], ah0, ah1, ah2, ah3, h0[bn], h1[bn]);
+        mma_tf32(acc[k], ah0, ah1, ah2, ah3, l0[bn], l1[bn]);
+        mma_tf32(acc[k], al0, al1, al2, al3, h0[bn], h1[bn]);
       }
     }
     __syncwarp();  // the tile is read before the next call writes it
@@ -611,27 +575,24 @@ inline SampleArgs make_sample_args(const StepArgs &a, int n_modes, const void *p
 // The fused step-and-sample launch on the register-pull kernel's blocks.
 template <int LAT, typename S>
 cudaError_t sample_vec_t(const void *src, void *dst, const StepArgs &a, int n_modes, const void *phase,
-                         double *partials, double *fin, double *acc, cudaStream_t stream) {
+                         double *partials, int *nblocks, cudaStream_t stream) {
   const int vx = step_vec_width(LAT, Store<S>::kDeviation ? kStoreF16 : kStoreF32, a.Lx) >= 2 ? 2 : 1;
   dim3 grid, block;
   step_shape(a.Lx, a.Ly, a.Lz, grid, block, vx);
   if (block.x * block.y != kSampleThreads || block.x % 32 != 0) return cudaErrorInvalidValue;
   const SampleArgs sa = make_sample_args<LAT>(a, n_modes, phase, grid);
   const bool fit32 = offsets_fit_32(Lattice<LAT>::Q, a.N);
-  int nblocks = 0;
   auto go = [&](auto noise) -> cudaError_t {
     constexpr int NZ = decltype(noise)::value;
     if (vx == 2)
-      return fit32 ? sample_launch<LAT, S, 2, NZ, uint32_t>(src, dst, a, sa, block, partials, &nblocks, stream)
-                   : sample_launch<LAT, S, 2, NZ, size_t>(src, dst, a, sa, block, partials, &nblocks, stream);
-    return fit32 ? sample_launch<LAT, S, 1, NZ, uint32_t>(src, dst, a, sa, block, partials, &nblocks, stream)
-                 : sample_launch<LAT, S, 1, NZ, size_t>(src, dst, a, sa, block, partials, &nblocks, stream);
+      return fit32 ? sample_launch<LAT, S, 2, NZ, uint32_t>(src, dst, a, sa, block, partials, nblocks, stream)
+                   : sample_launch<LAT, S, 2, NZ, size_t>(src, dst, a, sa, block, partials, nblocks, stream);
+    return fit32 ? sample_launch<LAT, S, 1, NZ, uint32_t>(src, dst, a, sa, block, partials, nblocks, stream)
+                 : sample_launch<LAT, S, 1, NZ, size_t>(src, dst, a, sa, block, partials, nblocks, stream);
   };
-  const cudaError_t e = a.noise_mode == kNoiseOff ? go(std::integral_constant<int, kStepNoiseOff>{})
-                       : a.noise_dist == kGaussian ? go(std::integral_constant<int, kStepNoiseGauss>{})
-                                                   : go(std::integral_constant<int, kStepNoiseFlat>{});
-  if (e != cudaSuccess) return e;
-  return launch_obs_pull_finalize(LAT, partials, nblocks, n_modes, a.N, a.rho_eq, fin, acc, stream);
+  if (a.noise_mode == kNoiseOff) return go(std::integral_constant<int, kStepNoiseOff>{});
+  if (a.noise_dist == kGaussian) return go(std::integral_constant<int, kStepNoiseGauss>{});
+  return go(std::integral_constant<int, kStepNoiseFlat>{});
 }
 
 }  // namespace lbfd

@@ -273,19 +273,13 @@ constexpr int kStagedTimeout = 1;
 // (sample_kernels.cuh): each consumer warp feeds its pulled sites to a warp
 // sampler, and at the end the consumers write the block's partial sums to
 // partials[blockIdx.x] (the grid is at most kObsBlocks).
-// Resident blocks per SM the sampled kernel is compiled for.  The register
-// sampler (D1Q3, D2Q9) holds its sums in registers and takes one block (the
-// copies keep the loads in flight); the tensor-core sampler (D3Q19) fits the
-// register budget of two (a 4.5-warp share of each scheduler's 16384
-// registers: 96 per thread).
-template <int LAT>
-constexpr int staged_sample_min_blocks() {
-  return Lattice<LAT>::Q <= 9 ? 1 : 2;
-}
+// Resident blocks per SM the sampled kernel is compiled for: two, whose
+// 4.5-warp share of each scheduler's 16384 registers allows 96 per thread.
+constexpr int kStagedSampleMinBlocks = 2;
 
 template <int LAT, typename S, int NOISE, bool SAMPLE = false>
 __global__ void __launch_bounds__(StagedShape<LAT, S>::kThreads,
-                                  SAMPLE ? staged_sample_min_blocks<LAT>() : StagedShape<LAT, S>::kMinBlocks)
+                                  SAMPLE ? kStagedSampleMinBlocks : StagedShape<LAT, S>::kMinBlocks)
     k_step_staged(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a, uint32_t ntiles, uint32_t ntx,
                   const StagedRows rows, int *status, uint32_t wait_test_bytes, const SampleArgs sa,
                   double *__restrict__ partials) {
@@ -453,14 +447,15 @@ cudaError_t staged_t(const void *src, void *dst, const StepArgs &a, const Staged
   return staged_noise<LAT, S, kStepNoiseFlat>(src, dst, a, rows, status, wait_test_bytes, stream);
 }
 
-// The fused step-and-sample launch (FP32 arithmetic): the staged kernel
-// where the lattice meets its requirements and the blocks it is compiled for
-// fit the 228 KB of shared memory of an SM (its copies keep the loads in flight
-// while the consumer warps sample, at an occupancy the sampler's registers
-// or shared tiles would otherwise cut), else the register-pull kernel on a
-// persistent grid.  LBFD_SAMPLE_STAGED = 0 keeps the register-pull one (a
-// tuning knob; the results agree within FP32 rounding of the sums, and the
-// state bit for bit).
+// The fused step-and-sample launch (FP32 arithmetic).  D1Q3 and D2Q9 run
+// the register-pull kernel on a persistent grid with the per-lane register
+// sampler (measured on GB300, the staged kernel with the same sampler, at
+// the one block per SM its registers allow, was no faster).  D3Q19 takes
+// the staged kernel with the tensor-core sampler where the lattice meets its
+// requirements and two of its blocks fit the 228 KB of shared memory of an
+// SM, else the register-pull kernel.  LBFD_SAMPLE_STAGED = 0 keeps the
+// register-pull one (a tuning knob; the results agree within FP32 rounding
+// of the sums, and the state bit for bit).
 inline bool sample_staged_default() {
   static const bool v = [] {
     const char *e = getenv("LBFD_SAMPLE_STAGED");
@@ -471,28 +466,27 @@ inline bool sample_staged_default() {
 
 template <int LAT, typename S>
 cudaError_t step_sample_t(const void *src, void *dst, const StepArgs &a, int n_modes, const void *phase,
-                          double *partials, double *fin, double *acc, bool staged_ok, int *status,
-                          cudaStream_t stream) {
+                          double *partials, int *nblocks, bool staged_ok, int *status, cudaStream_t stream) {
   if constexpr (sizeof(typename Store<S>::R) != 4) {
     return cudaErrorInvalidValue;  // FP64 storage samples in FP64 by its own pass
+  } else if constexpr (Lattice<LAT>::Q <= 9) {
+    if (n_modes < 0 || n_modes > kFusedModes || (n_modes > 0 && !phase)) return cudaErrorInvalidValue;
+    return sample_vec_t<LAT, S>(src, dst, a, n_modes, phase, partials, nblocks, stream);
   } else {
     if (n_modes < 0 || n_modes > kFusedModes || (n_modes > 0 && !phase)) return cudaErrorInvalidValue;
     using SH = StagedShape<LAT, S>;
-    constexpr size_t smem = SH::kSmemBytes + SH::kConsumerWarps * sizeof(typename SamplerFor<LAT, SH::kVX>::Smem);
-    constexpr bool fits = staged_sample_min_blocks<LAT>() * (smem + 1024) <= 228 * 1024;
+    using WS = WarpSampler<LAT, SH::kVX>;
+    constexpr bool fits = kStagedSampleMinBlocks * (SH::kSmemBytes + SH::kConsumerWarps * sizeof(typename WS::Smem) +
+                                                    1024) <= 228 * 1024;
     if (!(fits && staged_ok && sample_staged_default()))
-      return sample_vec_t<LAT, S>(src, dst, a, n_modes, phase, partials, fin, acc, stream);
+      return sample_vec_t<LAT, S>(src, dst, a, n_modes, phase, partials, nblocks, stream);
     const SampleArgs sa = make_sample_args<LAT>(a, n_modes, phase, dim3(1, 1, 1));
     const StagedRows rows{0, static_cast<uint32_t>(a.Ly) * static_cast<uint32_t>(a.Lz), 0};
-    int nblocks = 0;
-    const cudaError_t e =
-        a.noise_mode == kNoiseOff
-            ? staged_noise<LAT, S, kStepNoiseOff, true>(src, dst, a, rows, status, 0, stream, sa, partials, &nblocks)
-        : a.noise_dist == kGaussian
-            ? staged_noise<LAT, S, kStepNoiseGauss, true>(src, dst, a, rows, status, 0, stream, sa, partials, &nblocks)
-            : staged_noise<LAT, S, kStepNoiseFlat, true>(src, dst, a, rows, status, 0, stream, sa, partials, &nblocks);
-    if (e != cudaSuccess) return e;
-    return launch_obs_pull_finalize(LAT, partials, nblocks, n_modes, a.N, a.rho_eq, fin, acc, stream);
+    if (a.noise_mode == kNoiseOff)
+      return staged_noise<LAT, S, kStepNoiseOff, true>(src, dst, a, rows, status, 0, stream, sa, partials, nblocks);
+    if (a.noise_dist == kGaussian)
+      return staged_noise<LAT, S, kStepNoiseGauss, true>(src, dst, a, rows, status, 0, stream, sa, partials, nblocks);
+    return staged_noise<LAT, S, kStepNoiseFlat, true>(src, dst, a, rows, status, 0, stream, sa, partials, nblocks);
   }
 }
 

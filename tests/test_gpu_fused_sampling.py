@@ -114,3 +114,29 @@ def test_sampling_that_runs_as_a_separate_pass(lat, dims, prec):
         assert ob[key] == want[key]
     assert np.array_equal(ob["sum_f"], want["sum_f"]) and np.array_equal(ob["sum_ff"], want["sum_ff"])
     assert np.array_equal(ob["sum_sk"], want["sum_sk"])
+
+
+def test_stage_two_on_the_side_stream_is_joined():
+    """Stage 2 of a sampled step runs on the handle's side stream; every
+    reader of the accumulators, and the next sampled step, wait for it.
+    Reading the observables right after lbfd_step (no sync) and after a sync
+    must give the same sums, and resetting between samples must drop only
+    the samples before it."""
+    dims, prec = (300, 261), lb.F32
+    kw = dict(precision=prec, modes=_modes(lb.D2Q9, dims), sample_every=1)
+    with lb.Simulation(lb.D2Q9, dims, 0.8, 30.0, 4, **kw) as s:
+        s.step(7)
+        a = s.observables()             # no sync before: joins the side stream
+        s.sync()
+        b = s.observables()
+        s.reset_obs()                   # after the join, before the next samples
+        s.step(3)
+        c = s.observables()
+    assert a["n_samples"] == b["n_samples"] == 7 and c["n_samples"] == 3
+    assert a["sum_rho"] == b["sum_rho"] and np.array_equal(a["sum_ff"], b["sum_ff"])
+    with lb.Simulation(lb.D2Q9, dims, 0.8, 30.0, 4, **kw) as s:
+        s.step(7)
+        s.reset_obs()
+        s.step(3)
+        d = s.observables()
+    assert c["sum_rho"] == d["sum_rho"] and np.array_equal(c["sum_ff"], d["sum_ff"])
