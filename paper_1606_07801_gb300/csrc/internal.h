@@ -29,6 +29,7 @@ struct NvtxRange {
 // Per-launch arguments of the step kernel (passed by value).
 struct StepArgs {
   int32_t Lx, Ly, Lz;
+  int32_t sweep;       // one-launch-per-step kernels: 0 = work blocks in grid order, 1 = reversed
   int64_t N;           // sites
   double omega;        // 1 - 1/tau (what is left of the non-equilibrium part)
   double inv_tau;      // 1/tau

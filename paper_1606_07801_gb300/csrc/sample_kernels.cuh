@@ -494,8 +494,9 @@ __global__ void __launch_bounds__(kSampleThreads, 2)
   WS ws;
   ws.init(&wsm[warp], tid & 31);
 
-  pdl_launch_dependents();
-  pdl_wait();
+  // a plain launch (no programmatic dependent launch either way): as a
+  // dependent of a multi-wave step its persistent blocks cost D3Q19 256^3
+  // 0.5 ms per sample on GB300
   for (int vb = blockIdx.x; vb < sa.nvb; vb += gridDim.x) {
     const int vbx = vb % sa.gx, vr = vb / sa.gx;
     const int vby = vr % sa.gy, vbz = vr / sa.gy;
@@ -542,17 +543,8 @@ cudaError_t sample_launch(const void *src, void *dst, const StepArgs &a, const S
   }
   const int grid = std::max(1, std::min(sa_in.nvb, g));
   *nblocks = grid;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = step_pdl() ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, static_cast<const S *>(src), static_cast<S *>(dst), a, sa_in, partials);
+  kern<<<grid, block, smem, stream>>>(static_cast<const S *>(src), static_cast<S *>(dst), a, sa_in, partials);
+  return cudaGetLastError();
 }
 
 // Arguments of a fused sampled step for a lattice in FP32 arithmetic.

@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(StagedShape<LAT, S>::kThreads,
   __shared__ __align__(8) uint64_t full[NS], empty[NS];
   __shared__ StagedTile meta[NS];
 
-  pdl_launch_dependents();
+  if constexpr (!SAMPLE) pdl_launch_dependents();  // the sampled form is launched plainly (as k_step_sample)
   const uint32_t G = gridDim.x;
   const int warp = static_cast<int>(threadIdx.x) >> 5, lane = static_cast<int>(threadIdx.x) & 31;
   if (threadIdx.x == 0) {
@@ -432,7 +432,7 @@ cudaError_t staged_noise(const void *src, void *dst, const StepArgs &a, const St
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = step_pdl() ? 1 : 0;
+  cfg.numAttrs = step_pdl() && !SAMPLE ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<const S *>(src), static_cast<S *>(dst), a, ntiles, ntx, rows,
                             status, wait_test_bytes, sa, partials);
 }

@@ -77,8 +77,16 @@ struct SrtCollide {
 template <int LAT, typename S, int NOISE>
 using SrtCollideFor = SrtCollide<LAT, typename Store<S>::R, NOISE, Store<S>::kDeviation>;
 
-// Scalar kernel: one site per thread, any lattice shape.  S is the storage
-// type (float, double, or a 16-bit deviation format with FP32 arithmetic).
+// The work block of this CTA: its own index, or for sweep = 1 the mirror
+// image, so that a step launched after a forward one starts on the rows the
+// previous step wrote last, which are still in L2.  The hardware dispatches
+// CTAs in index order either way; which CTA takes which block changes
+// nothing else.
+__device__ __forceinline__ uint3 sweep_block(int32_t sweep) {
+  if (!sweep) return blockIdx;
+  return make_uint3(gridDim.x - 1 - blockIdx.x, gridDim.y - 1 - blockIdx.y, gridDim.z - 1 - blockIdx.z);
+}
+
 // Update of site (x, y, z) of one lattice (any shape).  S is the storage
 // type (float, double, or a 16-bit deviation format with FP32 arithmetic).
 // Idx is the type of the value offsets i N + site: uint32_t when Q N < 2^32
@@ -128,9 +136,10 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 template <int LAT, typename S, int NOISE, typename Idx>
 __global__ void __launch_bounds__(256) k_step(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   pdl_launch_dependents();
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const uint3 b = sweep_block(a.sweep);
+  const int x = b.x * blockDim.x + threadIdx.x;
+  const int y = b.y * blockDim.y + threadIdx.y;
+  const int z = b.z;
   pdl_wait();
   if (x >= a.Lx || y >= a.Ly) return;
   step_scalar_body<LAT, S, NOISE, SrtCollideFor<LAT, S, NOISE>, Idx>(src, dst, a, x, y, z);
@@ -276,9 +285,10 @@ template <int LAT, typename S, int VX, int NOISE, typename Idx>
 __global__ void __launch_bounds__(256, step_min_blocks<LAT, S, VX>())
     k_step_vec(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a) {
   pdl_launch_dependents();
-  const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const uint3 b = sweep_block(a.sweep);
+  const int x0 = (b.x * blockDim.x + threadIdx.x) * VX;
+  const int y = b.y * blockDim.y + threadIdx.y;
+  const int z = b.z;
   pdl_wait();
   if (x0 >= a.Lx || y >= a.Ly) return;
   step_vec_body<LAT, S, VX, NOISE, SrtCollideFor<LAT, S, NOISE>, Idx>(src, dst, a, x0, y, z);
