@@ -200,14 +200,15 @@ struct PackCvt<__nv_bfloat16, 2> {
 };
 
 // Minimum resident 256-thread blocks per SM asked of the register allocator
-// for the vector kernel.  Measured on GB300 (FP32, local Gaussian noise,
-// two sites per thread): D2Q9 2048^2 is fastest at 4 blocks (<= 64
-// registers), D3Q19 256^3 at 3 (<= 85 registers); the unconstrained
-// allocation leaves D3Q19 one block per SM, and tighter caps spill.  FP64
-// kernels need more registers: 2.
+// for the vector kernel.  Measured on GB300 (FP32, local Gaussian noise):
+// D2Q9 2048^2 is fastest at 4 blocks (<= 64 registers, no spills with two
+// or four sites per thread; four sites: 47.9 against 48.9 us per step at 3
+// blocks), D3Q19 256^3 at 3 (<= 85 registers); the unconstrained allocation
+// leaves D3Q19 one block per SM, and tighter caps spill.  D3Q19 with four
+// sites per thread (16-bit storage) and FP64 kernels need more registers: 2.
 template <int LAT, typename S, int VX = 2>
 constexpr int step_min_blocks() {
-  if (VX == 4) return (sizeof(typename Store<S>::R) != 4 || LAT == kD3Q19) ? 2 : 3;
+  if (VX == 4) return (sizeof(typename Store<S>::R) != 4 || LAT == kD3Q19) ? 2 : 4;
   if (sizeof(typename Store<S>::R) != 4) return 2;
   return LAT == kD3Q19 ? 3 : 4;
 }
