@@ -253,14 +253,48 @@ int lbfd_moments(lbfd_t h, double *rho_host, double *j_host);
 /* Same into caller-owned device buffers; asynchronous on the handle's stream. */
 int lbfd_moments_device(lbfd_t h, double *rho_dev, double *j_dev);
 
-/* Total mass sum_x sum_i f_i by a deterministic FP64 reduction.  Synchronous. */
+/* Total mass sum_x sum_i f_i by a deterministic FP64 reduction (paper Sec.
+ * IV: the mass the dynamics conserve).  For a slab handle: the FP64 sum over
+ * its owned planes of the stored state, a permutation of the lattice's
+ * values, so the sum of the slabs' masses over all ranks (an FP64
+ * all-reduce) is the lattice's mass.  Synchronous. */
 int lbfd_mass(lbfd_t h, double *mass);
 
 /* Adds the current state's statistics to the FP64 accumulators (sums of rho,
- * rho^2, f_i, f_i f_j over sites and |rho(k)|^2 for the configured modes).
- * Asynchronous. */
+ * rho^2, f_i, f_i f_j over sites and |rho(k)|^2 for the configured modes;
+ * paper Sec. IV, eqs. rhoth, dijexp, fkfk).  Asynchronous.  Not for slab
+ * handles (see lbfd_sample_totals). */
 int lbfd_sample(lbfd_t h);
 int lbfd_reset_obs(lbfd_t h);
+
+/* One sample's sums over this handle's own sites, before they are combined:
+ * totals[nq], nq = 2 + Q + 2 K + Q (Q + 1) / 2 (K = the handle's modes), in
+ * FP64: [sum delta, sum delta^2, sum_x e_i (i < Q), (re, im) of
+ * sum_x (rho - rho_mean) e^{-2 pi i k_m.x / L} (m < K), sum_x e_i e_j (i <= j,
+ * row-major)], with e_i = f_i - c_i, c_i = w_i rho_mean rounded to FP32 and
+ * delta = sum_i e_i.  Every entry is a sum over sites, so the totals of the
+ * slabs of one lattice add up (an FP64 all-reduce over the ranks) to the
+ * lattice's; the mode phases use the global site coordinates and periods.
+ * For a slab handle the sites are its owned planes, whose neighbours in the
+ * halo planes must be current (filled as before a step).  The state is read
+ * as it stands (f(x, t)); FP32-arithmetic formats only (FP64 storage:
+ * LBFD_ENOTSUP); sums in FP32 over tiles of 256 sites, FP64 beyond.
+ * Synchronous; the handle's accumulators do not change. */
+int lbfd_sample_totals(lbfd_t h, double *totals);
+
+/* The accumulator entries of one sample from its (combined) totals, in the
+ * layout of lbfd_obs: acc[2 + Q + Q*Q + K] = [sum rho, sum rho^2, sum f_i,
+ * sum f_i f_j (Q x Q), |rho(k_m)|^2], for a lattice of n_sites sites (rho =
+ * sum_i c_i + delta and f_i = c_i + e_i expanded in FP64; the squares of the
+ * modes taken after the slabs are combined).  Host arithmetic only, no
+ * device work. */
+int lbfd_obs_restore(int32_t lattice, int32_t n_modes, double rho_mean, int64_t n_sites, const double *totals,
+                     double *acc);
+
+/* Adds one sample's accumulator entries (lbfd_obs_restore) into the handle's
+ * accumulators and counts the sample: how slab handles accumulate the
+ * lattice's statistics.  Synchronous. */
+int lbfd_obs_add(lbfd_t h, const double *acc);
 
 /* Reads the accumulators and the current mass.  Synchronous. */
 int lbfd_observables(lbfd_t h, lbfd_obs *obs);

@@ -400,13 +400,19 @@ int lbfd_create_ex(lbfd_t *out, const lbfd_options *opt) {
   const size_t fin_n = size_t(obs_quantities(h->Q, LBFD_MAX_MODES)) + 1;
   if (e == cudaSuccess) e = cudaMalloc(&h->fin, sizeof(double) * fin_n);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->fin, 0, sizeof(double) * fin_n, h->stream);
-  // the structure-factor phases of FP32 sampling as per-axis tables (when small)
-  const size_t nphase = obs_phase_values(opt->n_modes, int32_t(opt->dims[0]), int32_t(opt->dims[1]),
-                                         int32_t(opt->dims[2]));
+  // the structure-factor phases of FP32 sampling as per-axis tables (when
+  // small), over the stored lattice; a slab's stored plane c is global plane
+  // slab_first - 1 + c of slab_global
+  const size_t nphase = obs_phase_values(opt->n_modes, h->sd[0], h->sd[1], h->sd[2]);
   if (e == cudaSuccess && opt->precision != LBFD_F64 && nphase > 0 && nphase <= (size_t(1) << 22)) {
     std::vector<float> tab(2 * nphase);
-    obs_phase_fill(opt->n_modes, &h->modes_host[0][0], int32_t(opt->dims[0]), int32_t(opt->dims[1]),
-                   int32_t(opt->dims[2]), tab.data());
+    int64_t period[3] = {h->sd[0], h->sd[1], h->sd[2]}, offset[3] = {0, 0, 0};
+    if (h->slab) {
+      const int ax = slow_axis_of(opt->lattice);
+      period[ax] = opt->slab_global;
+      offset[ax] = opt->slab_first - 1;
+    }
+    obs_phase_fill(opt->n_modes, &h->modes_host[0][0], h->sd[0], h->sd[1], h->sd[2], tab.data(), period, offset);
     e = cudaMalloc(&h->phase, sizeof(float) * tab.size());
     if (e == cudaSuccess) e = cudaMemcpy(h->phase, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice);
   }
@@ -767,11 +773,17 @@ int lbfd_moments(lbfd_t h, double *rho_host, double *j_host) {
 
 int lbfd_mass(lbfd_t h, double *mass) {
   if (!h || !mass) return fail(LBFD_EINVAL, "lbfd_mass: null argument");
-  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_mass: not offered for slab handles");
   DeviceGuard g(h->device);
   const lbfd_options &o = h->opt;
   LBFD_CU(obs_join(h));
-  LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, o.rho_mean, h->partials, h->d_mass, h->stream));
+  if (h->slab) {
+    // the owned planes of the stored state (a permutation of the lattice's
+    // values, so the slabs' masses sum to the lattice's)
+    const char *f = static_cast<const char *>(h->f[h->cur]) + h->plane * h->elem;
+    LBFD_CU(launch_mass(o.lattice, o.precision, f, h->N, o.rho_mean, h->partials, h->d_mass, h->stream, h->NS));
+  } else {
+    LBFD_CU(launch_mass(o.lattice, o.precision, h->f[h->cur], h->N, o.rho_mean, h->partials, h->d_mass, h->stream));
+  }
   LBFD_CU(cudaMemcpyAsync(mass, h->d_mass, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LBFD_CU(cudaStreamSynchronize(h->stream));
   return check_status(h);
@@ -786,7 +798,6 @@ int lbfd_sample(lbfd_t h) {
 
 int lbfd_reset_obs(lbfd_t h) {
   if (!h) return fail(LBFD_EINVAL, "lbfd_reset_obs: null handle");
-  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_reset_obs: not offered for slab handles");
   DeviceGuard g(h->device);
   LBFD_CU(obs_join(h));
   LBFD_CU(cudaMemsetAsync(h->acc, 0, sizeof(double) * h->acc_n, h->stream));
@@ -794,9 +805,76 @@ int lbfd_reset_obs(lbfd_t h) {
   return LBFD_OK;
 }
 
+int lbfd_sample_totals(lbfd_t h, double *totals) {
+  if (!h || !totals) return fail(LBFD_EINVAL, "lbfd_sample_totals: null argument");
+  const lbfd_options &o = h->opt;
+  if (o.precision == LBFD_F64) return fail(LBFD_ENOTSUP, "lbfd_sample_totals: FP32-arithmetic formats only");
+  if (h->NS >= (int64_t(1) << 31)) return fail(LBFD_ENOTSUP, "lbfd_sample_totals: 2^31 stored sites or more");
+  if (h->slab && o.n_modes > 0 && !h->phase)
+    return fail(LBFD_ENOTSUP, "lbfd_sample_totals: the slab's phase tables are too large");
+  DeviceGuard g(h->device);
+  LBFD_CU(obs_join(h));
+  // the owned sites: planes 1 .. n of a slab's stored lattice, or all of it
+  const int64_t s0 = h->slab ? h->plane : 0;
+  int nblocks = 0;
+  LBFD_CU(launch_observables_pull_partials(o.lattice, o.precision, h->f[h->cur], h->sd[0], h->sd[1], h->sd[2], s0, h->N,
+                                           o.rho_mean, o.n_modes, &h->modes_host[0][0], h->phase, h->partials,
+                                           &nblocks, h->stream));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  const int nq = obs_quantities(h->Q, o.n_modes);
+  std::vector<double> part(size_t(nblocks) * nq);
+  LBFD_CU(cudaMemcpyAsync(part.data(), h->partials, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  if (int rc = check_status(h)) return rc;
+  for (int q = 0; q < nq; ++q) {
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += part[size_t(b) * nq + q];  // block order
+    totals[q] = t;
+  }
+  return LBFD_OK;
+}
+
+int lbfd_obs_restore(int32_t lattice, int32_t n_modes, double rho_mean, int64_t n_sites, const double *totals,
+                     double *acc_out) {
+  if (!totals || !acc_out) return fail(LBFD_EINVAL, "lbfd_obs_restore: null argument");
+  if (lattice < LBFD_D1Q3 || lattice > LBFD_D3Q19) return fail(LBFD_EINVAL, "lbfd_obs_restore: D1Q3, D2Q9 or D3Q19");
+  if (n_modes < 0 || n_modes > LBFD_MAX_MODES || n_sites < 0 || !(rho_mean >= 0.0))
+    return fail(LBFD_EINVAL, "lbfd_obs_restore: bad argument");
+  const float rho_f = static_cast<float>(rho_mean);
+  return dispatch_lattice(lattice, [&](auto lat) -> cudaError_t {
+           constexpr int LAT = decltype(lat)::value;
+           constexpr int Q = Lattice<LAT>::Q;
+           double cs[Q];
+           double C = 0.0;
+           for (int i = 0; i < Q; ++i) {
+             cs[i] = static_cast<double>(obs_offset<LAT>(i, rho_f));
+             C += cs[i];
+           }
+           const int nacc = 2 + Q + Q * Q + n_modes;
+           for (int k = 0; k < nacc; ++k) acc_out[k] = obs_restore<Q>(k, totals, cs, C, double(n_sites), n_modes);
+           return cudaSuccess;
+         }) == cudaSuccess
+             ? LBFD_OK
+             : fail(LBFD_EINVAL, "lbfd_obs_restore: unknown lattice");
+}
+
+int lbfd_obs_add(lbfd_t h, const double *acc_sample) {
+  if (!h || !acc_sample) return fail(LBFD_EINVAL, "lbfd_obs_add: null argument");
+  DeviceGuard g(h->device);
+  std::vector<double> acc(h->acc_n);
+  LBFD_CU(obs_join(h));
+  LBFD_CU(cudaMemcpyAsync(acc.data(), h->acc, sizeof(double) * h->acc_n, cudaMemcpyDeviceToHost, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  const int nacc = 2 + h->Q + h->Q * h->Q + h->opt.n_modes;
+  for (int k = 0; k < nacc; ++k) acc[k] += acc_sample[k];
+  LBFD_CU(cudaMemcpyAsync(h->acc, acc.data(), sizeof(double) * h->acc_n, cudaMemcpyHostToDevice, h->stream));
+  LBFD_CU(cudaStreamSynchronize(h->stream));
+  h->n_samples += 1;
+  return check_status(h);
+}
+
 int lbfd_observables(lbfd_t h, lbfd_obs *obs) {
   if (!h || !obs) return fail(LBFD_EINVAL, "lbfd_observables: null argument");
-  if (h->slab) return fail(LBFD_ENOTSUP, "lbfd_observables: not offered for slab handles");
   DeviceGuard g(h->device);
   std::vector<double> acc(h->acc_n);
   LBFD_CU(obs_join(h));

@@ -212,8 +212,10 @@ constexpr int kObsBlocks = 608;      // 4 x 152 SMs: the FP32 observable pass (p
 // Number of FP64 quantities the observable pass produces for a lattice and mode count.
 int obs_quantities(int Q, int n_modes);
 
+// FP64 sum_i sum_s f_i(s) over N sites whose population i starts at f + i
+// stride (stride 0: N, a whole lattice).
 cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double rho_mean, double *partials,
-                        double *out, cudaStream_t stream);
+                        double *out, cudaStream_t stream, int64_t stride = 0);
 
 cudaError_t launch_observables(int lattice, int precision, const void *f, int32_t Lx, int32_t Ly, int32_t Lz,
                                double rho_mean, int n_modes, const int32_t *modes /*device, n_modes*3*/,
@@ -230,8 +232,18 @@ cudaError_t launch_observables(int lattice, int precision, const void *f, int32_
 cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
                                     double rho_mean, int n_modes, const int32_t *modes, const void *phase,
                                     double *partials, double *fin, double *acc, cudaStream_t stream);
+// Stage 1 alone over the sites s0 .. s0 + count - 1 of the stored lattice
+// (a slab's owned planes): per-block partials, *nblocks of them, in the
+// layout above, for the caller to sum.
+cudaError_t launch_observables_pull_partials(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly,
+                                             int32_t Lz, int64_t s0, int64_t count, double rho_mean, int n_modes,
+                                             const int32_t *modes, const void *phase, double *partials, int *nblocks,
+                                             cudaStream_t stream);
 size_t obs_phase_values(int n_modes, int32_t Lx, int32_t Ly, int32_t Lz);
-void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out);
+// period, offset (optional, per axis): coordinate u of the table is the
+// global coordinate (offset + u) mod period (a slab's stored planes).
+void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out,
+                    const int64_t *period = nullptr, const int64_t *offset = nullptr);
 
 // c_i = w_i rho_mean in FP32, the constants the FP32-arithmetic observables
 // take their deviations e_i = f_i - c_i from (rounded so that every kernel
@@ -248,7 +260,8 @@ __host__ __device__ __forceinline__ float obs_offset(int i, float rho_f) {
 // row-major]), with cs[i] = c_i, C = sum_i c_i and Nd sites: rho = C +
 // delta and f_i = c_i + e_i expanded, in FP64.
 template <int Q>
-__device__ __forceinline__ double obs_restore(int k, const double *tt, const double *cs, double C, double Nd, int K) {
+__host__ __device__ __forceinline__ double obs_restore(int k, const double *tt, const double *cs, double C, double Nd,
+                                                       int K) {
   const int nq1 = 2 + Q + 2 * K;
   if (k == 0) return tt[0] + Nd * C;
   if (k == 1) return tt[1] + 2.0 * C * tt[0] + Nd * C * C;

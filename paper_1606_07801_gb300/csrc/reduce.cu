@@ -30,8 +30,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Mass
 // ---------------------------------------------------------------------------
 template <int LAT, typename S>
-__global__ void __launch_bounds__(kReduceThreads) k_mass_partials(const S *__restrict__ f, int64_t N, double rho_mean,
-                                                                 double *__restrict__ partials) {
+__global__ void __launch_bounds__(kReduceThreads) k_mass_partials(const S *__restrict__ f, int64_t N, int64_t stride,
+                                                                 double rho_mean, double *__restrict__ partials) {
   using L = Lattice<LAT>;
   __shared__ double warp_tot[kReduceThreads / 32];
   double acc = 0.0;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_mass_partials(const S *__res
     double r = 0.0;
     static_for<L::Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      r += Store<S>::getd(f[i * N + s], L::w(i) * rho_mean);
+      r += Store<S>::getd(f[i * stride + s], L::w(i) * rho_mean);
     });
     acc += r;
   }
@@ -63,12 +63,13 @@ __global__ void k_sum_partials(const double *__restrict__ partials, int nblocks,
 }
 
 cudaError_t launch_mass(int lattice, int precision, const void *f, int64_t N, double rho_mean, double *partials,
-                        double *out, cudaStream_t stream) {
+                        double *out, cudaStream_t stream, int64_t stride) {
+  if (stride == 0) stride = N;
   return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
     constexpr int LAT = decltype(lat)::value;
     using S = typename decltype(tag)::type;
-    k_mass_partials<LAT, S><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const S *>(f), N, rho_mean,
-                                                                          partials);
+    k_mass_partials<LAT, S><<<kReduceBlocks, kReduceThreads, 0, stream>>>(static_cast<const S *>(f), N, stride,
+                                                                          rho_mean, partials);
     k_sum_partials<<<1, 32, 0, stream>>>(partials, kReduceBlocks, out);
     return cudaGetLastError();
   });
@@ -291,6 +292,7 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // Sizes of the lattice with their fast divisions and FP32 inverses.
 struct ObsDims {
   int32_t Lx, Ly, Lz;
+  uint32_t s0, count;           // the sites sampled: s0 .. s0 + count - 1
   FastDiv div_x, div_y, div_z;  // exact for numerators below 2^31
   float inv_x, inv_y, inv_z;
   int32_t big;                  // some side >= 46341: k x may not fit 31 bits
@@ -379,14 +381,15 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
     __syncthreads();
   };
 
-  for (uint32_t base = blockIdx.x * kObsThreads; base < N; base += gridDim.x * kObsThreads) {
-    const uint32_t s = base + threadIdx.x;
+  for (uint32_t base = blockIdx.x * kObsThreads; base < dm.count; base += gridDim.x * kObsThreads) {
+    const bool valid = base + threadIdx.x < dm.count;
+    const uint32_t s = dm.s0 + base + threadIdx.x;
     float e[QP];
 #pragma unroll
     for (int i = 0; i < QP; ++i) e[i] = 0.0f;
     float delta = 0.0f;
     uint32_t x = 0, y = 0, z = 0;
-    if (s < N) {
+    if (valid) {
       const uint32_t r = fastdiv(s, dm.div_x);
       x = s - r * static_cast<uint32_t>(Lx);
       z = fastdiv(r, dm.div_y);
@@ -418,7 +421,7 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_pull(const S *__restrict__ 
       if (lane == 0) wsum[warp][q] = v;
     };
     if (K > 0) {
-      const float d = s < N ? delta + d_off : 0.0f;
+      const float d = valid ? delta + d_off : 0.0f;
       for (int m = 0; m < K; ++m) {
         float cs, sn;
         if (phase) {
@@ -583,12 +586,13 @@ int obs_pull_blocks(int64_t N) {
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(kObsBlocks, (N + kObsThreads - 1) / kObsThreads)));
 }
 
-cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
-                                    double rho_mean, int n_modes, const int32_t *modes, const void *phase,
-                                    double *partials, double *fin, double *acc, cudaStream_t stream) {
+cudaError_t launch_observables_pull_partials(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly,
+                                             int32_t Lz, int64_t s0, int64_t count, double rho_mean, int n_modes,
+                                             const int32_t *modes, const void *phase, double *partials, int *nblocks,
+                                             cudaStream_t stream) {
   if (n_modes < 0 || n_modes > LBFD_MAX_MODES_DEV || precision == kStoreF64) return cudaErrorInvalidValue;
   const int64_t N = int64_t(Lx) * Ly * Lz;
-  if (N >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+  if (N >= (int64_t(1) << 31) || s0 < 0 || count < 0 || s0 + count > N) return cudaErrorInvalidValue;
   const int32_t L3[3] = {Lx, Ly, Lz};
   ModeArgs ma{};
   ma.n = n_modes;
@@ -599,6 +603,8 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
   dm.Lx = Lx;
   dm.Ly = Ly;
   dm.Lz = Lz;
+  dm.s0 = static_cast<uint32_t>(s0);
+  dm.count = static_cast<uint32_t>(count);
   dm.div_x = make_fastdiv(uint32_t(Lx));
   dm.div_y = make_fastdiv(uint32_t(Ly));
   dm.div_z = make_fastdiv(uint32_t(Lz));
@@ -607,7 +613,7 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
   dm.inv_z = 1.0f / float(Lz);
   dm.big = (Lx >= 46341 || Ly >= 46341 || Lz >= 46341) ? 1 : 0;
   const float rho_f = static_cast<float>(rho_mean);
-  const int nblocks = obs_pull_blocks(N);
+  *nblocks = obs_pull_blocks(count);
   return dispatch_lattice_storage(lattice, precision, [&](auto lat, auto tag) {
     constexpr int LAT = decltype(lat)::value;
     using S = typename decltype(tag)::type;
@@ -619,28 +625,41 @@ cudaError_t launch_observables_pull(int lattice, int precision, const void *g, i
       double C = 0.0;
       for (int i = 0; i < Q; ++i) C += static_cast<double>(static_cast<float>(Lattice<LAT>::w(i)) * rho_f);
       const float d_off = static_cast<float>(C - rho_mean);
-      k_obs_pull<LAT, S><<<nblocks, kObsThreads, 0, stream>>>(static_cast<const S *>(g), dm, rho_f, d_off, ma,
-                                                              static_cast<const float2 *>(phase), partials);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      return pull_finalize_t<LAT>(partials, nblocks, n_modes, N, rho_f, fin, acc, stream);
+      k_obs_pull<LAT, S><<<*nblocks, kObsThreads, 0, stream>>>(static_cast<const S *>(g), dm, rho_f, d_off, ma,
+                                                               static_cast<const float2 *>(phase), partials);
+      return cudaGetLastError();
     }
   });
+}
+
+cudaError_t launch_observables_pull(int lattice, int precision, const void *g, int32_t Lx, int32_t Ly, int32_t Lz,
+                                    double rho_mean, int n_modes, const int32_t *modes, const void *phase,
+                                    double *partials, double *fin, double *acc, cudaStream_t stream) {
+  const int64_t N = int64_t(Lx) * Ly * Lz;
+  int nblocks = 0;
+  cudaError_t e = launch_observables_pull_partials(lattice, precision, g, Lx, Ly, Lz, 0, N, rho_mean, n_modes, modes,
+                                                   phase, partials, &nblocks, stream);
+  if (e != cudaSuccess) return e;
+  return launch_obs_pull_finalize(lattice, partials, nblocks, n_modes, N, rho_mean, fin, acc, stream);
 }
 
 size_t obs_phase_values(int n_modes, int32_t Lx, int32_t Ly, int32_t Lz) {
   return size_t(n_modes) * (size_t(Lx) + size_t(Ly) + size_t(Lz));
 }
 
-void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out) {
-  // per axis d and mode m: e^{-2 pi i r / L_d}, r = (k_d u) mod L_d, u < L_d, in FP64 then rounded
+void obs_phase_fill(int n_modes, const int32_t *modes, int32_t Lx, int32_t Ly, int32_t Lz, float *out,
+                    const int64_t *period, const int64_t *offset) {
+  // per axis d and mode m: e^{-2 pi i r / P_d}, r = (k_d ((o_d + u) mod P_d)) mod P_d, u < L_d, in FP64 then
+  // rounded (P_d = L_d and o_d = 0 unless a slab gives its global period and its first stored plane)
   const int32_t L3[3] = {Lx, Ly, Lz};
   size_t at = 0;
   for (int d = 0; d < 3; ++d)
     for (int m = 0; m < n_modes; ++m) {
-      const int64_t L = L3[d], k = ((int64_t(modes[3 * m + d]) % L) + L) % L;
-      for (int64_t u = 0; u < L; ++u, ++at) {
-        const double a = 2.0 * 3.14159265358979323846 * double((k * u) % L) / double(L);
+      const int64_t P = period ? period[d] : L3[d], o = offset ? offset[d] : 0;
+      const int64_t k = ((int64_t(modes[3 * m + d]) % P) + P) % P;
+      for (int64_t u = 0; u < L3[d]; ++u, ++at) {
+        const int64_t x = ((o + u) % P + P) % P;
+        const double a = 2.0 * 3.14159265358979323846 * double((k * x) % P) / double(P);
         out[2 * at] = static_cast<float>(std::cos(a));
         out[2 * at + 1] = static_cast<float>(-std::sin(a));
       }

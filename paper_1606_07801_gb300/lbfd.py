@@ -130,6 +130,9 @@ SIGNATURES = {
     "lbfd_moments_device": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "lbfd_mass": (c_int32, [c_void_p, P(c_double)]),
     "lbfd_sample": (c_int32, [c_void_p]),
+    "lbfd_sample_totals": (c_int32, [c_void_p, c_void_p]),
+    "lbfd_obs_restore": (c_int32, [c_int32, c_int32, c_double, c_int64, c_void_p, c_void_p]),
+    "lbfd_obs_add": (c_int32, [c_void_p, c_void_p]),
     "lbfd_reset_obs": (c_int32, [c_void_p]),
     "lbfd_observables": (c_int32, [c_void_p, P(Obs)]),
     "lbfd_query": (c_int32, [c_void_p, P(c_int32), P(c_int32), P(c_int64), P(c_int32)]),
@@ -350,6 +353,34 @@ def lbfd_sample(h: int) -> None:
 
 def lbfd_reset_obs(h: int) -> None:
     _check(load().lbfd_reset_obs(h), "lbfd_reset_obs")
+
+
+def obs_totals_count(Q: int, n_modes: int) -> int:
+    """Entries of one sample's totals (lbfd_sample_totals)."""
+    return 2 + Q + 2 * n_modes + Q * (Q + 1) // 2
+
+
+def lbfd_sample_totals(h: int, Q: int, n_modes: int) -> np.ndarray:
+    """One sample's FP64 sums over the handle's own sites (see include/lbfd.h)."""
+    out = np.zeros(obs_totals_count(Q, n_modes))
+    _check(load().lbfd_sample_totals(h, _ptr(out)), "lbfd_sample_totals")
+    return out
+
+
+def lbfd_obs_restore(lattice: int, n_modes: int, rho_mean: float, n_sites: int, totals) -> np.ndarray:
+    """Accumulator entries of one sample from its combined totals (host arithmetic)."""
+    Q = Q_OF[lattice]
+    t = np.ascontiguousarray(totals, dtype=np.float64)
+    if t.size != obs_totals_count(Q, n_modes):
+        raise ValueError("totals: wrong length")
+    out = np.zeros(2 + Q + Q * Q + n_modes)
+    _check(load().lbfd_obs_restore(lattice, n_modes, rho_mean, n_sites, _ptr(t), _ptr(out)), "lbfd_obs_restore")
+    return out
+
+
+def lbfd_obs_add(h: int, acc) -> None:
+    a = np.ascontiguousarray(acc, dtype=np.float64)
+    _check(load().lbfd_obs_add(h, _ptr(a)), "lbfd_obs_add")
 
 
 def lbfd_observables(h: int) -> dict:

@@ -16,8 +16,13 @@ This module holds the orchestration around the library:
   exchange_local  the same for several slabs held by one process
   SlabSimulation  a slab handle on this process's GPU, stepped one step at
                   a time with an exchange after each step
+  allreduce_sum   the FP64 all-reduce of the slabs' sums: the mass (each
+                  slab's owned planes, lbfd_mass) and the sampled
+                  observables (lbfd_sample_totals, combined by
+                  lbfd_obs_restore after the sum, so |rho(k)|^2 squares the
+                  lattice's mode sum, not the slabs')
 Arithmetic of the method stays in the CUDA library; here are only index
-ranges and copies.
+ranges, copies and the sums over ranks.
 """
 from __future__ import annotations
 
@@ -118,6 +123,31 @@ def exchange_local(plans, states) -> None:
         _unpack(p, s, 1, downs[p.above])
 
 
+def allreduce_sum(values, group=None) -> np.ndarray:
+    """FP64 sum of `values` over the ranks of `group`; every rank gets it
+    (a copy when there is no process group or one rank)."""
+    a = np.array(values, dtype=np.float64, copy=True).reshape(-1)
+    try:
+        import torch
+        import torch.distributed as dist
+    except ImportError:  # pragma: no cover
+        return a
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return a
+    t = torch.from_numpy(a)
+    if dist.get_backend(group) == "nccl":
+        t = t.cuda(torch.cuda.current_device())
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t.cpu().numpy()
+
+
+def sample_entries(plan: SlabPlan, rho_mean: float, n_modes: int, totals) -> np.ndarray:
+    """The accumulator entries of one sample of the whole lattice from the
+    totals summed over all its slabs."""
+    n_sites = int(np.prod(plan.global_dims))
+    return abi.lbfd_obs_restore(plan.lattice, n_modes, rho_mean, n_sites, totals)
+
+
 class SlabSimulation:
     """This rank's slab of one lattice on its GPU: a slab handle of the
     library whose buffers are torch tensors, on torch's current stream (so
@@ -134,6 +164,8 @@ class SlabSimulation:
 
         self.plan = SlabPlan(lattice, global_dims, nranks, rank)
         self.group = group
+        self.rho_mean = float(rho_mean)
+        self.n_modes = len(kw.get("modes") or ())
         kw.setdefault("stream", torch.cuda.current_stream())
         self.sim = Simulation(lattice, self.plan.dims, tau, rho_mean, seed, torch_buffers=True, device=device,
                               slab_global=self.plan.global_dims[self.plan.axis], slab_first=self.plan.first, **kw)
@@ -163,6 +195,21 @@ class SlabSimulation:
         """f(x, t) on the owned planes, [Q, owned sites]."""
         return self.sim.get_f()
 
+    def mass(self) -> float:
+        """The lattice's mass: the slabs' FP64 masses summed over the ranks."""
+        return float(allreduce_sum([abi.lbfd_mass(self.sim.h)], self.group)[0])
+
+    def sample(self) -> None:
+        """Adds the lattice's observables of the current state to this
+        slab's accumulators (every rank's hold the same sums): the slabs'
+        totals, summed over the ranks, then combined."""
+        totals = abi.lbfd_sample_totals(self.sim.h, self.plan.Q, self.n_modes)
+        total = allreduce_sum(totals, self.group)
+        abi.lbfd_obs_add(self.sim.h, sample_entries(self.plan, self.rho_mean, self.n_modes, total))
+
+    def observables(self) -> dict:
+        return self.sim.observables()
+
     def close(self) -> None:
         self.sim.close()
 
@@ -171,6 +218,23 @@ class SlabSimulation:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def mass_local(slabs) -> float:
+    """The lattice's mass from all of its slabs held by this process."""
+    return float(sum(abi.lbfd_mass(sl.sim.h) for sl in slabs))
+
+
+def sample_local(slabs) -> None:
+    """sample() for all slabs of a lattice held by this process: their
+    totals summed in slab order, combined, and added to every slab."""
+    total = None
+    for sl in slabs:
+        t = abi.lbfd_sample_totals(sl.sim.h, sl.plan.Q, sl.n_modes)
+        total = t if total is None else total + t
+    entries = sample_entries(slabs[0].plan, slabs[0].rho_mean, slabs[0].n_modes, total)
+    for sl in slabs:
+        abi.lbfd_obs_add(sl.sim.h, entries)
 
 
 def step_local(slabs, n: int = 0) -> None:

@@ -81,11 +81,79 @@ def test_slab_handle_limits():
         with pytest.raises(abi.LbfdError) as e:
             sl.sim.step(2)
         assert e.value.code == abi.EINVAL
-        with pytest.raises(abi.LbfdError) as e:
-            sl.sim.mass()
+        with pytest.raises(abi.LbfdError) as e:  # its sampling goes through lbfd_sample_totals
+            sl.sim.sample()
         assert e.value.code == abi.ENOTSUP
     with pytest.raises(abi.LbfdError) as e:  # rows not on 16-byte boundaries: no staged kernel, no slab
         lb.Simulation(lb.D2Q9, (66, 8), 0.8, 10.0, 1, slab_global=16, slab_first=8)
     assert e.value.code == abi.ENOTSUP
     with pytest.raises(abi.LbfdError):
         lb.Simulation(lb.D2Q9, (64, 8), 0.8, 10.0, 1, slab_global=12, slab_first=8)
+
+
+@pytest.mark.parametrize("lat,gdims,prec,nranks,modes", [
+    (lb.D2Q9, (264, 40, 1), lb.F32, 2, [(1, 0, 0), (2, 3, 0)]),
+    (lb.D2Q9, (520, 7, 1), lb.F32_BF16, 3, [(0, 1, 0)]),
+    (lb.D3Q19, (24, 10, 12), lb.F32, 3, [(1, 0, 0), (0, 1, 2), (1, 1, 1)]),
+    (lb.D3Q19, (32, 6, 8), lb.F32_F16, 2, [(0, 0, 1)]),
+])
+def test_slab_mass_and_observables_sum_to_the_whole(lat, gdims, prec, nranks, modes):
+    """The slabs' FP64 masses (owned planes of the stored state) add up to the
+    lattice's mass, and their observable totals (lbfd_sample_totals, modes at
+    global coordinates), summed and combined by lbfd_obs_restore, give the
+    whole lattice's sampled sums (paper Sec. IV) to FP32-tile accuracy; the
+    slab path runs the same FP32 pass over other tiles, so the sums agree to
+    the rounding of 256-term FP32 tiles, not bit for bit."""
+    Q, N = lb.Q_OF[lat], int(np.prod(gdims))
+    dims = gdims[:2] if lat == lb.D2Q9 else gdims
+    rho, tau, seed = 25.0, 0.9, 11
+    f0 = synth.random_populations(Q, N, rho, 0.3, seed=N + 1)
+    kw = dict(precision=prec, init=lb.INIT_NONE, lattice_id=4, modes=modes)
+    with lb.Simulation(lat, dims, tau, rho, seed, **kw) as whole:
+        whole.set_f(f0)
+        masses, obs_whole = [], None
+        for _ in range(3):
+            whole.step(2)
+            whole.sample()
+            masses.append(whole.mass())
+        obs_whole = whole.observables()
+    slabs = [slab.SlabSimulation(lat, dims, tau, rho, seed, nranks=nranks, rank=r, local=True, **kw)
+             for r in range(nranks)]
+    try:
+        for sl in slabs:
+            sl.sim.set_f(_stored_planes(f0, gdims, sl.plan))
+        slab.step_local(slabs)
+        for k in range(3):
+            slab.step_local(slabs, 2)
+            slab.sample_local(slabs)
+            assert slab.mass_local(slabs) == pytest.approx(masses[k], rel=1e-13)
+        obs = [sl.observables() for sl in slabs]
+    finally:
+        for sl in slabs:
+            sl.close()
+    n = 3 * N
+    var = obs_whole["sum_rho2"] / n - (obs_whole["sum_rho"] / n) ** 2
+    cov = np.asarray(obs_whole["sum_ff"]) / n - np.outer(obs_whole["sum_f"], obs_whole["sum_f"]) / n ** 2
+    for ob in obs:
+        # the bounds of the FP32 sampling tests, doubled (both sides carry FP32 tile sums)
+        assert ob["n_samples"] == 3
+        assert abs(ob["sum_rho"] - obs_whole["sum_rho"]) <= 1e-6 * obs_whole["sum_rho"]
+        assert abs(ob["sum_rho2"] - obs_whole["sum_rho2"]) / n <= 2e-4 * var
+        assert np.max(np.abs(ob["sum_f"] - obs_whole["sum_f"])) <= 1e-6 * np.max(obs_whole["sum_f"])
+        assert np.max(np.abs(np.asarray(ob["sum_ff"]) - obs_whole["sum_ff"])) / n <= 2e-4 * np.max(np.abs(cov))
+        assert np.all(np.abs(ob["sum_sk"] - obs_whole["sum_sk"]) <= 2e-4 * obs_whole["sum_sk"] + 2e-3 * n * var)
+    assert all(np.array_equal(obs[0]["sum_ff"], o["sum_ff"]) for o in obs)
+
+
+def test_sample_totals_of_a_whole_handle_match_lbfd_sample():
+    """For a whole lattice, lbfd_sample_totals + lbfd_obs_restore is the
+    separate sampling pass with the stage-2 sum taken on the host."""
+    lat, dims, modes = lb.D2Q9, (96, 70), [(1, 2, 0), (3, 0, 0)]
+    with lb.Simulation(lat, dims, 0.8, 40.0, 2, modes=modes) as s:
+        s.step(5)
+        s.sample()
+        want = s.observables()
+        t = abi.lbfd_sample_totals(s.h, 9, len(modes))
+        got = abi.lbfd_obs_restore(lat, len(modes), 40.0, 96 * 70, t)
+    flat = np.concatenate([[want["sum_rho"], want["sum_rho2"]], want["sum_f"], np.ravel(want["sum_ff"]), want["sum_sk"]])
+    assert np.allclose(got, flat, rtol=1e-12, atol=1e-12 * abs(flat).max())

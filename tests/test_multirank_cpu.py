@@ -201,3 +201,88 @@ def test_slab_plan_host_arithmetic():
     assert [p for p, _ in send_hi] == [p for p, _ in recv_lo] == abi.lbfd_slab_cross(abi.D3Q19, 1)
     assert {c for _, c in send_hi} == {lo.count} and {c for _, c in recv_lo} == {0}
     assert lo.faces[0][2] == 30
+
+
+def _slab_totals(lat, f, gdims, first, count, plane, axis, rho_mean, modes):
+    """One slab's totals in the layout of lbfd_sample_totals, by their
+    definition: sums over the slab's sites of e_i = f_i - c_i (c_i = w_i
+    rho_mean rounded to FP32), delta = sum_i e_i, delta^2, e_i e_j, and
+    (rho - rho_mean) e^{-2 pi i k.x / L} at the sites' global coordinates."""
+    import oracle
+
+    _, Q, v, w = oracle.lattice(lat)
+    c = (np.float32(w) * np.float32(rho_mean)).astype(np.float64)
+    e = f - c[:, None]
+    delta = e.sum(0)
+    Lx, Ly, Lz = gdims
+    s = np.arange(count * plane)
+    x = s % Lx
+    y = (s // Lx) % (Ly if axis == 2 else count) + (first if axis == 1 else 0)
+    z = s // (Lx * Ly) + first if axis == 2 else np.zeros_like(s)
+    d = f.sum(0) - rho_mean
+    out = [delta.sum(), (delta ** 2).sum()] + list(e.sum(1))
+    for k in modes:
+        ph = 2 * np.pi * (k[0] * x / Lx + k[1] * y / Ly + k[2] * z / Lz)
+        out += [(d * np.cos(ph)).sum(), -(d * np.sin(ph)).sum()]
+    out += [(e[i] * e[j]).sum() for i in range(Q) for j in range(i, Q)]
+    return np.array(out)
+
+
+def _obs_rank(rank, world, port, out, lat, gdims, modes):
+    import os
+
+    import torch.distributed as dist
+
+    os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import oracle
+        from paper_1606_07801_gb300 import slab, synth
+
+        oracle.build()
+        _, Q, v, _ = oracle.lattice(lat)
+        N = int(np.prod(gdims))
+        rho = 30.0
+        f0 = synth.random_populations(Q, N, rho, 0.3, seed=77)
+        f = oracle.run(lat, gdims[: 2 if lat == 1 else 3], f0, 3, 0.8, oracle.NOISE_LOCAL, oracle.GAUSSIAN,
+                       rho_eq=rho, seed=4, lattice_id=1)
+        plan = slab.SlabPlan(lat, gdims, world, rank)
+        mine = f[:, plan.first * plan.plane:(plan.first + plan.count) * plan.plane]
+        totals = _slab_totals(lat, mine, plan.global_dims, plan.first, plan.count, plan.plane, plan.axis, rho, modes)
+        total = slab.allreduce_sum(totals)
+        entries = slab.sample_entries(plan, rho, len(modes), total)
+        mass = slab.allreduce_sum([mine.sum()])[0]
+        out.put((rank, entries, mass))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,lat,gdims,modes", [
+    (2, 1, (12, 10, 1), [(1, 0, 0), (2, 3, 0)]),
+    (3, 2, (6, 4, 7), [(1, 0, 0), (0, 1, 2), (1, 1, 1)]),
+])
+def test_slab_observables_allreduce_match_whole_lattice(orc, world, lat, gdims, modes):
+    """Each rank sums the observables of its own planes; the FP64 all-reduce
+    of those totals (paper_1606_07801_gb300.slab.allreduce_sum), combined by
+    the library's lbfd_obs_restore, gives the whole lattice's sums of rho,
+    rho^2, f_i, f_i f_j and |rho(k)|^2 (paper Sec. IV, eqs. rhoth, dijexp,
+    fkfk), the modes squared after the sum; and the slabs' masses add up to
+    the lattice's."""
+    got = _spawn(_obs_rank, world, (lat, gdims, modes))
+    _, Q, v, w = orc.lattice(lat)
+    N = int(np.prod(gdims))
+    from paper_1606_07801_gb300 import synth
+
+    f0 = synth.random_populations(Q, N, 30.0, 0.3, seed=77)
+    f = orc.run(lat, gdims[: 2 if lat == 1 else 3], f0, 3, 0.8, orc.NOISE_LOCAL, orc.GAUSSIAN, rho_eq=30.0,
+                seed=4, lattice_id=1)
+    rho = f.sum(0)
+    Lx, Ly, Lz = gdims
+    field = (rho - 30.0).reshape(Lz, Ly, Lx)
+    F = np.fft.fftn(field)
+    want = np.concatenate([[rho.sum(), (rho ** 2).sum()], f.sum(1), (f @ f.T).ravel(),
+                           [abs(F[k[2] % Lz, k[1] % Ly, k[0] % Lx]) ** 2 for k in modes]])
+    for rank, entries, mass in got:
+        assert np.allclose(entries, want, rtol=1e-11, atol=1e-9 * abs(want).max()), rank
+        assert mass == pytest.approx(f.sum(), rel=1e-13)
+    assert all(np.array_equal(got[0][1], g[1]) for g in got)
