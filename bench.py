@@ -424,7 +424,7 @@ def run_served(args):
     bytes_alg = int(sum(int(np.prod(sp["dims"])) * sp["steps"] * 2 * 4 * Q_OF[sp["lattice"]] for sp in specs))
     d2h = int(np.sum(sites) * 8)
     sink = torch.empty(args.sink_mb << 20, dtype=torch.uint8).pin_memory()
-    policy = lb.POLICY_SHORTEST if args.policy == "shortest" else lb.POLICY_FIFO
+    policy = {"shortest": lb.POLICY_SHORTEST, "longest": lb.POLICY_LONGEST}.get(args.policy, lb.POLICY_FIFO)
 
     def make_server():
         return lb.Server(hbm_budget=int(args.budget_gb * (1 << 30)), max_active=4096, max_ahead=4,
@@ -523,7 +523,7 @@ def main():
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--rate", type=float, default=500.0)
     ap.add_argument("--budget-gb", type=float, default=120.0)
-    ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest"])
+    ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest", "longest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
     ap.add_argument("--walk", default="per_tile", choices=WALKS)

@@ -456,6 +456,9 @@ int lbfd_ensemble_mass(lbfd_ens_t e, int32_t member, double *mass);
 
 #define LBFD_POLICY_FIFO 0      /* admit in arrival order (later requests may pass one that does not fit) */
 #define LBFD_POLICY_SHORTEST 1  /* admit the request with the fewest site updates (sites x steps) first */
+#define LBFD_POLICY_LONGEST 2   /* admit the request with the most site updates first: a backlog ends with
+                                   fewer long simulations running alone (a shorter makespan), at the cost of
+                                   the short requests' latency */
 /* Tile order of the batched kernel: a persistent grid whose blocks take every
  * grid-th tile (STRIDED) or one run of consecutive tiles (CONTIGUOUS); one
  * block per tile (PER_TILE); or one block per tile with the members'
@@ -481,7 +484,7 @@ typedef struct lbfd_server_options {
     int32_t max_active;     /* simulations resident at once (<= 65536) */
     int32_t max_ahead;      /* time steps the host may queue ahead of the GPU (>= 1) */
     int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
-    int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST */
+    int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST / LBFD_POLICY_LONGEST */
     int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
     int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_STRIDED, _CONTIGUOUS or
                                _PER_TILE (LBFD_WALK_PARAM is for ensembles only) */

@@ -16,8 +16,8 @@ from . import build as _build_mod
 from .lbfd import (D1Q3, D2Q5, D2Q9, D3Q19, D_OF, EBUSY, ECUDA, EINVAL, ENOMEM, ENOTSUP, ETIMEOUT, F32, F32_BF16, F32_F16,
                    F64, GAUSSIAN, INIT_HOST, INIT_NONE, INIT_SINE, INIT_UNIFORM, KERNEL_AUTO, KERNEL_CLUSTER,
                    KERNEL_MRT, KERNEL_SCALAR, KERNEL_SMALL, KERNEL_STAGED, KERNEL_VEC, MAX_MODES, MAX_Q, NOISE_GLOBAL,
-                   NOISE_LOCAL, NOISE_OFF, OK, POLICY_FIFO, POLICY_SHORTEST, Q_OF, REQ_DONE, REQ_QUEUED, REQ_RUNNING,
-                   REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, WALK_CONTIGUOUS, WALK_PARAM, WALK_PER_TILE,
+                   NOISE_LOCAL, NOISE_OFF, OK, POLICY_FIFO, POLICY_LONGEST, POLICY_SHORTEST, Q_OF, REQ_DONE,
+                   REQ_QUEUED, REQ_RUNNING, REQ_UNKNOWN, RESULT_F, RESULT_NONE, RESULT_RHO, UNIFORM, WALK_CONTIGUOUS, WALK_PARAM, WALK_PER_TILE,
                    WALK_STRIDED, LbfdError, Options, load)
 from . import lbfd as abi
 
@@ -25,6 +25,7 @@ __all__ = ["Simulation", "Ensemble", "Server", "STORAGE_DTYPE", "abi", "build", 
            "D1Q3", "D2Q9", "D3Q19", "D2Q5", "F32", "F64", "F32_F16", "F32_BF16",
            "NOISE_LOCAL", "NOISE_GLOBAL", "NOISE_OFF", "GAUSSIAN", "UNIFORM", "INIT_UNIFORM", "INIT_SINE",
            "INIT_NONE", "INIT_HOST", "RESULT_F", "RESULT_RHO", "RESULT_NONE", "POLICY_FIFO", "POLICY_SHORTEST",
+           "POLICY_LONGEST",
            "WALK_STRIDED", "WALK_CONTIGUOUS", "WALK_PER_TILE", "WALK_PARAM", "REQ_QUEUED", "REQ_RUNNING", "REQ_DONE",
            "REQ_UNKNOWN", "Q_OF", "D_OF", "KERNEL_AUTO", "KERNEL_VEC", "KERNEL_SCALAR", "KERNEL_SMALL",
            "KERNEL_CLUSTER", "KERNEL_MRT", "KERNEL_STAGED"]

@@ -249,7 +249,9 @@ int64_t submit_request(lbfd_server *s, SrvRequest &&q, double t_submit) {
   const int64_t id = static_cast<int64_t>(s->reqs.size());
   q.t_submit = t_submit;
   q.state = kQueued;
-  const int64_t prio = s->opt.policy == LBFD_POLICY_SHORTEST ? q.work : id;
+  const int64_t prio = s->opt.policy == LBFD_POLICY_SHORTEST  ? q.work
+                       : s->opt.policy == LBFD_POLICY_LONGEST ? -q.work
+                                                              : id;
   s->reqs.push_back(std::move(q));
   s->queue.insert({prio, id});
   return id;
@@ -575,7 +577,7 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
   if (o.max_ahead < 1 || o.max_ahead > 1024) return srv_fail(LBFD_EINVAL, "server: max_ahead must be in [1, 1024]");
   if (o.passes != 1 && o.passes != 2 && o.passes != 4 && o.passes != 8)
     return srv_fail(LBFD_EINVAL, "server: passes must be 1, 2, 4 or 8");
-  if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST)
+  if (o.policy != LBFD_POLICY_FIFO && o.policy != LBFD_POLICY_SHORTEST && o.policy != LBFD_POLICY_LONGEST)
     return srv_fail(LBFD_EINVAL, "server: unknown policy");
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.vx_max != 1 && o.vx_max != 2) return srv_fail(LBFD_EINVAL, "server: vx_max must be 1 or 2");

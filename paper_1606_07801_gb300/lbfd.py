@@ -25,7 +25,7 @@ NOISE_LOCAL, NOISE_GLOBAL, NOISE_OFF = 0, 1, 2
 GAUSSIAN, UNIFORM = 0, 1
 INIT_UNIFORM, INIT_SINE, INIT_NONE, INIT_HOST = 0, 1, 2, 3
 RESULT_F, RESULT_RHO, RESULT_NONE = 0, 1, 2
-POLICY_FIFO, POLICY_SHORTEST = 0, 1
+POLICY_FIFO, POLICY_SHORTEST, POLICY_LONGEST = 0, 1, 2
 WALK_STRIDED, WALK_CONTIGUOUS, WALK_PER_TILE, WALK_PARAM = 0, 1, 2, 3
 REQ_UNKNOWN, REQ_QUEUED, REQ_RUNNING, REQ_DONE = -1, 0, 1, 2
 MAX_Q, MAX_MODES = 19, 16

@@ -142,6 +142,13 @@ def test_budget_slots_and_site_limit_bound_admission():
     assert st["peak_resident_sites"] <= 3 * 4096 and st["peak_active"] == 3
     for k, sp in enumerate(reversed(specs)):
         assert np.array_equal(got[k], _alone(sp, lb.F32))
+    # longest-work-first admission: other order, same results
+    with lb.Server(hbm_budget=64 << 20, max_active_sites=3 * 4096, policy=lb.POLICY_LONGEST) as srv:
+        ids = [_submit(srv, sp) for sp in specs]
+        srv.drain()
+        got = [srv.result(i) for i in ids]
+    for k, sp in enumerate(specs):
+        assert np.array_equal(got[k], _alone(sp, lb.F32))
 
 
 def test_requests_that_never_fit_are_rejected():
