@@ -486,8 +486,10 @@ typedef struct lbfd_server_options {
     int32_t passes;         /* tile passes of the batched kernel: 1, 2, 4 or 8 */
     int32_t policy;         /* LBFD_POLICY_FIFO / LBFD_POLICY_SHORTEST / LBFD_POLICY_LONGEST */
     int32_t occupancy;      /* register/occupancy variant of the batched kernel: 0 or 1 (fewer blocks per SM) */
-    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_STRIDED, _CONTIGUOUS or
-                               _PER_TILE (LBFD_WALK_PARAM is for ensembles only) */
+    int32_t walk;           /* tile order of the batched kernel: LBFD_WALK_STRIDED, _CONTIGUOUS,
+                               _PER_TILE (default) or _PARAM (the members' arguments in the kernel
+                               parameters, one launch per group of up to 112 residents, regrouped
+                               whenever the resident set changes) */
     int32_t vx_max;         /* sites per work item of the batched kernel at most: 2 (members with even Lx
                                take two) or 1 (a kernel without the two-site path, fewer registers) */
     int32_t reserved[5];

@@ -149,6 +149,9 @@ struct lbfd_server {
   bool dirty = true;
   int seg_off[3] = {0, 0, 0}, seg_n[3] = {0, 0, 0}, seg_vx[3] = {1, 1, 1};
   int64_t seg_tiles[3] = {0, 0, 0};
+  // parameter-space launches (tile order LBFD_WALK_PARAM): the segment's
+  // members in groups of up to kParamMembers, rebuilt with every table upload
+  std::vector<BatchParams> groups[3];
   uint64_t clock = 0;
   int64_t n_done = 0, site_updates = 0, resident_bytes = 0, peak_resident_bytes = 0, resident_sites = 0,
           peak_resident_sites = 0, launches = 0;
@@ -421,6 +424,9 @@ int upload_tables(lbfd_server *s) {
     s->seg_vx[L] = 1;
     for (int m = s->seg_off[L]; m < n; ++m) s->seg_vx[L] = std::max(s->seg_vx[L], int(hm[m].vx));
     s->seg_tiles[L] = batch_assign_tiles(hm + s->seg_off[L], s->seg_n[L], s->opt.passes, hts + s->seg_off[L]);
+    if (s->opt.walk == LBFD_WALK_PARAM)
+      batch_build_params(hm + s->seg_off[L], s->seg_n[L], s->seg_tiles[L], s->opt.noise_mode, s->opt.noise_dist,
+                         s->groups[L]);
   }
   if (n > 0) {
     SRV_CU(cudaMemcpyAsync(s->d_members, hm, sizeof(BatchMember) * size_t(n), cudaMemcpyHostToDevice, s->cs));
@@ -457,12 +463,20 @@ int tick(lbfd_server *s) {
     cudaStream_t st = fork ? s->ls[L] : s->cs;
     if (fork) SRV_CU(cudaStreamWaitEvent(st, s->fork_ev, 0));
     const int vx = s->seg_vx[L];
-    const int grid =
-        int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L][vx - 1])));
-    SRV_CU(launch_batch_step(L, s->opt.precision, s->arena, s->d_steps + s->seg_off[L], s->d_tile_start + s->seg_off[L],
-                             s->seg_n[L], s->seg_tiles[L], s->opt.passes, s->opt.occupancy, s->opt.walk, vx,
-                             s->opt.noise_mode, s->opt.noise_dist, grid, st));
-    s->launches += 1;
+    if (s->opt.walk == LBFD_WALK_PARAM) {
+      // one launch per group, the members' arguments in the kernel parameters
+      const int G = static_cast<int>(s->groups[L].size());
+      SRV_CU(launch_batch_param(L, s->opt.precision, s->arena, s->groups[L].data(), G, s->d_steps + s->seg_off[L],
+                                s->opt.passes, s->opt.occupancy, vx, s->opt.noise_mode, s->opt.noise_dist, st));
+      s->launches += G;
+    } else {
+      const int grid =
+          int(std::max<int64_t>(1, std::min<int64_t>(s->seg_tiles[L], int64_t(s->sms) * s->bps[L][vx - 1])));
+      SRV_CU(launch_batch_step(L, s->opt.precision, s->arena, s->d_steps + s->seg_off[L],
+                               s->d_tile_start + s->seg_off[L], s->seg_n[L], s->seg_tiles[L], s->opt.passes,
+                               s->opt.occupancy, s->opt.walk, vx, s->opt.noise_mode, s->opt.noise_dist, grid, st));
+      s->launches += 1;
+    }
     if (fork) {
       SRV_CU(cudaEventRecord(s->lat_ev[L], st));
       SRV_CU(cudaStreamWaitEvent(s->cs, s->lat_ev[L], 0));
@@ -581,8 +595,9 @@ int lbfd_server_create(lbfd_server_t *out, const lbfd_server_options *opt) {
     return srv_fail(LBFD_EINVAL, "server: unknown policy");
   if (o.occupancy != 0 && o.occupancy != 1) return srv_fail(LBFD_EINVAL, "server: occupancy must be 0 or 1");
   if (o.vx_max != 1 && o.vx_max != 2) return srv_fail(LBFD_EINVAL, "server: vx_max must be 1 or 2");
-  if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS && o.walk != LBFD_WALK_PER_TILE)
-    return srv_fail(LBFD_EINVAL, "server: walk must be LBFD_WALK_STRIDED, _CONTIGUOUS or _PER_TILE");
+  if (o.walk != LBFD_WALK_STRIDED && o.walk != LBFD_WALK_CONTIGUOUS && o.walk != LBFD_WALK_PER_TILE &&
+      o.walk != LBFD_WALK_PARAM)
+    return srv_fail(LBFD_EINVAL, "server: walk must be LBFD_WALK_STRIDED, _CONTIGUOUS, _PER_TILE or _PARAM");
   if (o.max_active_sites < 0) return srv_fail(LBFD_EINVAL, "server: max_active_sites must be >= 0");
   if (o.solo_sites < 0) return srv_fail(LBFD_EINVAL, "server: solo_sites must be >= 0");
   int dev = o.device;

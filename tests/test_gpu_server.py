@@ -78,7 +78,8 @@ def _mixed_specs(precision):
 @pytest.mark.parametrize("precision,solo,walk,vx_max", [
     (lb.F32, 0, lb.WALK_STRIDED, 2), (lb.F32, 400, lb.WALK_STRIDED, 2), (lb.F64, 400, lb.WALK_CONTIGUOUS, 2),
     (lb.F32_F16, 0, lb.WALK_CONTIGUOUS, 1), (lb.F32_F16, 1000, lb.WALK_STRIDED, 2), (lb.F32, 0, lb.WALK_CONTIGUOUS, 1),
-    (lb.F32, 0, lb.WALK_CONTIGUOUS, 2), (lb.F32, 400, lb.WALK_PER_TILE, 2), (lb.F32_BF16, 0, lb.WALK_PER_TILE, 1)])
+    (lb.F32, 0, lb.WALK_CONTIGUOUS, 2), (lb.F32, 400, lb.WALK_PER_TILE, 2), (lb.F32_BF16, 0, lb.WALK_PER_TILE, 1),
+    (lb.F32, 400, lb.WALK_PARAM, 2), (lb.F32_F16, 0, lb.WALK_PARAM, 1)])
 def test_served_results_bit_identical_to_alone(precision, solo, walk, vx_max):
     """solo: simulations of at least this many sites take their own
     single-lattice launch each step (0: all batched); walk and vx_max: tile

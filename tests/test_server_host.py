@@ -104,7 +104,7 @@ def test_server_option_defaults_and_checks():
     h = ctypes.c_void_p()
     for field, bad in [("passes", 3), ("max_active", 0), ("max_ahead", 0), ("policy", 7), ("precision", 9),
                        ("hbm_budget", 16), ("solo_sites", -1), ("occupancy", 2),
-                       ("walk", 3), ("vx_max", 0), ("vx_max", 3)]:
+                       ("walk", 4), ("vx_max", 0), ("vx_max", 3)]:
         b = abi.lbfd_server_options_init()
         setattr(b, field, bad)
         assert lib.lbfd_server_create(ctypes.byref(h), ctypes.byref(b)) == abi.EINVAL, field
