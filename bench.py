@@ -526,9 +526,9 @@ def main():
     ap.add_argument("--policy", default="shortest", choices=["fifo", "shortest", "longest"])
     ap.add_argument("--passes", type=int, default=4)
     ap.add_argument("--occupancy", type=int, default=0)
-    ap.add_argument("--walk", default="per_tile", choices=WALKS)
+    ap.add_argument("--walk", default="param", choices=WALKS)
     ap.add_argument("--vx-max", type=int, default=2, choices=[1, 2])
-    ap.add_argument("--solo-sites", type=int, default=1 << 17)
+    ap.add_argument("--solo-sites", type=int, default=0)
     ap.add_argument("--max-active-sites", type=int, default=20_000_000)
     ap.add_argument("--sink-mb", type=int, default=2048)
     ap.add_argument("--plain-requests", type=int, default=-1)
