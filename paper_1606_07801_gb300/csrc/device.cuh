@@ -72,6 +72,109 @@ __host__ __device__ __forceinline__ double sub_rn(double a, double b) {
   return a - b;  // host code is compiled without FMA contraction
 #endif
 }
+__host__ __device__ __forceinline__ double mul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;  // host code is compiled without FMA contraction
+#endif
+}
+__host__ __device__ __forceinline__ float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
+}
+__host__ __device__ __forceinline__ double fma_rn(double a, double b, double c) {
+#ifdef __CUDA_ARCH__
+  return __fma_rn(a, b, c);
+#else
+  return fma(a, b, c);
+#endif
+}
+
+// ---------------------------------------------------------------------------
+// Two sites at once.  From sm_100 on, an FP32 add, multiply or fused
+// multiply-add can act on a pair of registers (add/mul/fma.rn.f32x2), each
+// lane rounded exactly as the scalar instruction rounds it.  The collision
+// is written once over a value type V -- float or double for one site, float2
+// for the same quantity of two neighbouring sites -- with every operation an
+// explicit add_rn / sub_rn / mul_rn / fma_rn, so that nothing is fused
+// differently in the two forms and a site's update is the same bit pattern
+// whether a thread computes it alone or paired with the next site.
+// Conversions, comparisons and the special-function unit act lane by lane.
+// ---------------------------------------------------------------------------
+template <typename V>
+struct LaneOf {
+  using type = V;
+  static constexpr int kLanes = 1;
+};
+template <>
+struct LaneOf<float2> {
+  using type = float;
+  static constexpr int kLanes = 2;
+};
+template <typename V>
+__host__ __device__ __forceinline__ V splat(typename LaneOf<V>::type s) {
+  if constexpr (LaneOf<V>::kLanes == 2)
+    return make_float2(s, s);
+  else
+    return s;
+}
+// A compile-time constant rounded once to the lane type.
+template <typename V>
+__host__ __device__ __forceinline__ V cst(double c) {
+  return splat<V>(static_cast<typename LaneOf<V>::type>(c));
+}
+// (Before sm_100, and on the host, two scalar operations.)
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define LBFD_F32X2 1
+#endif
+__host__ __device__ __forceinline__ float2 add_rn(float2 a, float2 b) {
+#ifdef LBFD_F32X2
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(add_rn(a.x, b.x), add_rn(a.y, b.y));
+#endif
+}
+__host__ __device__ __forceinline__ float2 sub_rn(float2 a, float2 b) {
+#ifdef LBFD_F32X2
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+#else
+  return make_float2(sub_rn(a.x, b.x), sub_rn(a.y, b.y));
+#endif
+}
+__host__ __device__ __forceinline__ float2 mul_rn(float2 a, float2 b) {
+#ifdef LBFD_F32X2
+  return __fmul2_rn(a, b);
+#else
+  return make_float2(mul_rn(a.x, b.x), mul_rn(a.y, b.y));
+#endif
+}
+__host__ __device__ __forceinline__ float2 fma_rn(float2 a, float2 b, float2 c) {
+#ifdef LBFD_F32X2
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(fma_rn(a.x, b.x, c.x), fma_rn(a.y, b.y, c.y));
+#endif
+}
+// x where x > 0, else +0 (also for NaN), lane by lane.
+template <typename V>
+__host__ __device__ __forceinline__ V positive_part(V x) {
+  if constexpr (LaneOf<V>::kLanes == 2)
+    return make_float2(x.x > 0.0f ? x.x : 0.0f, x.y > 0.0f ? x.y : 0.0f);
+  else
+    return x > V(0) ? x : V(0);
+}
+// v < t ? a : b, lane by lane.
+template <typename V>
+__host__ __device__ __forceinline__ V select_below(V v, typename LaneOf<V>::type t, V a, V b) {
+  if constexpr (LaneOf<V>::kLanes == 2)
+    return make_float2(v.x < t ? a.x : b.x, v.y < t ? a.y : b.y);
+  else
+    return v < t ? a : b;
+}
 
 template <typename S>
 struct Store;
@@ -217,6 +320,14 @@ struct Lattice<kD2Q5> {
   }
   __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
 };
+
+// The first moving velocity j >= 1 with the weight of velocity i.
+template <int LAT>
+__host__ __device__ constexpr int first_of_weight(int i) {
+  for (int j = 1; j < i; ++j)
+    if (Lattice<LAT>::w(j) == Lattice<LAT>::w(i)) return j;
+  return i;
+}
 
 // ---------------------------------------------------------------------------
 // Moment basis by weighted Gram-Schmidt, evaluated by the compiler.
@@ -375,6 +486,10 @@ __host__ __device__ __forceinline__ float noise_amplitude<float>(float x) {
   return sqrtf(x);
 #endif
 }
+template <>
+__host__ __device__ __forceinline__ float2 noise_amplitude<float2>(float2 x) {
+  return make_float2(noise_amplitude<float>(x.x), noise_amplitude<float>(x.y));
+}
 
 // Box-Muller pair (z0, z1) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1) from
 // two Philox words, u = ((r >> 8) + 1/2) 2^-24.
@@ -405,26 +520,9 @@ template <>
 struct BoxMuller<float> {
   __host__ __device__ static __forceinline__ void pair(uint32_t r0, uint32_t r1, float &z0, float &z1) {
 #ifdef __CUDA_ARCH__
-    // u0 = (k + 1/2) 2^-24 is one rounding of k 2^-24 + 2^-25, and v = 1 - u0
-    // = (1 - k 2^-24) - 2^-25: both steps exact wherever v < 1/2 (k 2^-24 has
-    // 24 significant bits at most)
-    const float k0 = static_cast<float>(r0 >> 8);
-    const float u0 = fmaf(k0, 5.9604644775390625e-08f, 2.98023223876953125e-08f);
-    const float v = fmaf(k0, -5.9604644775390625e-08f, 1.0f) - 2.98023223876953125e-08f;
-    // -2 ln(1 - v) = v (2 + v (1 + v (2/3 + v/2))) + O(v^5), used below 1/64;
-    // above, -2 ln u0 = -2 ln(2) log2(u0)
-    const float series = v * fmaf(v, fmaf(v, fmaf(v, 0.5f, 0.6666667f), 1.0f), 2.0f);
-    const float x = v < 0.015625f ? series : -1.38629436111989061f * __log2f(u0);  // x >= 2^-24 > 0
-    const float rad = sqrt_sfu(x);
-    // angle 2 pi u1 taken to [-pi, pi): the arithmetic shift of the word is
-    // (r1 >> 8) - 2^24 when the top bit is set, an exact turn less
-    const float angle = fmaf(static_cast<float>(static_cast<int32_t>(r1) >> 8),
-                             3.7450703871400037e-07f /* 2 pi 2^-24 */,
-                             1.8725351935700019e-07f /* pi 2^-24 */);
-    float s, c;
-    __sincosf(angle, &s, &c);
-    z0 = rad * c;
-    z1 = rad * s;
+    // the arithmetic shift of the angle word is (r1 >> 8) - 2^24 when the top
+    // bit is set, an exact turn less
+    sfu_pair<float>(static_cast<float>(r0 >> 8), static_cast<float>(static_cast<int32_t>(r1) >> 8), z0, z1);
 #else
     const float rad = sqrtf(-2.0f * logf(unit24<float>(r0)));
     float s, c;
@@ -433,6 +531,52 @@ struct BoxMuller<float> {
     z1 = rad * s;
 #endif
   }
+#ifdef __CUDACC__
+  // The pairs of two sites (words ra0, ra1 and rb0, rb1) in the two lanes:
+  // lane by lane the same values as pair().
+  __device__ static __forceinline__ void pair2(uint32_t ra0, uint32_t ra1, uint32_t rb0, uint32_t rb1, float2 &z0,
+                                               float2 &z1) {
+    sfu_pair<float2>(make_float2(static_cast<float>(ra0 >> 8), static_cast<float>(rb0 >> 8)),
+                     make_float2(static_cast<float>(static_cast<int32_t>(ra1) >> 8),
+                                 static_cast<float>(static_cast<int32_t>(rb1) >> 8)),
+                     z0, z1);
+  }
+#endif
+
+ private:
+#ifdef __CUDACC__
+  // k0 = r0 >> 8 and k1 = the arithmetic shift r1 >> 8 as floats (exact).
+  template <typename V>
+  __device__ static __forceinline__ void sfu_pair(V k0, V k1, V &z0, V &z1) {
+    // u0 = (k + 1/2) 2^-24 is one rounding of k 2^-24 + 2^-25, and v = 1 - u0
+    // = (1 - k 2^-24) - 2^-25: both steps exact wherever v < 1/2 (k 2^-24 has
+    // 24 significant bits at most)
+    const V u0 = fma_rn(k0, splat<V>(5.9604644775390625e-08f), splat<V>(2.98023223876953125e-08f));
+    const V v = sub_rn(fma_rn(k0, splat<V>(-5.9604644775390625e-08f), splat<V>(1.0f)),
+                       splat<V>(2.98023223876953125e-08f));
+    // -2 ln(1 - v) = v (2 + v (1 + v (2/3 + v/2))) + O(v^5), used below 1/64;
+    // above, -2 ln u0 = -2 ln(2) log2(u0)
+    const V series = mul_rn(
+        v, fma_rn(v, fma_rn(v, fma_rn(v, splat<V>(0.5f), splat<V>(0.6666667f)), splat<V>(1.0f)), splat<V>(2.0f)));
+    const V lg = mul_rn(splat<V>(-1.38629436111989061f), log2_sfu(u0));
+    const V x = select_below(v, 0.015625f, series, lg);  // x >= 2^-24 > 0
+    const V rad = noise_amplitude<V>(x);
+    // angle 2 pi u1 taken to [-pi, pi)
+    const V angle = fma_rn(k1, splat<V>(3.7450703871400037e-07f) /* 2 pi 2^-24 */,
+                           splat<V>(1.8725351935700019e-07f) /* pi 2^-24 */);
+    V s, c;
+    sincos_sfu(angle, s, c);
+    z0 = mul_rn(rad, c);
+    z1 = mul_rn(rad, s);
+  }
+  __device__ static __forceinline__ float log2_sfu(float x) { return __log2f(x); }
+  __device__ static __forceinline__ float2 log2_sfu(float2 x) { return make_float2(__log2f(x.x), __log2f(x.y)); }
+  __device__ static __forceinline__ void sincos_sfu(float a, float &s, float &c) { __sincosf(a, &s, &c); }
+  __device__ static __forceinline__ void sincos_sfu(float2 a, float2 &s, float2 &c) {
+    __sincosf(a.x, &s.x, &c.x);
+    __sincosf(a.y, &s.y, &c.y);
+  }
+#endif
 };
 
 // Philox4x32-10 for the step kernel.  In one step every thread's counter is
@@ -501,6 +645,15 @@ __host__ __device__ __forceinline__ uint4 philox_site(uint32_t s_hi, uint32_t s_
 // Call j has counter (site, lattice_id, t_lo, t_hi * 8 + j); moment 4j + k + 1
 // takes word k.  GAUSS: Box-Muller on the word pairs (0,1) and (2,3);
 // otherwise flat variates sqrt(3) (2u - 1).
+// Flat variate sqrt3 (2 u - 1) of the uniform u = (k + 1/2) 2^-24, k = r >> 8
+// given as a float (exact): in exact arithmetic mean 0 and variance 1 - 2^-48.
+template <typename V>
+__host__ __device__ __forceinline__ V flat_variate(V k) {
+  using R = typename LaneOf<V>::type;
+  const V u = mul_rn(add_rn(k, splat<V>(R(0.5))), splat<V>(R(5.9604644775390625e-08)));
+  return mul_rn(cst<V>(kSqrt3), fma_rn(splat<V>(R(2)), u, splat<V>(R(-1))));
+}
+
 template <typename R, int NMOM, bool GAUSS>
 __host__ __device__ __forceinline__ void draw_variates_t(R (&z)[NMOM], uint32_t site, const PhiloxStep &P) {
   constexpr int NCALL = (NMOM + 3) / 4;
@@ -523,10 +676,44 @@ __host__ __device__ __forceinline__ void draw_variates_t(R (&z)[NMOM], uint32_t 
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        if (4 * j + k < NMOM) z[4 * j + k] = R(kSqrt3) * (R(2) * unit24<R>(w[k]) - R(1));
+        if (4 * j + k < NMOM) z[4 * j + k] = flat_variate<R>(static_cast<R>(w[k] >> 8));
     }
   }
 }
+
+#ifdef __CUDACC__
+// The variates of sites (site, site + 1) in the two lanes: lane by lane the
+// same values as draw_variates_t<float, NMOM, GAUSS> of each site.
+template <int NMOM, bool GAUSS>
+__device__ __forceinline__ void draw_variates_pair(float2 (&z)[NMOM], uint32_t site, const PhiloxStep &P) {
+  constexpr int NCALL = (NMOM + 3) / 4;
+  const uint64_t spa = static_cast<uint64_t>(site) * Philox::M0;
+  const uint64_t spb = static_cast<uint64_t>(site + 1u) * Philox::M0;
+#pragma unroll
+  for (int j = 0; j < NCALL; ++j) {
+    const uint4 ra = philox_site(static_cast<uint32_t>(spa >> 32), static_cast<uint32_t>(spa), P, j);
+    const uint4 rb = philox_site(static_cast<uint32_t>(spb >> 32), static_cast<uint32_t>(spb), P, j);
+    const uint32_t wa[4] = {ra.x, ra.y, ra.z, ra.w}, wb[4] = {rb.x, rb.y, rb.z, rb.w};
+    if constexpr (GAUSS) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        if (4 * j + 2 * p < NMOM) {
+          float2 z0, z1;
+          BoxMuller<float>::pair2(wa[2 * p], wa[2 * p + 1], wb[2 * p], wb[2 * p + 1], z0, z1);
+          z[4 * j + 2 * p] = z0;
+          if (4 * j + 2 * p + 1 < NMOM) z[4 * j + 2 * p + 1] = z1;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (4 * j + k < NMOM)
+          z[4 * j + k] =
+              flat_variate<float2>(make_float2(static_cast<float>(wa[k] >> 8), static_cast<float>(wb[k] >> 8)));
+    }
+  }
+}
+#endif
 
 template <typename R, int NMOM>
 __host__ __device__ __forceinline__ void draw_variates(R (&z)[NMOM], uint32_t site, const PhiloxStep &P, int dist) {
@@ -569,31 +756,51 @@ constexpr bool basis_has_parity() {
 
 // Generic transform, weighted: wT_i = w_i sum_{a>=1} m_i^a z^a.  The
 // constants w_i m_i^a are folded at compile time and zeros skipped; each pair
-// (i, -i) shares its even part E and odd part O: wT_i = E + O, wT_-i = E - O.
+// (i, -i) shares its even part E and odd part O: wT_i = E + O, wT_-i = E - O,
+// or, when O is a single term c z, wT_+-i = fma(+-c, z, E).  apply() takes z
+// and returns wT as R (one site) or, for R = float, float2 (two sites).
 template <int LAT, typename R>
 struct NoiseTransform {
   static constexpr bool kWeighted = true;
   static_assert(basis_has_parity<LAT>(), "basis rows must have definite parity");
+  // number of terms of part<I, PAR>
   template <int I, int PAR>
-  __host__ __device__ static __forceinline__ R part(const R (&z)[Lattice<LAT>::Q - 1]) {
+  static constexpr int terms() {
     constexpr int Q = Lattice<LAT>::Q;
-    R acc = R(0);
+    int n = 0;
+    for (int a = 1; a < Q; ++a)
+      if (kBasisTable<LAT>.m[a][I] != 0.0 && (PAR < 0 || row_parity<LAT>(a) == PAR)) ++n;
+    return n;
+  }
+  // the row of the first term of part<I, PAR>
+  template <int I, int PAR>
+  static constexpr int first_row() {
+    constexpr int Q = Lattice<LAT>::Q;
+    for (int a = 1; a < Q; ++a)
+      if (kBasisTable<LAT>.m[a][I] != 0.0 && (PAR < 0 || row_parity<LAT>(a) == PAR)) return a;
+    return 0;
+  }
+  template <int I, int PAR, typename V>
+  __host__ __device__ static __forceinline__ V part(const V (&z)[Lattice<LAT>::Q - 1]) {
+    constexpr int Q = Lattice<LAT>::Q;
+    V acc = splat<V>(0);
     bool first = true;
     static_for<Q - 1>([&](auto A) {
       constexpr int a = decltype(A)::value + 1;
       constexpr double c = kBasis<LAT, a, I> * Lattice<LAT>::w(I);
       if constexpr (c != 0.0 && (PAR < 0 || row_parity<LAT>(a) == PAR)) {
         if (first) {
-          acc = R(c) * z[a - 1];
+          acc = mul_rn(cst<V>(c), z[a - 1]);
           first = false;
         } else {
-          acc = fma(R(c), z[a - 1], acc);
+          acc = fma_rn(cst<V>(c), z[a - 1], acc);
         }
       }
     });
     return acc;
   }
-  __host__ __device__ static __forceinline__ void apply(const R (&z)[Lattice<LAT>::Q - 1], R (&wT)[Lattice<LAT>::Q]) {
+  template <typename V>
+  __host__ __device__ static __forceinline__ void apply(const V (&z)[Lattice<LAT>::Q - 1], V (&wT)[Lattice<LAT>::Q]) {
     constexpr int Q = Lattice<LAT>::Q;
     static_for<Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
@@ -601,9 +808,17 @@ struct NoiseTransform {
       if constexpr (ip == i) {
         wT[i] = part<i, -1>(z);
       } else if constexpr (i < ip) {
-        const R E = part<i, 0>(z), O = part<i, 1>(z);
-        wT[i] = E + O;
-        wT[ip] = E - O;
+        const V E = part<i, 0>(z);
+        if constexpr (terms<i, 1>() == 1) {
+          constexpr int a = first_row<i, 1>();
+          constexpr double c = kBasis<LAT, a, i> * Lattice<LAT>::w(i);
+          wT[i] = fma_rn(cst<V>(c), z[a - 1], E);
+          wT[ip] = fma_rn(cst<V>(-c), z[a - 1], E);
+        } else {
+          const V O = part<i, 1>(z);
+          wT[i] = add_rn(E, O);
+          wT[ip] = sub_rn(E, O);
+        }
       }
     });
   }
@@ -614,24 +829,31 @@ struct NoiseTransform {
 template <typename R>
 struct NoiseTransform<kD2Q9, R> {
   static constexpr bool kWeighted = false;  // returns T_i; the caller applies w_i
-  __host__ __device__ static __forceinline__ void apply(const R (&z)[8], R (&T)[9]) {
-    // zeta[p][q] = z^{3p+q}, zeta[0][0] = 0
-    const R zeta[3][3] = {{R(0), z[0], z[1]}, {z[2], z[3], z[4]}, {z[5], z[6], z[7]}};
-    R G[3][3];  // G[p][c]: c = 0 (v_y = 0), 1 (v_y = +1), 2 (v_y = -1)
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      G[p][0] = fma(R(-kInvSqrt2), zeta[p][2], zeta[p][0]);
-      const R even = fma(R(kSqrt2), zeta[p][2], zeta[p][0]);
-      G[p][1] = fma(R(kSqrt3), zeta[p][1], even);
-      G[p][2] = fma(R(-kSqrt3), zeta[p][1], even);
+  template <typename V>
+  __host__ __device__ static __forceinline__ void apply(const V (&z)[8], V (&T)[9]) {
+    // zeta[p][q] = z^{3p+q}, zeta[0][0] = 0: the q = 0 terms of p = 0 drop out
+    V G[3][3];  // G[p][c]: c = 0 (v_y = 0), 1 (v_y = +1), 2 (v_y = -1)
+    G[0][0] = mul_rn(cst<V>(-kInvSqrt2), z[1]);
+    {
+      const V even = mul_rn(cst<V>(kSqrt2), z[1]);
+      G[0][1] = fma_rn(cst<V>(kSqrt3), z[0], even);
+      G[0][2] = fma_rn(cst<V>(-kSqrt3), z[0], even);
     }
-    R H[3][3];  // H[cx][cy]
+#pragma unroll
+    for (int p = 1; p < 3; ++p) {
+      const V z0 = z[3 * p - 1], z1 = z[3 * p], z2 = z[3 * p + 1];
+      G[p][0] = fma_rn(cst<V>(-kInvSqrt2), z2, z0);
+      const V even = fma_rn(cst<V>(kSqrt2), z2, z0);
+      G[p][1] = fma_rn(cst<V>(kSqrt3), z1, even);
+      G[p][2] = fma_rn(cst<V>(-kSqrt3), z1, even);
+    }
+    V H[3][3];  // H[cx][cy]
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      H[0][c] = fma(R(-kInvSqrt2), G[2][c], G[0][c]);
-      const R even = fma(R(kSqrt2), G[2][c], G[0][c]);
-      H[1][c] = fma(R(kSqrt3), G[1][c], even);
-      H[2][c] = fma(R(-kSqrt3), G[1][c], even);
+      H[0][c] = fma_rn(cst<V>(-kInvSqrt2), G[2][c], G[0][c]);
+      const V even = fma_rn(cst<V>(kSqrt2), G[2][c], G[0][c]);
+      H[1][c] = fma_rn(cst<V>(kSqrt3), G[1][c], even);
+      H[2][c] = fma_rn(cst<V>(-kSqrt3), G[1][c], even);
     }
     // velocity -> (cx, cy): 0 -> 0, +1 -> 1, -1 -> 2
     T[0] = H[0][0];
@@ -650,11 +872,12 @@ struct NoiseTransform<kD2Q9, R> {
 template <typename R>
 struct NoiseTransform<kD1Q3, R> {
   static constexpr bool kWeighted = false;
-  __host__ __device__ static __forceinline__ void apply(const R (&z)[2], R (&T)[3]) {
-    T[0] = R(-kInvSqrt2) * z[1];
-    const R even = R(kSqrt2) * z[1];
-    T[1] = fma(R(kSqrt3), z[0], even);
-    T[2] = fma(R(-kSqrt3), z[0], even);
+  template <typename V>
+  __host__ __device__ static __forceinline__ void apply(const V (&z)[2], V (&T)[3]) {
+    T[0] = mul_rn(cst<V>(-kInvSqrt2), z[1]);
+    const V even = mul_rn(cst<V>(kSqrt2), z[1]);
+    T[1] = fma_rn(cst<V>(kSqrt3), z[0], even);
+    T[2] = fma_rn(cst<V>(-kSqrt3), z[0], even);
   }
 };
 

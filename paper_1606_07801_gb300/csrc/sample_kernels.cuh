@@ -479,6 +479,13 @@ __device__ __forceinline__ void WarpSampler<LAT, VX>::block_partials(Smem *w, in
 template <int LAT, int VX>
 using SamplerFor = std::conditional_t<(Lattice<LAT>::Q <= 9), ThreadSampler<LAT, VX>, WarpSampler<LAT, VX>>;
 
+// Whether the sampled register-pull kernel collides its sites two at a time
+// (collide_pair): as the unsampled kernel does.
+template <int LAT, typename S, int VX>
+__host__ __device__ constexpr bool sample_pairs() {
+  return step_pairs<LAT, S, VX>();
+}
+
 template <int LAT, typename S, int VX, int NOISE, typename Idx>
 __global__ void __launch_bounds__(kSampleThreads, 2)
     k_step_sample(const S *__restrict__ src, S *__restrict__ dst, const StepArgs a, const SampleArgs sa,
@@ -510,9 +517,7 @@ __global__ void __launch_bounds__(kSampleThreads, 2)
     ws.template add<S>(f, active, x0, y, z, a.Lx, a.Ly, a.Lz, sa);
     // the step: the collision and store of k_step_vec
     if (active) {
-#pragma unroll
-      for (int k = 0; k < VX; ++k)
-        collide_site<LAT, R, NOISE, Store<S>::kDeviation>(f[k], row + static_cast<uint32_t>(x0 + k), a);
+      collide_sites<LAT, S, VX, NOISE, sample_pairs<LAT, S, VX>()>(f, row + static_cast<uint32_t>(x0), a);
       vec_store<LAT, S, VX, Idx>(dst, a, row, x0, f);
     }
   }

@@ -277,6 +277,13 @@ constexpr int kStagedTimeout = 1;
 // 4.5-warp share of each scheduler's 16384 registers allows 96 per thread.
 constexpr int kStagedSampleMinBlocks = 2;
 
+// Whether the staged kernel collides its sites two at a time (collide_pair):
+// as the register-pull kernel does.
+template <int LAT, typename S, int VX, bool SAMPLE>
+__host__ __device__ constexpr bool staged_pairs() {
+  return step_pairs<LAT, S, VX>();
+}
+
 template <int LAT, typename S, int NOISE, bool SAMPLE = false>
 __global__ void __launch_bounds__(StagedShape<LAT, S>::kThreads,
                                   SAMPLE ? kStagedSampleMinBlocks : StagedShape<LAT, S>::kMinBlocks)
@@ -363,9 +370,7 @@ __global__ void __launch_bounds__(StagedShape<LAT, S>::kThreads,
     if (mine) {
       const uint32_t off = static_cast<uint32_t>(m.row) * static_cast<uint32_t>(a.Lx) + static_cast<uint32_t>(m.x0 + k0);
       const uint32_t key = off + rows.row_key * static_cast<uint32_t>(a.Lx);
-#pragma unroll
-      for (int k = 0; k < VX; ++k)
-        collide_site<LAT, R, NOISE, Store<S>::kDeviation>(f[k], key + static_cast<uint32_t>(k), a);
+      collide_sites<LAT, S, VX, NOISE, staged_pairs<LAT, S, VX, SAMPLE>()>(f, key, a);
       staged_store_regs<LAT, S, VX>(dst, off, f, a);
     }
   }
