@@ -127,34 +127,57 @@ template <typename V>
 __host__ __device__ __forceinline__ V cst(double c) {
   return splat<V>(static_cast<typename LaneOf<V>::type>(c));
 }
-// (Before sm_100, and on the host, two scalar operations.)
+// On the device these are the PTX instructions add/sub/mul/fma.rn.f32x2 in
+// inline assembly: an explicit rounding modifier keeps the assembler from
+// fusing a multiply into a following add, and the compiler cannot see into
+// the assembly to fuse them earlier, so a packed product added to something
+// rounds twice, as __fmul_rn and __fadd_rn do.  (Before sm_100, and on the
+// host, two scalar operations.)
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
 #define LBFD_F32X2 1
+__device__ __forceinline__ uint64_t f32x2_bits(float2 a) {
+  uint64_t u;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(u) : "f"(a.x), "f"(a.y));
+  return u;
+}
+__device__ __forceinline__ float2 f32x2_value(uint64_t u) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(u));
+  return a;
+}
 #endif
 __host__ __device__ __forceinline__ float2 add_rn(float2 a, float2 b) {
 #ifdef LBFD_F32X2
-  return __fadd2_rn(a, b);
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f32x2_bits(a)), "l"(f32x2_bits(b)));
+  return f32x2_value(r);
 #else
   return make_float2(add_rn(a.x, b.x), add_rn(a.y, b.y));
 #endif
 }
 __host__ __device__ __forceinline__ float2 sub_rn(float2 a, float2 b) {
 #ifdef LBFD_F32X2
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f32x2_bits(a)), "l"(f32x2_bits(b)));
+  return f32x2_value(r);
 #else
   return make_float2(sub_rn(a.x, b.x), sub_rn(a.y, b.y));
 #endif
 }
 __host__ __device__ __forceinline__ float2 mul_rn(float2 a, float2 b) {
 #ifdef LBFD_F32X2
-  return __fmul2_rn(a, b);
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f32x2_bits(a)), "l"(f32x2_bits(b)));
+  return f32x2_value(r);
 #else
   return make_float2(mul_rn(a.x, b.x), mul_rn(a.y, b.y));
 #endif
 }
 __host__ __device__ __forceinline__ float2 fma_rn(float2 a, float2 b, float2 c) {
 #ifdef LBFD_F32X2
-  return __ffma2_rn(a, b, c);
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f32x2_bits(a)), "l"(f32x2_bits(b)), "l"(f32x2_bits(c)));
+  return f32x2_value(r);
 #else
   return make_float2(fma_rn(a.x, b.x, c.x), fma_rn(a.y, b.y, c.y));
 #endif
