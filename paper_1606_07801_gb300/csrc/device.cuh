@@ -96,7 +96,7 @@ __host__ __device__ __forceinline__ double fma_rn(double a, double b, double c) 
 
 // ---------------------------------------------------------------------------
 // Two sites at once.  From sm_100 on, an FP32 add, multiply or fused
-// multiply-add can act on a pair of registers (add/mul/fma.rn.f32x2), each
+// multiply-add can act on a pair of registers (add/sub/mul/fma.rn.f32x2), each
 // lane rounded exactly as the scalar instruction rounds it.  The collision
 // is written once over a value type V -- float or double for one site, float2
 // for the same quantity of two neighbouring sites -- with every operation an
