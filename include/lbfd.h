@@ -335,6 +335,18 @@ int lbfd_noise_draw(int32_t precision, int32_t dist, uint64_t seed, uint32_t lat
  * temporary device buffers. */
 int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t npairs, double *z_host);
 
+/* The FP32 arithmetic of the collision on given operands, one value at a time
+ * and two values per packed instruction (the step kernels collide two
+ * neighbouring sites at once where that is faster, and the two forms must
+ * round alike).  For k < n (n even) and the operations op = 0 add a + b,
+ * 1 sub a - b, 2 mul a b, 3 fma(a, b, c), 4 (a b) + c and 5 c - (a b) (the
+ * last two rounded twice), out[(2 op + form) n + k] holds the result of
+ * (a[k], b[k], c[k]), form 0 computed alone and form 1 packed with value
+ * k ^ 1.  Host arrays: a, b, c of n floats, out of 12 n.  Current device;
+ * synchronous; allocates temporary device buffers.  LBFD_EINVAL for a null
+ * array or an odd or negative n. */
+int lbfd_lane_ops_probe(const float *a_host, const float *b_host, const float *c_host, int64_t n, float *out_host);
+
 /* Total mass sum_x sum_i f_i, like lbfd_mass, for callers that cannot
  * allocate device memory: a host framework that reserved the GPU for its own
  * allocator and forbids libraries to allocate, a service under a fixed

@@ -978,6 +978,23 @@ int lbfd_box_muller_probe(int32_t precision, const uint32_t *words_host, int64_t
   return LBFD_OK;
 }
 
+int lbfd_lane_ops_probe(const float *a_host, const float *b_host, const float *c_host, int64_t n, float *out_host) {
+  if (!a_host || !b_host || !c_host || !out_host || n < 0 || n % 2)
+    return fail(LBFD_EINVAL, "lbfd_lane_ops_probe: bad argument");
+  if (n == 0) return LBFD_OK;
+  const size_t in_bytes = sizeof(float) * size_t(n), out_bytes = 12 * in_bytes;
+  float *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 3 * in_bytes + out_bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(d, a_host, in_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + n, b_host, in_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + 2 * n, c_host, in_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_lane_ops_probe(d, d + n, d + 2 * n, n, d + 3 * n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out_host, d + 3 * n, out_bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail("lbfd_lane_ops_probe", e);
+  return LBFD_OK;
+}
+
 const char *lbfd_last_error(void) { return g_err.c_str(); }
 
 int64_t lbfd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -201,6 +201,14 @@ cudaError_t launch_noise_draw(int precision, int dist, const PhiloxStep &ph, int
 cudaError_t launch_box_muller_probe(int precision, const uint32_t *words, int64_t npairs, double *z,
                                     cudaStream_t stream);
 
+// The collision's arithmetic on given operands, once per value and once on
+// two values per packed instruction: out[(2 op + form) n + k] for the
+// operations op = add, sub, mul, fma, mul then add, mul then sub of
+// (a[k], b[k], c[k]), form 0 one value at a time, form 1 packed with the
+// neighbour k ^ 1 (n even).
+cudaError_t launch_lane_ops_probe(const float *a, const float *b, const float *c, int64_t n, float *out,
+                                  cudaStream_t stream);
+
 // Deterministic FP64 reductions.
 //   Stage 1 writes per-block partials of `nq` quantities to partials[block][nq];
 //   stage 2 sums them in block order and adds the totals into acc[nq] (or

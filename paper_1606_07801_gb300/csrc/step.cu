@@ -287,6 +287,53 @@ __global__ void k_box_muller_probe(const uint32_t *__restrict__ words, int64_t n
   }
 }
 
+// The lane operations of the collision (add_rn, sub_rn, mul_rn, fma_rn) on
+// float and on float2: a thread takes values 2p and 2p + 1, computes each
+// operation twice per value, one value at a time and both in one packed
+// instruction, and stores both forms.
+__global__ void k_lane_ops_probe(const float *__restrict__ a, const float *__restrict__ b, const float *__restrict__ c,
+                                 int64_t n, float *__restrict__ out) {
+  const int64_t npairs = n / 2;
+  for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < npairs;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t k = 2 * p;
+    const float2 A = make_float2(a[k], a[k + 1]), B = make_float2(b[k], b[k + 1]), C = make_float2(c[k], c[k + 1]);
+    float s[6][2];
+    float2 v[6];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const float x = l ? A.y : A.x, y = l ? B.y : B.x, z = l ? C.y : C.x;
+      s[0][l] = add_rn(x, y);
+      s[1][l] = sub_rn(x, y);
+      s[2][l] = mul_rn(x, y);
+      s[3][l] = fma_rn(x, y, z);
+      s[4][l] = add_rn(mul_rn(x, y), z);
+      s[5][l] = sub_rn(z, mul_rn(x, y));
+    }
+    v[0] = add_rn(A, B);
+    v[1] = sub_rn(A, B);
+    v[2] = mul_rn(A, B);
+    v[3] = fma_rn(A, B, C);
+    v[4] = add_rn(mul_rn(A, B), C);
+    v[5] = sub_rn(C, mul_rn(A, B));
+#pragma unroll
+    for (int op = 0; op < 6; ++op) {
+      out[(2 * op) * n + k] = s[op][0];
+      out[(2 * op) * n + k + 1] = s[op][1];
+      out[(2 * op + 1) * n + k] = v[op].x;
+      out[(2 * op + 1) * n + k + 1] = v[op].y;
+    }
+  }
+}
+
+cudaError_t launch_lane_ops_probe(const float *a, const float *b, const float *c, int64_t n, float *out,
+                                  cudaStream_t stream) {
+  const int64_t blocks = (n / 2 + 255) / 256;
+  const int grid = static_cast<int>(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
+  k_lane_ops_probe<<<grid, 256, 0, stream>>>(a, b, c, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_box_muller_probe(int precision, const uint32_t *words, int64_t npairs, double *z,
                                     cudaStream_t stream) {
   const int64_t blocks = (npairs + 255) / 256;

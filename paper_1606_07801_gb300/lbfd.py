@@ -142,6 +142,7 @@ SIGNATURES = {
     "lbfd_noise_draw": (c_int32, [c_int32, c_int32, c_uint64, c_uint32, c_uint64, c_int64, c_int64, c_int32,
                                   c_void_p]),
     "lbfd_box_muller_probe": (c_int32, [c_int32, c_void_p, c_int64, c_void_p]),
+    "lbfd_lane_ops_probe": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p]),
     "lbfd_mass_noalloc": (c_int32, [c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p]),
     "lbfd_ensemble_create": (c_int32, [P(c_void_p), c_int32, c_int32, c_int32, c_int32, P(Member), c_int32, c_void_p]),
     "lbfd_ensemble_destroy": (c_int32, [c_void_p]),
@@ -427,6 +428,19 @@ def lbfd_box_muller_probe(precision: int, words: np.ndarray) -> np.ndarray:
     z = np.empty(w.size, dtype=np.float64)
     _check(load().lbfd_box_muller_probe(precision, _ptr(w), w.size // 2, _ptr(z)), "lbfd_box_muller_probe")
     return z
+
+
+def lbfd_lane_ops_probe(a: np.ndarray, b: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """[6, 2, n] float32: the collision's six lane operations on (a, b, c),
+    form 0 one value at a time, form 1 two values per packed instruction."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    c = np.ascontiguousarray(c, dtype=np.float32)
+    if not (a.shape == b.shape == c.shape) or a.ndim != 1:
+        raise ValueError("a, b and c must be 1-D arrays of one length")
+    out = np.empty(12 * a.size, dtype=np.float32)
+    _check(load().lbfd_lane_ops_probe(_ptr(a), _ptr(b), _ptr(c), a.size, _ptr(out)), "lbfd_lane_ops_probe")
+    return out.reshape(6, 2, a.size)
 
 
 def lbfd_mass_noalloc(lattice: int, precision: int, f_dev_ptr: int, n_sites: int, mass_dev_ptr: int,

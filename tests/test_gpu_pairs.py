@@ -49,3 +49,62 @@ def test_vector_kernel_bit_identical_to_one_site_per_thread(lat, dims, precision
     b = _run(lat, dims, precision, lb.KERNEL_SCALAR, f0, 4, rho, mode, dist)
     assert np.array_equal(a, b)
     assert not np.array_equal(a, f0)
+
+
+def _lane_operands(n, seed):
+    """Operands that cover what rounding can distinguish: ordinary values at
+    several scales, subnormals, signed zeros, infinities, NaN, near-overflow
+    and exact cancellation, mixed so that the two lanes of a packed
+    instruction see different kinds."""
+    g = np.random.default_rng(seed)
+    kinds = [
+        lambda m: g.standard_normal(m),
+        lambda m: g.standard_normal(m) * 1e-30,
+        lambda m: g.standard_normal(m) * 1e30,
+        lambda m: g.uniform(-1, 1, m) * 1e-38,       # subnormal products and sums
+        lambda m: g.choice([1e-45, -1e-45, 1.4e-40, -2.9e-39], m),
+        lambda m: g.choice([0.0, -0.0], m),
+        lambda m: g.choice([np.inf, -np.inf, np.nan, 3.4e38, -3.4e38], m),
+    ]
+    cols = []
+    for _ in range(3):
+        k = g.integers(0, len(kinds), n)
+        v = np.empty(n)
+        for j, f in enumerate(kinds):
+            sel = k == j
+            v[sel] = f(int(sel.sum()))
+        cols.append(v.astype(np.float32))
+    a, b, c = cols
+    # exact cancellation: c = -(a b) and b = a at some places
+    with np.errstate(all="ignore"):
+        c[::7] = -(a[::7] * b[::7])
+    b[::5] = a[::5]
+    return a, b, c
+
+
+def _same(x, y):
+    both_nan = np.isnan(x) & np.isnan(y)
+    return np.all(both_nan | (x.view(np.uint32) == y.view(np.uint32)))
+
+
+def test_packed_lane_operations_round_as_one_value_at_a_time():
+    """add/sub/mul/fma.rn.f32x2 against the scalar operations, bit for bit,
+    with subnormals kept (no flush to zero) and a product added to a third
+    value rounded twice in both forms (no fusion into an FMA)."""
+    n = 1 << 16
+    a, b, c = _lane_operands(n, 2024)
+    r = abi.lbfd_lane_ops_probe(a, b, c)
+    for op in range(6):
+        assert _same(r[op, 0], r[op, 1]), f"operation {op}: packed and one-at-a-time forms differ"
+    with np.errstate(all="ignore"):
+        ref = [a + b, a - b, a * b, None, (a * b) + c, c - (a * b)]
+    for op in (0, 1, 2, 4, 5):
+        assert _same(r[op, 0], ref[op].astype(np.float32)), f"operation {op} differs from IEEE FP32"
+    # a product added to c rounds twice: somewhere it must differ from the fused form
+    finite = np.isfinite(r[3, 0]) & np.isfinite(r[4, 0])
+    assert np.any(r[3, 0][finite] != r[4, 0][finite])
+
+
+def test_lane_ops_probe_rejects_bad_sizes():
+    with pytest.raises(lb.LbfdError):
+        abi.lbfd_lane_ops_probe(np.zeros(3, np.float32), np.zeros(3, np.float32), np.zeros(3, np.float32))
