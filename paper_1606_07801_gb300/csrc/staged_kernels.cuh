@@ -452,19 +452,19 @@ cudaError_t staged_t(const void *src, void *dst, const StepArgs &a, const Staged
   return staged_noise<LAT, S, kStepNoiseFlat>(src, dst, a, rows, status, wait_test_bytes, stream);
 }
 
-// The fused step-and-sample launch (FP32 arithmetic).  D1Q3 and D2Q9 run
-// the register-pull kernel on a persistent grid with the per-lane register
-// sampler (measured on GB300, the staged kernel with the same sampler, at
-// the one block per SM its registers allow, was no faster).  D3Q19 takes
-// the staged kernel with the tensor-core sampler where the lattice meets its
-// requirements and two of its blocks fit the 228 KB of shared memory of an
-// SM, else the register-pull kernel.  LBFD_SAMPLE_STAGED = 0 keeps the
-// register-pull one (a tuning knob; the results agree within FP32 rounding
-// of the sums, and the state bit for bit).
+// The fused step-and-sample launch (FP32 arithmetic): the register-pull
+// kernel on a persistent grid, with the per-lane register sampler for D1Q3
+// and D2Q9 and the tensor-core sampler for D3Q19 (measured on GB300, the
+// staged kernel with the same samplers was no faster: for D2Q9 at the one
+// block per SM its registers allow; for D3Q19 16-bit 256^3 at a sample every
+// 10 steps 36.8 against 37.7 GLUPS).  LBFD_SAMPLE_STAGED = 1 takes the
+// staged kernel for D3Q19 where the lattice meets its requirements and two
+// of its blocks fit the 228 KB of shared memory of an SM (a tuning knob; the
+// results agree within FP32 rounding of the sums, and the state bit for bit).
 inline bool sample_staged_default() {
   static const bool v = [] {
     const char *e = getenv("LBFD_SAMPLE_STAGED");
-    return !(e && atoi(e) == 0);
+    return e && atoi(e) == 1;
   }();
   return v;
 }

@@ -140,3 +140,32 @@ def test_stage_two_on_the_side_stream_is_joined():
         s.step(3)
         d = s.observables()
     assert c["sum_rho"] == d["sum_rho"] and np.array_equal(c["sum_ff"], d["sum_ff"])
+
+
+STAGED_RUN = """
+import sys
+sys.path.insert(0, {root!r})
+import paper_1606_07801_gb300 as lb
+from tests.test_gpu_fused_sampling import test_fused_sampling_matches_fp64_sums_and_keeps_the_state as check
+check({lat}, {dims!r}, {prec})
+print("staged sampled steps ok")
+"""
+
+
+@pytest.mark.parametrize("lat,dims,prec", [
+    (lb.D3Q19, (40, 33, 21), lb.F32_F16),
+    (lb.D3Q19, (48, 40, 36), lb.F32_BF16),  # both above the many-steps-per-launch paths
+])
+def test_staged_sampled_steps_on_request(lat, dims, prec):
+    """LBFD_SAMPLE_STAGED = 1 (read once per process, hence a child process)
+    samples D3Q19 16-bit lattices in the staged kernel: the same checks as
+    the default register-pull path."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, LBFD_SAMPLE_STAGED="1")
+    r = subprocess.run([sys.executable, "-c", STAGED_RUN.format(root=root, lat=lat, dims=dims, prec=prec)],
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "staged sampled steps ok" in r.stdout
