@@ -480,13 +480,13 @@ template <int LAT, int VX>
 using SamplerFor = std::conditional_t<(Lattice<LAT>::Q <= 9), ThreadSampler<LAT, VX>, WarpSampler<LAT, VX>>;
 
 // Whether the sampled register-pull kernel collides its sites two at a time
-// (collide_pair): as the unsampled kernel does, and for D3Q19 with 16-bit
-// storage at two sites per thread too, where the sampled kernel's 128
-// registers hold both sites' variates (256^3 at a sample every 10 steps:
-// 37.7 against 37.4 GLUPS).
+// (collide_pair): as the unsampled kernel does, and for D3Q19 at two sites
+// per thread too, where the sampled kernel's 128 registers hold both sites'
+// variates (256^3 at a sample every 10 steps: 16-bit 37.7 against 37.4
+// GLUPS, FP32 35.8 against 35.2).
 template <int LAT, typename S, int VX>
 __host__ __device__ constexpr bool sample_pairs() {
-  return step_pairs<LAT, S, VX>() || (LAT == kD3Q19 && Store<S>::kDeviation);
+  return step_pairs<LAT, S, VX>() || LAT == kD3Q19;
 }
 
 template <int LAT, typename S, int VX, int NOISE, typename Idx>
