@@ -81,8 +81,9 @@ extern "C" {
  * Every kernel computes the same site update with the same arithmetic, so the
  * choice changes speed only, never a result bit. */
 #define LBFD_KERNEL_AUTO 0    /* the library's choice (option value only) */
-#define LBFD_KERNEL_VEC 1     /* k_step_vec: two sites of a row per thread, pulled straight from global memory
-                                 (Lx even) */
+#define LBFD_KERNEL_VEC 1     /* k_step_vec: two or four sites of a row per thread, pulled straight from
+                                 global memory (Lx even); FP32-arithmetic formats collide two sites at a time
+                                 on the packed FP32 instructions where that is faster, with the same result */
 #define LBFD_KERNEL_SCALAR 2  /* k_step: one site per thread (any Lx) */
 #define LBFD_KERNEL_SMALL 3   /* k_step_small: many steps per launch in one block's shared memory (small
                                  lattices, n >= 2; chosen automatically) */
