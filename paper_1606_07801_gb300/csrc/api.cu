@@ -472,7 +472,24 @@ int lbfd_destroy(lbfd_t h) {
 static int sample_now(lbfd_sim *h) {
   const lbfd_options &o = h->opt;
   LBFD_CU(obs_join(h));
-  if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
+  if ((o.lattice == LBFD_D1Q3 || o.lattice == LBFD_D2Q9) && !h->slab &&
+      sample_fusable(o.lattice, o.precision, int32_t(o.dims[0]), int32_t(o.dims[1]), int32_t(o.dims[2]), o.n_modes,
+                     h->phase)) {
+    // FP32 arithmetic, register sampler: the fused step's sampler as a pass
+    // of its own over the lattice's register-pull blocks, then stage 2
+    StepArgs a{};
+    a.Lx = h->sd[0];
+    a.Ly = h->sd[1];
+    a.Lz = h->sd[2];
+    a.N = h->NS;
+    fill_step_params(a, o.tau, o.rho_mean);
+    int nblocks = 0;
+    LBFD_CU(launch_obs_sample(o.lattice, o.precision, h->f[h->cur], a, o.n_modes, h->phase, h->partials, &nblocks,
+                              h->stream));
+    LBFD_CU(launch_obs_pull_finalize(o.lattice, h->partials, nblocks, o.n_modes, h->N, o.rho_mean, h->fin, h->acc,
+                                     h->stream));
+    g_launches.fetch_add(2, std::memory_order_relaxed);
+  } else if (o.precision != LBFD_F64 && h->N < (int64_t(1) << 31)) {
     // FP32 arithmetic: pulled straight from the stored state
     LBFD_CU(launch_observables_pull(o.lattice, o.precision, h->f[h->cur], int32_t(o.dims[0]), int32_t(o.dims[1]),
                                     int32_t(o.dims[2]), o.rho_mean, o.n_modes, &h->modes_host[0][0], h->phase,

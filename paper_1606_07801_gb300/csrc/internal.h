@@ -340,6 +340,22 @@ inline cudaError_t launch_step_sample(int lattice, int precision, const void *sr
   return cudaErrorInvalidValue;
 }
 
+// The observables of a state without a step, for the register-sampler
+// lattices (D1Q3, D2Q9; FP32 arithmetic; the shape sample_fusable accepts):
+// the sampler of the fused step as the separate sampling pass, in the
+// partials layout of k_obs_pull (then launch_obs_pull_finalize).
+// cudaErrorInvalidValue for other lattices.
+cudaError_t launch_obs_sample_d1q3(int precision, const void *src, const StepArgs &a, int n_modes,
+                                   const void *phase, double *partials, int *nblocks, cudaStream_t stream);
+cudaError_t launch_obs_sample_d2q9(int precision, const void *src, const StepArgs &a, int n_modes,
+                                   const void *phase, double *partials, int *nblocks, cudaStream_t stream);
+inline cudaError_t launch_obs_sample(int lattice, int precision, const void *src, const StepArgs &a, int n_modes,
+                                     const void *phase, double *partials, int *nblocks, cudaStream_t stream) {
+  if (lattice == kD1Q3) return launch_obs_sample_d1q3(precision, src, a, n_modes, phase, partials, nblocks, stream);
+  if (lattice == kD2Q9) return launch_obs_sample_d2q9(precision, src, a, n_modes, phase, partials, nblocks, stream);
+  return cudaErrorInvalidValue;
+}
+
 // Records msg as the calling thread's lbfd_last_error() and returns code.
 int set_last_error(int code, const std::string &msg);
 

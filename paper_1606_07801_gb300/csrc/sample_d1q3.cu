@@ -13,4 +13,12 @@ cudaError_t launch_step_sample_d1q3(int precision, const void *src, void *dst, c
   });
 }
 
+cudaError_t launch_obs_sample_d1q3(int precision, const void *src, const StepArgs &a, int n_modes,
+                                   const void *phase, double *partials, int *nblocks, cudaStream_t stream) {
+  return dispatch_storage(precision, [&](auto tag) {
+    using S = typename decltype(tag)::type;
+    return obs_sample_t<kD1Q3, S>(src, a, n_modes, phase, partials, nblocks, stream);
+  });
+}
+
 }  // namespace lbfd

@@ -555,6 +555,65 @@ cudaError_t sample_launch(const void *src, void *dst, const StepArgs &a, const S
   return cudaGetLastError();
 }
 
+// The sampled observables of a state alone, without the step: the pull and
+// the sampler of k_step_sample on a persistent grid.  The separate sampling
+// pass of the register-sampler lattices (D1Q3, D2Q9), in the partials
+// layout of k_obs_pull.
+template <int LAT, typename S, int VX, typename Idx>
+__global__ void __launch_bounds__(kSampleThreads, 2)
+    k_obs_sample(const S *__restrict__ src, const StepArgs a, const SampleArgs sa, double *__restrict__ partials) {
+  using L = Lattice<LAT>;
+  using R = typename Store<S>::R;
+  using WS = SamplerFor<LAT, VX>;
+  constexpr int Q = L::Q;
+  extern __shared__ __align__(16) unsigned char sample_smem[];
+  typename WS::Smem *wsm = reinterpret_cast<typename WS::Smem *>(sample_smem);
+  const int tid = static_cast<int>(threadIdx.x + blockDim.x * threadIdx.y);
+  const int warp = tid >> 5;
+  WS ws;
+  ws.init(&wsm[warp], tid & 31);
+  for (int vb = blockIdx.x; vb < sa.nvb; vb += gridDim.x) {
+    const int vbx = vb % sa.gx, vr = vb / sa.gx;
+    const int vby = vr % sa.gy, vbz = vr / sa.gy;
+    const int x0 = (vbx * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x)) * VX;
+    const int y = vby * static_cast<int>(blockDim.y) + static_cast<int>(threadIdx.y);
+    const int z = vbz;
+    const bool active = x0 < a.Lx && y < a.Ly;
+    R f[VX][Q];
+    if (active) (void)vec_pull<LAT, S, VX, Idx>(src, a, x0, y, z, f);
+    ws.template add<S>(f, active, x0, y, z, a.Lx, a.Ly, a.Lz, sa);
+  }
+  ws.flush(sa.K);
+  __syncthreads();
+  const int nq = 2 + Q + 2 * sa.K + Q * (Q + 1) / 2;
+  WS::block_partials(wsm, kSampleWarps, sa.K, partials + static_cast<size_t>(blockIdx.x) * nq, tid, kSampleThreads,
+                     [] { __syncthreads(); });
+}
+
+template <int LAT, typename S, int VX, typename Idx>
+cudaError_t obs_sample_launch(const void *src, const StepArgs &a, const SampleArgs &sa_in, dim3 block,
+                              double *partials, int *nblocks, cudaStream_t stream) {
+  auto kern = k_obs_sample<LAT, S, VX, Idx>;
+  constexpr size_t smem = kSampleWarps * sizeof(typename SamplerFor<LAT, VX>::Smem);
+  static std::atomic<int> slots{0};  // resident blocks per SM times SMs, found once
+  int g = slots.load(std::memory_order_relaxed);
+  if (g == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int dev = 0, sms = 0, occ = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSampleThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1 || sms < 1) return cudaErrorInvalidConfiguration;
+    g = std::min(occ * sms, kObsBlocks);
+    slots.store(g, std::memory_order_relaxed);
+  }
+  const int grid = std::max(1, std::min(sa_in.nvb, g));
+  *nblocks = grid;
+  kern<<<grid, block, smem, stream>>>(static_cast<const S *>(src), a, sa_in, partials);
+  return cudaGetLastError();
+}
+
 // Arguments of a fused sampled step for a lattice in FP32 arithmetic.
 template <int LAT>
 inline SampleArgs make_sample_args(const StepArgs &a, int n_modes, const void *phase, const dim3 &grid) {
@@ -593,6 +652,29 @@ cudaError_t sample_vec_t(const void *src, void *dst, const StepArgs &a, int n_mo
   if (a.noise_mode == kNoiseOff) return go(std::integral_constant<int, kStepNoiseOff>{});
   if (a.noise_dist == kGaussian) return go(std::integral_constant<int, kStepNoiseGauss>{});
   return go(std::integral_constant<int, kStepNoiseFlat>{});
+}
+
+// The separate sampling pass on the register-pull kernel's blocks (D1Q3,
+// D2Q9, FP32 arithmetic, the shape sample_fusable accepts).
+template <int LAT, typename S>
+cudaError_t obs_sample_t(const void *src, const StepArgs &a, int n_modes, const void *phase, double *partials,
+                         int *nblocks, cudaStream_t stream) {
+  if constexpr (sizeof(typename Store<S>::R) != 4 || Lattice<LAT>::Q > 9) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (n_modes < 0 || n_modes > kFusedModes || (n_modes > 0 && !phase)) return cudaErrorInvalidValue;
+    const int vx = step_vec_width(LAT, Store<S>::kDeviation ? kStoreF16 : kStoreF32, a.Lx) >= 2 ? 2 : 1;
+    dim3 grid, block;
+    step_shape(a.Lx, a.Ly, a.Lz, grid, block, vx);
+    if (block.x * block.y != kSampleThreads || block.x % 32 != 0) return cudaErrorInvalidValue;
+    const SampleArgs sa = make_sample_args<LAT>(a, n_modes, phase, grid);
+    const bool fit32 = offsets_fit_32(Lattice<LAT>::Q, a.N);
+    if (vx == 2)
+      return fit32 ? obs_sample_launch<LAT, S, 2, uint32_t>(src, a, sa, block, partials, nblocks, stream)
+                   : obs_sample_launch<LAT, S, 2, size_t>(src, a, sa, block, partials, nblocks, stream);
+    return fit32 ? obs_sample_launch<LAT, S, 1, uint32_t>(src, a, sa, block, partials, nblocks, stream)
+                 : obs_sample_launch<LAT, S, 1, size_t>(src, a, sa, block, partials, nblocks, stream);
+  }
 }
 
 }  // namespace lbfd

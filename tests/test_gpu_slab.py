@@ -146,14 +146,21 @@ def test_slab_mass_and_observables_sum_to_the_whole(lat, gdims, prec, nranks, mo
 
 
 def test_sample_totals_of_a_whole_handle_match_lbfd_sample():
-    """For a whole lattice, lbfd_sample_totals + lbfd_obs_restore is the
-    separate sampling pass with the stage-2 sum taken on the host."""
+    """For a whole lattice, lbfd_sample_totals + lbfd_obs_restore gives the
+    observables of lbfd_sample's separate pass with the stage-2 sum taken on
+    the host.  (For D2Q9 the separate pass runs the step's register sampler,
+    and lbfd_sample_totals the site-range pass: the same FP32 values summed
+    in another order, hence FP32-level tolerances.)"""
     lat, dims, modes = lb.D2Q9, (96, 70), [(1, 2, 0), (3, 0, 0)]
-    with lb.Simulation(lat, dims, 0.8, 40.0, 2, modes=modes) as s:
+    rho, N = 40.0, 96 * 70
+    with lb.Simulation(lat, dims, 0.8, rho, 2, modes=modes) as s:
         s.step(5)
         s.sample()
         want = s.observables()
         t = abi.lbfd_sample_totals(s.h, 9, len(modes))
-        got = abi.lbfd_obs_restore(lat, len(modes), 40.0, 96 * 70, t)
-    flat = np.concatenate([[want["sum_rho"], want["sum_rho2"]], want["sum_f"], np.ravel(want["sum_ff"]), want["sum_sk"]])
-    assert np.allclose(got, flat, rtol=1e-12, atol=1e-12 * abs(flat).max())
+        got = abi.lbfd_obs_restore(lat, len(modes), rho, N, t)
+    flat = np.concatenate([[want["sum_rho"], want["sum_rho2"]], want["sum_f"], np.ravel(want["sum_ff"])])
+    nk = len(modes)
+    assert np.allclose(got[:-nk], flat, rtol=2e-6, atol=0.0)
+    sk = np.asarray(want["sum_sk"])
+    assert np.all(np.abs(got[-nk:] - sk) <= 1e-4 * sk + 1e-3 * N * rho)
