@@ -154,22 +154,24 @@ __device__ __forceinline__ void step_scalar_body(const S *__restrict__ src, S *_
   using L = Lattice<LAT>;
   using R = typename Store<S>::R;
   constexpr int Q = L::Q;
-  // periodic neighbours
-  const int xm = (x == 0 ? a.Lx : x) - 1, xp = (x + 1 == a.Lx) ? 0 : x + 1;
-  const int ym = (y == 0 ? a.Ly : y) - 1, yp = (y + 1 == a.Ly) ? 0 : y + 1;
-  const int zm = (z == 0 ? a.Lz : z) - 1, zp = (z + 1 == a.Lz) ? 0 : z + 1;
   const uint32_t Lx = static_cast<uint32_t>(a.Lx), Lxy = Lx * static_cast<uint32_t>(a.Ly);
+  const uint32_t Lxyz = Lxy * static_cast<uint32_t>(a.Lz);
   const uint32_t s = static_cast<uint32_t>(x) + Lx * static_cast<uint32_t>(y) + Lxy * static_cast<uint32_t>(z);
+  // periodic neighbours as offsets from s (modulo 2^32): to x - 1 and x + 1,
+  // y - 1 and y + 1, z - 1 and z + 1
+  const uint32_t dxm = x == 0 ? Lx - 1u : 0u - 1u, dxp = x + 1 == a.Lx ? 1u - Lx : 1u;
+  const uint32_t dym = y == 0 ? Lxy - Lx : 0u - Lx, dyp = y + 1 == a.Ly ? Lx - Lxy : Lx;
+  const uint32_t dzm = z == 0 ? Lxyz - Lxy : 0u - Lxy, dzp = z + 1 == a.Lz ? Lxy - Lxyz : Lxy;
 
   // pull: population i arrives from x - v_i
   R f[Q];
   static_for<Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     constexpr int vx = L::v(i, 0), vy = L::v(i, 1), vz = L::v(i, 2);
-    const int xs = vx == 0 ? x : (vx > 0 ? xm : xp);
-    const int ys = vy == 0 ? y : (vy > 0 ? ym : yp);
-    const int zs = vz == 0 ? z : (vz > 0 ? zm : zp);
-    const uint32_t so = static_cast<uint32_t>(xs) + Lx * static_cast<uint32_t>(ys) + Lxy * static_cast<uint32_t>(zs);
+    const uint32_t ox = vx == 0 ? 0u : (vx > 0 ? dxm : dxp);
+    const uint32_t oy = vy == 0 ? 0u : (vy > 0 ? dym : dyp);
+    const uint32_t oz = vz == 0 ? 0u : (vz > 0 ? dzm : dzp);
+    const uint32_t so = s + ox + oy + oz;
     f[i] = Store<S>::load(src[static_cast<Idx>(i) * static_cast<Idx>(a.N) + so]);
   });
   collide(f, s, a);
