@@ -13,16 +13,10 @@ namespace lbfd {
 
 enum StepNoise : int { kStepNoiseOff = 0, kStepNoiseGauss = 1, kStepNoiseFlat = 2 };
 
-// Collision of one site in registers: f holds the pulled populations
-// f_i(x, t) on entry and the post-collision f*_i(x) on exit; s is the site
-// index that keys the noise.
-//
-// DEV: f holds the deviations d_i = f_i - w_i rho_mean instead (the 16-bit
-// storage formats).  With rho = rho_mean + drho, drho = sum_i d_i, and
-// 1 - 1/tau = omega, the update f*_i = omega f_i + w_i rho/tau + w_i sigma T_i
-// is d*_i = omega d_i + w_i drho/tau + w_i sigma T_i in exact arithmetic (the
-// w_i rho_mean terms cancel), so the same code runs on the deviations with
-// drho in place of rho; only the noise amplitude needs rho itself.
+// The collision (collide_site below) written once over the value type V of
+// device.cuh's lane arithmetic: V = R for one site, V = float2 (R = float)
+// for sites s and s + 1 in the two lanes.  Every floating-point operation is
+// an explicit add_rn / sub_rn / mul_rn / fma_rn, so both forms round alike.
 template <int LAT, typename R, int NOISE, bool DEV, typename V>
 __device__ __forceinline__ void collide_lanes(V (&f)[Lattice<LAT>::Q], uint32_t s, const StepArgs &a) {
   using L = Lattice<LAT>;
