@@ -143,3 +143,15 @@ def test_create_rejects_bad_paper_variants(kw, code, msg):
     with pytest.raises(abi.LbfdError) as e:
         abi.lbfd_create_ex(o)
     assert e.value.code == code and msg in str(e.value)
+
+
+def test_lane_ops_probe_rejects_bad_arguments_without_gpu():
+    lib = abi.load()
+    x = np.zeros(4, np.float32)
+    p = x.ctypes.data_as(ctypes.c_void_p)
+    out = np.zeros(48, np.float32).ctypes.data_as(ctypes.c_void_p)
+    assert lib.lbfd_lane_ops_probe(p, p, p, 3, out) == abi.EINVAL   # odd count
+    assert lib.lbfd_lane_ops_probe(p, p, p, -2, out) == abi.EINVAL  # negative count
+    assert lib.lbfd_lane_ops_probe(None, p, p, 4, out) == abi.EINVAL
+    assert lib.lbfd_lane_ops_probe(p, p, p, 4, None) == abi.EINVAL
+    assert lib.lbfd_lane_ops_probe(p, p, p, 0, out) == abi.OK        # nothing to do
