@@ -2,6 +2,7 @@
 // noise variates and the noise back-transform the step kernel uses,
 // evaluated by the same source on the host.
 #include <stdint.h>
+#include <string.h>
 
 #include "device.cuh"
 
@@ -16,6 +17,32 @@ static int transform_t(const double *z, double *T) {
   NoiseTransform<LAT, R>::apply(zz, TT);
   for (int i = 0; i < Q; ++i) T[i] = static_cast<double>(TT[i]);
   return NoiseTransform<LAT, R>::kWeighted ? 1 : 0;
+}
+
+// The transform on two sites' variates at once (value type float2) and on
+// each alone (float): lane l of T2 against T of z lane l, as bit patterns.
+// Returns the number of values that differ.
+template <int LAT>
+static int transform_pair_t(const double *z2, double *T2) {
+  constexpr int Q = Lattice<LAT>::Q;
+  float2 zz[Q - 1], TT[Q];
+  float za[Q - 1], zb[Q - 1], Ta[Q], Tb[Q];
+  for (int a = 0; a < Q - 1; ++a) {
+    za[a] = static_cast<float>(z2[a]);
+    zb[a] = static_cast<float>(z2[Q - 1 + a]);
+    zz[a] = make_float2(za[a], zb[a]);
+  }
+  NoiseTransform<LAT, float>::apply(zz, TT);
+  NoiseTransform<LAT, float>::apply(za, Ta);
+  NoiseTransform<LAT, float>::apply(zb, Tb);
+  int bad = 0;
+  for (int i = 0; i < Q; ++i) {
+    T2[i] = static_cast<double>(TT[i].x);
+    T2[Q + i] = static_cast<double>(TT[i].y);
+    bad += memcmp(&TT[i].x, &Ta[i], sizeof(float)) != 0;
+    bad += memcmp(&TT[i].y, &Tb[i], sizeof(float)) != 0;
+  }
+  return bad;
 }
 
 template <typename R, int NMOM>
@@ -35,6 +62,28 @@ int dhc_transform(int lattice, int f64, const double *z, double *T) {
     case kD3Q19: return f64 ? transform_t<kD3Q19, double>(z, T) : transform_t<kD3Q19, float>(z, T);
   }
   return -1;
+}
+
+int dhc_transform_pair(int lattice, const double *z2, double *T2) {
+  switch (lattice) {
+    case kD1Q3: return transform_pair_t<kD1Q3>(z2, T2);
+    case kD2Q9: return transform_pair_t<kD2Q9>(z2, T2);
+    case kD3Q19: return transform_pair_t<kD3Q19>(z2, T2);
+  }
+  return -1;
+}
+
+// flat_variate of two words at once (float2) against each alone (float):
+// the number of the n pairs whose lanes differ as bit patterns.
+int dhc_flat_pair_mismatches(const uint32_t *words, int64_t n) {
+  int bad = 0;
+  for (int64_t k = 0; k + 1 < 2 * n; k += 2) {
+    const float a = static_cast<float>(words[k] >> 8), b = static_cast<float>(words[k + 1] >> 8);
+    const float2 v = flat_variate<float2>(make_float2(a, b));
+    const float va = flat_variate<float>(a), vb = flat_variate<float>(b);
+    bad += memcmp(&v.x, &va, sizeof(float)) != 0 || memcmp(&v.y, &vb, sizeof(float)) != 0;
+  }
+  return bad;
 }
 
 int dhc_variates(int f64, int nmom, int dist, uint64_t seed, uint32_t lid, uint32_t site, uint64_t t, double *z) {

@@ -32,6 +32,8 @@ def dhc(tmp_path_factory):
     lib.dhc_philox.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.dhc_philox_site.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                     ctypes.c_void_p]
+    lib.dhc_transform_pair.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.dhc_flat_pair_mismatches.argtypes = [ctypes.c_void_p, ctypes.c_int64]
     lib.dhc_fastdiv_mismatches.restype = ctypes.c_int64
     lib.dhc_fastdiv_mismatches.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64]
     return lib
@@ -79,6 +81,38 @@ def test_noise_transform_is_the_basis(orc, dhc, lat, f64, tol):
         weighted = dhc.dhc_transform(lat, f64, z.ctypes.data, T.ctypes.data)
         expect = m[a + 1] * w if weighted else m[a + 1]
         assert np.max(np.abs(T - expect)) < tol * 4
+
+
+@pytest.mark.parametrize("lat", [lb.D1Q3, lb.D2Q9, lb.D3Q19])
+def test_two_site_transform_is_lane_by_lane_the_one_site_transform(orc, dhc, lat):
+    """The transform instantiated on float2 (two neighbouring sites, as the
+    paired collision runs it) gives in each lane the float transform of that
+    lane's variates, bit for bit (host build: two scalar operations per
+    packed one; the device instructions are checked on the GPU), and both
+    lanes are the oracle's transform to FP32 accuracy."""
+    Q = lb.Q_OF[lat]
+    m = orc.basis(lat)
+    _, _, _, w = orc.lattice(lat)
+    g = np.random.default_rng(lat + 11)
+    for _ in range(20):
+        z2 = g.standard_normal(2 * (Q - 1))
+        T2 = np.zeros(2 * Q)
+        assert dhc.dhc_transform_pair(lat, z2.ctypes.data, T2.ctypes.data) == 0
+        T1 = np.zeros(Q)
+        weighted = dhc.dhc_transform(lat, 0, z2[: Q - 1].copy().ctypes.data, T1.ctypes.data)
+        for lane in range(2):
+            zl = z2[lane * (Q - 1):(lane + 1) * (Q - 1)]
+            expect = m[1:].T @ zl
+            if weighted:
+                expect = expect * w
+            assert np.max(np.abs(T2[lane * Q:(lane + 1) * Q] - expect)) < 1e-5 * max(1.0, np.max(np.abs(expect)))
+
+
+def test_two_site_flat_variate_is_lane_by_lane(dhc):
+    g = np.random.default_rng(5)
+    words = np.concatenate([g.integers(0, 2**32, 4096, dtype=np.uint64),
+                            [0, 1, 255, 256, 2**31 - 1, 2**31, 2**32 - 256, 2**32 - 1]]).astype(np.uint32)
+    assert dhc.dhc_flat_pair_mismatches(words.ctypes.data, words.size // 2) == 0
 
 
 @pytest.mark.parametrize("nmom", [2, 8, 18])
